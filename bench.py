@@ -1,0 +1,418 @@
+"""Benchmark of the HHL state-vector hot path on GB300.
+
+python bench.py [--gpus N --steps K --warmup W] [--workload couette_1024|poiseuille_16|poiseuille_2p18]
+                [--impl ours|reference] [--precision c64|c128] [--gemm auto|simt|tcgen05]
+
+A step is one whole HHL solve of the workload: a1 prepare_rhs, a2..a5 apply_circuit (QPE
+controlled-U_k, fused inverse QFT + inversion RY + QFT, uncompute, clock Hadamards),
+a6 postselection statistics and a7 the dissipation readout, on device-resident inputs.
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent replica of
+the solve on its own GPU (the single solve does not shard; no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the plain gate-by-gate simulator) on the
+host cores on the same workload; it never touches a GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "statevector gate GB/s (% of HBM peak); batched HHL solves/s at 1e-6 fidelity"
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "couette_1024": dict(flow="couette", n_s=10, n_c=12, expm="dense", unit="HHL solves/s",
+                         desc="Couette flow, N=1024 (10 system qubits), n_c=12 clock + 1 ancilla = 23 qubits, "
+                              "dense controlled exp(i A t) as complex GEMMs"),
+    "poiseuille_16": dict(flow="poiseuille", n_s=4, n_c=6, expm="dense", unit="HHL solves/s", t0_rule="power_law",
+                          desc="Poiseuille flow, N=16, n_c=6, 11 qubits, T0 from the power law"),
+    "poiseuille_2p18": dict(flow="poiseuille", n_s=18, n_c=13, expm="trotter", unit="GB/s",
+                            trotter_dt=1024.0, trotter_steps_max=8,
+                            desc="Poiseuille flow, N=2^18, n_c=13, 32 qubits, Strang-Trotter exp(i A t)"),
+}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _fp32_simt_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# ------------------------------------------------------------------------------ oracle arm
+
+
+def _oracle_setup(wl: dict):
+    from oracle import hhl_oracle as o
+    from synth_inputs import rhs
+    n = 1 << wl["n_s"]
+    diag, off = o.laplacian_tridiag(n)
+    pl = o.plan(o.dense_from_tridiag(diag, off), wl["n_c"], t0_rule=wl.get("t0_rule", "range_fill"))
+    t_k = [pl["t0"] * (1 << k) / (1 << wl["n_c"]) for k in range(wl["n_c"])]
+    ev = [o.evolution_dense(pl["a_hat"], t) for t in t_k]
+    return o, pl, ev, rhs(wl["flow"], n)
+
+
+def _oracle_solve(o, pl, ev, b, wl):
+    psi = o.hhl_circuit(b, wl["n_s"], pl, evolutions=ev)
+    post = o.postselect(psi, wl["n_s"], wl["n_c"])
+    u = o.velocity(post["v"], float((b @ b) ** 0.5), pl["C"], pl["lam_ub"])
+    return o.dissipation(u, 0.0, 1.0 if wl["flow"] == "couette" else 0.0, 0.1)
+
+
+def cpu_baseline_sample(workload: str, budget_s: float = 30.0) -> dict:
+    """The oracle as it stands, timed on the host cores on whole solves of the workload
+    (the plan's matrix exponentials excluded, as on the GPU side); stops after the first
+    solve that takes the total past ``budget_s``."""
+    wl = WORKLOADS[workload]
+    if wl["expm"] != "dense":
+        return {"value": None, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+                "sample": "not run: the oracle has no 32-qubit path within the time budget"}
+    o, pl, ev, b = _oracle_setup(wl)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        _oracle_solve(o, pl, ev, b, wl)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 50:
+            break
+    return {"value": len(times) / sum(times), "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(times)} whole oracle solve(s) of {workload} (plan excluded), "
+                      f"{sum(times):.1f} s, numpy BLAS threads = {os.environ.get('OPENBLAS_NUM_THREADS', 'default')}"}
+
+
+def _cpu_baseline_subprocess(workload: str) -> dict:
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(os.cpu_count()), OMP_NUM_THREADS=str(os.cpu_count()),
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json, bench; print('CPUBASE' + json.dumps(bench.cpu_baseline_sample(%r)))" % workload)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=240)
+        for line in out.stdout.splitlines():
+            if line.startswith("CPUBASE"):
+                return json.loads(line[7:])
+        return {"value": None, "kind": "oracle", "sample": "failed: " + out.stderr[-300:]}
+    except Exception as e:
+        return {"value": None, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    if wl["expm"] != "dense":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle has no 32-qubit path within minutes"}))
+        return
+    o, pl, ev, b = _oracle_setup(wl)
+    for _ in range(min(args.warmup, 1)):
+        _oracle_solve(o, pl, ev, b, wl)
+    times = []
+    deadline = time.perf_counter() + 150.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _oracle_solve(o, pl, ev, b, wl)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > deadline:
+            break
+    value = len(times) / sum(times)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": len(times),
+        "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"]}, "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{len(times)} whole oracle solves (plan excluded)"},
+        "e2e": {"value": value, "unit": wl["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+
+def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
+    """Algorithmic work per launch of each kernel (flops for the GEMMs, bytes otherwise)."""
+    n_s, n_c = wl["n_s"], wl["n_c"]
+    N, R = 1 << n_s, 1 << n_c
+    half = R * N * prec_bytes
+    m_sub = R // 2
+    return {
+        "k_ctrl_gemm_simt<f32>": ("flop", 8.0 * m_sub * N * N),
+        "k_ctrl_gemm_simt<f64>": ("flop", 8.0 * m_sub * N * N),
+        "k_ctrl_gemm_tc": ("flop", 8.0 * m_sub * N * N),
+        "k_rows_scatter": ("byte", 2.0 * m_sub * N * prec_bytes),
+        "k_clock_block": ("byte", 3.0 * half),
+        "k_register_transform": ("byte", 2.0 * half),
+        "k_prep_fill": ("byte", 2.0 * half),
+        "k_measure_sums": ("byte", 2.0 * half),
+        "k_trotter_pass": ("byte", 2.0 * m_sub * N * prec_bytes),
+        "k_rows_copy_back": ("byte", 2.0 * m_sub * N * prec_bytes),
+    }
+
+
+def run_ours(args, rank: int, world: int, local_rank: int) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2307_00391_gb300 as pkg
+    from paper_2307_00391_gb300 import build as _b
+    from synth_inputs import rhs, walls
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pkg.load()
+    wl = WORKLOADS[args.workload]
+    n_s, n_c = wl["n_s"], wl["n_c"]
+    N = 1 << n_s
+    diag, off = pkg.laplacian(N)
+    b = rhs(wl["flow"], N)
+    plan = pkg.HHLPlan(n_s, n_c, diag=diag, off=off, precision=args.precision, expm=wl["expm"],
+                       t0_rule=wl.get("t0_rule", "range_fill"), gemm=args.gemm, nu=0.1, walls=walls(wl["flow"]),
+                       trotter_dt=wl.get("trotter_dt", 1.0), trotter_steps_max=wl.get("trotter_steps_max", 0))
+    info = plan.info
+    stream = torch.cuda.Stream()
+    st = plan.new_state()
+    b_dev = torch.tensor(b.astype(np.complex128), device="cuda")
+    meas = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
+    eps = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        plan.prepare_rhs(b_dev, st, stream=stream)
+        plan.apply_circuit(st, stream=stream)
+        plan.measure_async(st, meas, stream=stream)
+        plan.dissipation_async(st, eps, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM), L2 flushed between steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pkg.profile_reset()
+    pkg.profile_enable(True)
+    launches0 = pkg.kernel_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                evs[i][0].record(stream)
+                step()
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = pkg.kernel_launch_count() - launches0
+    pkg.profile_enable(False)
+    prof = pkg.profile_read()
+    step_ms = [a.elapsed_time(c) for a, c in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+
+    # ---- end to end through the public API with host buffers
+    b_pin = torch.tensor(b, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.prepare_rhs_host(b_pin, st, stream=stream)
+        plan.apply_circuit(st, stream=stream)
+        m = plan.measure(st, stream=stream)
+        e = plan.dissipation(st, stream=stream)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_times = e2e_times[1:]
+    if world > 1:
+        t = torch.tensor([sum(e2e_times)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    else:
+        e2e_total = sum(e2e_times)
+
+    if rank != 0:
+        return
+    peaks = _peaks()
+    prec_bytes = 8 if args.precision == "c64" else 16
+    alg = _algorithmic(info, wl, prec_bytes)
+    breakdown = {}
+    total_prof = sum(ms for _, ms in prof.values()) or 1.0
+    for name, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        breakdown[name] = {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
+                           "share": ms / total_prof}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    clocks = clk.summary()
+    roofline = None
+    hbm_bytes_step = 0.0
+    hbm_ms_step = 0.0
+    for name, (n, ms) in prof.items():
+        kind, per = alg.get(name, (None, 0.0))
+        if kind == "byte":
+            hbm_bytes_step += per * n / args.steps
+            hbm_ms_step += ms / args.steps
+    if dom is not None and dom in alg:
+        kind, per = alg[dom]
+        n, ms = prof[dom]
+        avg_s = ms / n / 1e3
+        if kind == "flop":
+            achieved = per / avg_s / 1e12
+            if dom.startswith("k_ctrl_gemm_tc"):
+                peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+                bound, pk_note = "tensor", "TF32 dense = measured bf16 burst x nominal TF32/bf16 ratio 1.1/2.25"
+            elif dom.endswith("<f64>"):
+                peak = 1.25
+                bound, pk_note = "alu", "FP64 nominal 1.25 TFLOP/s"
+            else:
+                peak = _fp32_simt_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+                bound, pk_note = "alu", "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x max SM clock"
+            roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": pk_note,
+                        "algorithmic_per_launch": per, "avg_launch_ms": avg_s * 1e3}
+        else:
+            achieved = per / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
+                        "algorithmic_per_launch": per, "avg_launch_ms": avg_s * 1e3}
+    if wl["unit"] == "GB/s":
+        value = world * hbm_bytes_step * args.steps / total_s / 1e9
+        e2e_value = world * hbm_bytes_step * len(e2e_times) / e2e_total / 1e9
+    else:
+        value = world * args.steps / total_s
+        e2e_value = world * len(e2e_times) / e2e_total
+    cpu = _cpu_baseline_subprocess(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
+    out = {
+        "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)" if args.precision == "c64" else "c128 (f64)",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
+                   "gemm_impl": ["auto", "simt", "tcgen05"][info["gemm_impl"]], "uncompute": "postselect-early",
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "gate_gbs": {"bytes_per_step": hbm_bytes_step, "ms_per_step": hbm_ms_step,
+                     "achieved_gbs": hbm_bytes_step / (hbm_ms_step / 1e3) / 1e9 if hbm_ms_step else None,
+                     "peak_gbs": peaks.get("hbm_gbs")},
+        "breakdown": breakdown,
+        "plan": {"plan_seconds": info["plan_seconds"], "t0": info["t0"], "kappa": info["kappa"],
+                 "gemm_flops_per_solve": info["gemm_flops"], "trotter_passes": info["trotter_passes"]},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": wl["unit"], "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": (4 + 2 * N) * 8 + 8 + 8},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "result": {"p_success": m["p_success"], "eps": e},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="couette_1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--gemm", default="auto", choices=["auto", "simt", "tcgen05"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * hhl.h - C ABI of the GB300 (sm_103a) state-vector engine for the HHL quantum
+ * linear-systems circuit (QLSA-1) applied to discretised Poiseuille and Couette flow
+ * (Bharadwaj & Sreenivasan, "Hybrid quantum algorithms for flow problems").
+ *
+ * The problem the calls follow is the one stated in Sec. IV: a Hermitian, non-singular
+ * A in C^{N x N} (N = 2^n), b in C^N, a number of phase-estimation (clock) qubits and a
+ * Hamiltonian-simulation time T0 (Sec. VI); the output is the postselected state
+ * proportional to A^{-1} b, its success probability, and the viscous dissipation rate
+ * eps = nu <(du/dy)^2> of the resulting velocity field (Sec. VII, App. D).
+ *
+ * Register layout of a state buffer (the only layout this library reads or writes):
+ *   amplitude index = sys | clk << n_s | anc << (n_s + n_c),   qubit q = index bit q.
+ * So the buffer is the row-major array S[anc][clk][sys] of 2^(n_s+n_c+1) amplitudes,
+ * complex64 (float re, float im) or complex128 (double re, double im) interleaved.
+ *
+ * Conventions (readings of the paper, which is silent on them):
+ *   Ahat = A / lambda_ub, lambda_ub = max_i sum_j |A_ij| (Gershgorin bound);
+ *   U_k  = exp(+i Ahat T0 2^k / 2^n_c) for clock bit k ("total" T0 convention);
+ *   QFT|x> = 2^(-m/2) sum_y exp(+2 pi i x y / 2^m)|y>, inverse QFT its inverse;
+ *   RY(theta) = exp(-i theta Y / 2); theta_y = 2 arcsin(min(1, C T0 / (2 pi y))), theta_0 = 0;
+ *   C = 2 pi / T0 unless given.
+ *
+ * Ownership: the caller owns every state buffer and stream. A plan owns the device copies
+ * of its tables (U_k matrices or Trotter blocks, rotation angles, twiddles), a small
+ * workspace, and frees them in hhl_plan_destroy. Device pointers are plain
+ * cudaMalloc'ed (or PyTorch-allocated) addresses on the current device; streams are
+ * cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Errors: no call throws or aborts. Every call returns an hhl_status; the thread-local
+ * text of the last failure is hhl_last_error(). Arguments are validated on the host
+ * before any CUDA call. Device-side failures map to HHL_ERR_CUDA; a bounded device wait
+ * that runs out maps to HHL_ERR_TIMEOUT.
+ *
+ * Threading: a plan may be used from one host thread at a time; calls are asynchronous
+ * on the given stream except where a host result is returned (hhl_measure,
+ * hhl_dissipation), which synchronise that stream.
+ */
+#ifndef HHL_H_
+#define HHL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HHL_API_VERSION 1
+
+typedef enum hhl_status {
+  HHL_OK = 0,
+  HHL_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, a bad enum value */
+  HHL_ERR_NOT_HERMITIAN = 2, /* |A_ij - conj(A_ji)| > 1e-12 max|A| */
+  HHL_ERR_SINGULAR = 3,      /* |lambda|_min <= 1e-14 |lambda|_max, or |b| = 0 */
+  HHL_ERR_OOM = 4,           /* device allocation failed */
+  HHL_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
+  HHL_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+  HHL_ERR_NUMERIC = 7,       /* a non-finite value where a finite one is required */
+  HHL_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement */
+} hhl_status;
+
+typedef enum hhl_matrix_kind {
+  HHL_MATRIX_TRIDIAG = 0, /* real symmetric tridiagonal: diag[N], off[N-1] */
+  HHL_MATRIX_DENSE = 1    /* Hermitian, row-major dense_re/dense_im (N <= 256) */
+} hhl_matrix_kind;
+
+typedef enum hhl_t0_rule {
+  HHL_T0_USER = 0,       /* params.t0 as given (in params.t0_convention) */
+  HHL_T0_POWER_LAW = 1,  /* T0_per_unit = exp(0.918) kappa^-0.363: the T0*-kappa fit of
+                            Sec. VI read as a power law (a fallback; unpinned) */
+  HHL_T0_RANGE_FILL = 2  /* T0 = 2 pi (2^n_c - 1): lambdahat = 1 maps to the top clock value */
+} hhl_t0_rule;
+
+typedef enum hhl_t0_convention {
+  HHL_T0_TOTAL = 0,    /* U_k = exp(i Ahat T0 2^k / 2^n_c) */
+  HHL_T0_PER_UNIT = 1  /* U_k = exp(i Ahat T0 2^k): converted by T0_total = 2^n_c T0 */
+} hhl_t0_convention;
+
+typedef enum hhl_expm_mode {
+  HHL_EXPM_DENSE = 0,  /* U_k as dense N x N matrices; controlled U_k = complex GEMM */
+  HHL_EXPM_TROTTER = 1 /* U_k as a second-order Strang product of two-level gates
+                          (Toeplitz tridiagonal A only) */
+} hhl_expm_mode;
+
+typedef enum hhl_precision {
+  HHL_PREC_C64 = 32, /* complex64 amplitudes; FP64 angles, norms, probabilities */
+  HHL_PREC_C128 = 64 /* complex128 amplitudes throughout */
+} hhl_precision;
+
+typedef enum hhl_gemm_impl {
+  HHL_GEMM_AUTO = 0,    /* tensor cores (tcgen05, split TF32) for complex64 where built */
+  HHL_GEMM_SIMT = 1,    /* CUDA-core FMA tiles (FP32 or FP64) */
+  HHL_GEMM_TCGEN05 = 2  /* force the tcgen05 path (complex64 only) */
+} hhl_gemm_impl;
+
+/* The linear system A x = b of the steady channel flow (Sec. II Eq. 3, App. A.1). All
+ * pointers are HOST memory, read during hhl_plan_create only. */
+typedef struct hhl_problem {
+  int32_t kind;           /* hhl_matrix_kind */
+  int32_t n_sys_qubits;   /* n_s >= 1; N = 2^n_s */
+  const double* diag;     /* TRIDIAG: A_ii, length N */
+  const double* off;      /* TRIDIAG: A_{i,i+1} = A_{i+1,i}, length N-1 */
+  const double* dense_re; /* DENSE: Re A, row-major N x N */
+  const double* dense_im; /* DENSE: Im A, row-major N x N, or NULL for real symmetric */
+  double nu;              /* kinematic viscosity of the dissipation readout */
+  double wall_lo;         /* u(y=0) */
+  double wall_hi;         /* u(y=1) */
+} hhl_problem;
+
+typedef struct hhl_params {
+  int32_t n_clock;           /* n_c, 1..16 phase-estimation qubits */
+  int32_t t0_rule;           /* hhl_t0_rule */
+  int32_t t0_convention;     /* hhl_t0_convention (HHL_T0_USER only) */
+  int32_t precision;         /* hhl_precision */
+  double t0;                 /* HHL_T0_USER: the simulation time */
+  double C;                  /* inversion constant; 0 => 2 pi / T0 */
+  int32_t expm_mode;         /* hhl_expm_mode */
+  int32_t full_uncompute;    /* 1: uncompute both ancilla halves (the whole circuit);
+                                0: after the inversion rotation only the anc = 1 half is
+                                carried on (the anc = 0 half is left as rotated); the
+                                postselected result is identical */
+  double trotter_dt;         /* Strang step bound: r_k = clamp(ceil(t_k / dt), 1, max) */
+  int32_t trotter_steps_max; /* 0 = no cap */
+  int32_t gemm_impl;         /* hhl_gemm_impl */
+} hhl_params;
+
+typedef struct hhl_plan_info {
+  int32_t n_sys_qubits, n_clock, n_qubits, precision, expm_mode, gemm_impl;
+  double lambda_ub;       /* Gershgorin bound used to normalise A */
+  double lambda_min;      /* smallest eigenvalue of A (0 if not computed) */
+  double lambda_max;      /* largest eigenvalue of A (0 if not computed) */
+  double kappa;           /* condition number */
+  double t0;              /* T0 in the total convention */
+  double C;               /* inversion constant */
+  uint64_t state_bytes;   /* bytes of one state buffer for this plan */
+  uint64_t table_bytes;   /* device bytes of U_k / Trotter / angle tables */
+  uint64_t workspace_bytes;
+  double gemm_flops;      /* algorithmic flops of the controlled-U GEMMs of one circuit */
+  int64_t trotter_passes; /* Strang steps of one circuit (Trotter mode) */
+  double plan_seconds;    /* wall time of hhl_plan_create */
+} hhl_plan_info;
+
+typedef struct hhl_measurement {
+  double p_success; /* |v|^2, v = amplitudes with anc = 1 and clock = 0 */
+  double p_anc1;    /* total weight of the anc = 1 half */
+  double norm;      /* total weight of the state */
+  double b_norm;    /* |b| recorded by the last hhl_prepare_rhs on this plan */
+} hhl_measurement;
+
+typedef struct hhl_plan_s* hhl_plan_t;
+
+/* Version / diagnostics */
+int hhl_api_version(void);
+const char* hhl_status_string(hhl_status s);
+const char* hhl_last_error(void); /* thread-local detail of the last failure */
+
+/* Fill p with the defaults: n_clock 6, RANGE_FILL, TOTAL, C64, DENSE, postselect-early
+ * uncompute, trotter_dt 1, no step cap, GEMM AUTO. */
+void hhl_params_default(hhl_params* p);
+
+/* a0 - classical pre-computation (Sec. II.A: the parameters "beta" computed
+ * classically; Sec. VI: exp(i A T0) through the spectral decomposition of A).
+ * Validates A, normalises it by lambda_ub, computes kappa, T0, C, the rotation angles
+ * theta_y in FP64, the U_k matrices (dense mode; on the device, FP64) or the Strang
+ * blocks (Trotter mode), and uploads the tables. On success *out owns device memory.
+ * Requires A positive definite (the clock value is read as an unsigned fraction). */
+hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hhl_plan_t* out);
+void hhl_plan_destroy(hhl_plan_t plan);
+hhl_status hhl_plan_get_info(hhl_plan_t plan, hhl_plan_info* info);
+uint64_t hhl_state_bytes(hhl_plan_t plan);
+
+/* a1 - amplitude encoding of b (Sec. IV.A: the right-hand side loaded as a quantum state)
+ * followed by a Hadamard on every clock qubit: S[0][c][:] = b / (|b| 2^(n_c/2)),
+ * S[1][:][:] = 0. b_dev: DEVICE complex128 (re, im interleaved), length N. |b| is kept
+ * on the device for the dissipation readout. Error if |b| = 0 is detected later by
+ * hhl_measure / hhl_dissipation (HHL_ERR_SINGULAR). */
+hhl_status hhl_prepare_rhs(hhl_plan_t plan, const double* b_dev, void* state_dev, void* stream);
+
+/* As hhl_prepare_rhs with b in HOST memory (b_im may be NULL for real b): copies b to
+ * a plan-owned device buffer on the stream, then encodes it. */
+hhl_status hhl_prepare_rhs_host(hhl_plan_t plan, const double* b_re, const double* b_im,
+                                void* state_dev, void* stream);
+
+/* a2..a5 - the circuit after state preparation, in place (Sec. IV/VI, standard HHL):
+ * clock-bit-controlled U_k for k = 0..n_c-1, inverse QFT on the clock, clock-controlled
+ * RY on the ancilla, QFT on the clock, controlled U_k^dagger for k = n_c-1..0, Hadamard on
+ * every clock qubit. With full_uncompute = 0 the last three stages act on the anc = 1
+ * half only. */
+hhl_status hhl_apply_circuit(hhl_plan_t plan, void* state_dev, void* stream);
+
+/* The stages of hhl_apply_circuit one at a time, for checking each kernel on its own.
+ * HHL_STAGE_QPE_U: controlled U_k, k = 0..n_c-1, on the anc = 0 half.
+ * HHL_STAGE_CLOCK_BLOCK: inverse QFT + controlled RY + QFT, fused.
+ * HHL_STAGE_UNCOMPUTE_U: controlled U_k^dagger on the anc = 1 half (and anc = 0 if full).
+ * HHL_STAGE_FINAL_H: Hadamards on the clock of the same half or halves. */
+typedef enum hhl_stage {
+  HHL_STAGE_QPE_U = 0,
+  HHL_STAGE_CLOCK_BLOCK = 1,
+  HHL_STAGE_UNCOMPUTE_U = 2,
+  HHL_STAGE_FINAL_H = 3
+} hhl_stage;
+hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void* stream);
+
+/* a6 - postselection statistics (Sec. II.A: the end solution read by measurement).
+ * Asynchronous form: writes to out_dev (DEVICE, 4 + 2N doubles): [p_success, p_anc1,
+ * norm, b_norm, xhat_0.re, xhat_0.im, ...], xhat = v / |v|. */
+hhl_status hhl_measure_async(hhl_plan_t plan, const void* state_dev, double* out_dev, void* stream);
+
+/* Synchronous form: fills *out; if x_host != NULL writes xhat (HOST, 2N doubles,
+ * re/im interleaved). Synchronises the stream. HHL_ERR_SINGULAR if p_success = 0. */
+hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* out,
+                       double* x_host, void* stream);
+
+/* a7 - in-situ viscous dissipation rate (Sec. VII, App. D: eps = nu <(du/dy)^2>, the
+ * same finite-difference post-processing as the classical solution). The velocity is
+ * u_i = |b| Re(v_i) / (C lambda_ub) at the N interior nodes, u_0 = wall_lo,
+ * u_{N+1} = wall_hi, and eps = nu h sum_{i=0}^{N} ((u_{i+1} - u_i)/h)^2, h = 1/(N+1).
+ * Asynchronous form writes eps to eps_dev (DEVICE, 1 double). */
+hhl_status hhl_dissipation_async(hhl_plan_t plan, const void* state_dev, double* eps_dev, void* stream);
+
+/* Synchronous form: *eps_out (HOST); if u_host != NULL also the N velocities (HOST). */
+hhl_status hhl_dissipation(hhl_plan_t plan, const void* state_dev, double* eps_out,
+                           double* u_host, void* stream);
+
+/* Fused gate block: QFT (inverse = 0) or inverse QFT (inverse = 1) on the m-qubit
+ * register of bits [lo, lo + m) of an n-qubit state, in place (the QFT / IQFT subroutine
+ * of the algorithm library, App. B; the circuit of the Fig. 1c scaling experiment).
+ * precision: HHL_PREC_C64 or HHL_PREC_C128. Requires 1 <= m <= 13, lo + m <= n <= 34. */
+hhl_status hhl_apply_qft(void* state_dev, int32_t n_qubits, int32_t lo, int32_t m,
+                         int32_t inverse, int32_t precision, void* stream);
+
+/* Number of kernels this library has launched since load (all entry points). */
+uint64_t hhl_kernel_launch_count(void);
+
+/* Per-kernel device timing (tracing). While enabled, every kernel launch is bracketed by
+ * a pair of CUDA events on its stream; reading the profile waits for those events and
+ * folds them into per-kernel totals (launch count, summed milliseconds). Process-wide,
+ * off by default; enabling adds two event records per launch. */
+void hhl_profile_enable(int32_t on);
+void hhl_profile_reset(void);
+int32_t hhl_profile_count(void);
+/* Entry `index` (0 .. count-1, sorted by kernel name): name copied NUL-terminated into
+ * name[name_len]; launches and total_ms may be NULL. */
+hhl_status hhl_profile_get(int32_t index, char* name, int32_t name_len, uint64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHL_H_ */

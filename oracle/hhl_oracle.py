@@ -312,10 +312,28 @@ def trotter_unitary(diag_hat: np.ndarray, off_hat: np.ndarray, t: float, r: int)
     return u
 
 
+def _pair_blocks(diag_hat: np.ndarray, off_hat: np.ndarray, start: int, s: float,
+                 with_diag: bool) -> np.ndarray:
+    """exp(i s M_i) for the 2x2 blocks M_i = [[d_i, o_i], [o_i, d_i+1]] (or without the
+    diagonal) of the pairs (i, i+1), i = start, start+2, ...; equal blocks share one
+    library exponential."""
+    n = len(diag_hat)
+    cache: dict = {}
+    out = []
+    for i in range(start, n - 1, 2):
+        key = (diag_hat[i] if with_diag else 0.0, off_hat[i], diag_hat[i + 1] if with_diag else 0.0)
+        if key not in cache:
+            blk = np.array([[key[0], key[1]], [key[1], key[2]]])
+            cache[key] = scipy.linalg.expm(1j * s * blk)
+        out.append(cache[key])
+    return np.array(out).reshape(-1, 2, 2)
+
+
 def apply_trotter_controlled(psi: np.ndarray, n: int, n_s: int, control: int,
                              diag_hat: np.ndarray, off_hat: np.ndarray, t: float, r: int) -> None:
     """Gate by gate: r Strang steps of exp(i Ahat t) on the system register, each 2x2 block
-    a two-level gate on basis states (i, i+1), all conditioned on qubit ``control``."""
+    a two-level gate on basis states (i, i+1), all conditioned on qubit ``control``. The
+    gates of one layer act on disjoint pairs and commute, so a layer is applied at once."""
     nsys = 1 << n_s
     tau = t / r
     rows = psi.reshape((-1, nsys))
@@ -323,14 +341,16 @@ def apply_trotter_controlled(psi: np.ndarray, n: int, n_s: int, control: int,
     sel = ((ridx >> control) & 1) == 1
 
     def two_level_layer(start: int, s: float, with_diag: bool) -> None:
-        for i in range(start, nsys - 1, 2):
-            blk = np.array([[diag_hat[i] if with_diag else 0.0, off_hat[i]],
-                            [off_hat[i], diag_hat[i + 1] if with_diag else 0.0]])
-            g = scipy.linalg.expm(1j * s * blk)
-            a0 = rows[sel, i].copy()
-            a1 = rows[sel, i + 1].copy()
-            rows[sel, i] = g[0, 0] * a0 + g[0, 1] * a1
-            rows[sel, i + 1] = g[1, 0] * a0 + g[1, 1] * a1
+        g = _pair_blocks(diag_hat, off_hat, start, s, with_diag)
+        if g.shape[0] == 0:
+            return
+        i0 = np.arange(start, nsys - 1, 2)
+        sub = rows[sel]
+        a0 = sub[:, i0].copy()
+        a1 = sub[:, i0 + 1].copy()
+        sub[:, i0] = g[:, 0, 0] * a0 + g[:, 0, 1] * a1
+        sub[:, i0 + 1] = g[:, 1, 0] * a0 + g[:, 1, 1] * a1
+        rows[sel] = sub
 
     for _ in range(r):
         two_level_layer(0, tau / 2.0, True)

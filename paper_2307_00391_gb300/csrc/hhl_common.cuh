@@ -1,0 +1,119 @@
+// Internal definitions shared by the translation units of libhhl (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/hhl.h"
+
+namespace hhl {
+
+// ------------------------------------------------------------------ error reporting
+void set_error(const std::string& msg);
+hhl_status fail(hhl_status s, const std::string& msg);
+hhl_status cuda_fail(cudaError_t e, const char* what);
+extern std::atomic<uint64_t> g_launches;
+
+#define HHL_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return ::hhl::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Per-kernel timing (hhl_profile_*): when enabled, an event pair brackets every launch on
+// its stream; the pairs are resolved into per-kernel totals when the profile is read.
+extern std::atomic<bool> g_prof_on;
+void prof_begin(cudaStream_t st);
+void prof_end(const char* name);
+#define HHL_PROF_BEGIN(st)                                            \
+  do {                                                                \
+    if (::hhl::g_prof_on.load(std::memory_order_relaxed)) ::hhl::prof_begin(st); \
+  } while (0)
+
+// Check the launch just issued, count it, and close its timing record.
+#define HHL_LAUNCH_CHECK(name)                                 \
+  do {                                                         \
+    ::hhl::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    cudaError_t _e = cudaGetLastError();                       \
+    if (::hhl::g_prof_on.load(std::memory_order_relaxed)) ::hhl::prof_end(name); \
+    if (_e != cudaSuccess) return ::hhl::cuda_fail(_e, name);  \
+  } while (0)
+
+// ------------------------------------------------------------------ complex helpers
+template <class R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <class R> __host__ __device__ __forceinline__ typename Cx<R>::T mk(R re, R im) {
+  typename Cx<R>::T z; z.x = re; z.y = im; return z;
+}
+template <class T> __host__ __device__ __forceinline__ T cadd(T a, T b) { T z; z.x = a.x + b.x; z.y = a.y + b.y; return z; }
+template <class T> __host__ __device__ __forceinline__ T csub(T a, T b) { T z; z.x = a.x - b.x; z.y = a.y - b.y; return z; }
+template <class T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+template <class T> __host__ __device__ __forceinline__ T cconjmul(T a, T b) {  // a * conj(b)
+  T z; z.x = a.x * b.x + a.y * b.y; z.y = a.y * b.x - a.x * b.y; return z;
+}
+template <class T, class S> __host__ __device__ __forceinline__ T cscale(T a, S s) { T z; z.x = a.x * s; z.y = a.y * s; return z; }
+
+// ------------------------------------------------------------------ the plan
+struct Plan {
+  int n_s = 0, n_c = 0, n = 0;
+  int prec = HHL_PREC_C64;
+  int expm_mode = HHL_EXPM_DENSE;
+  int full = 0;
+  int gemm_impl = HHL_GEMM_SIMT;
+  int64_t N = 0;   // 2^n_s
+  int64_t R = 0;   // 2^n_c
+  double lam_ub = 0, lam_min = 0, lam_max = 0, kappa = 0, t0 = 0, C = 0;
+  double nu = 0, wall_lo = 0, wall_hi = 0;
+  std::vector<double> theta;  // rotation angles, 2^n_c
+  // device tables
+  void* d_bfwd = nullptr;     // n_c matrices, B_fwd[k][m][n] = U_k[n][m]   (SIMT GEMM operand)
+  void* d_badj = nullptr;     // n_c matrices, B_adj[k][m][n] = conj(U_k[m][n])
+  void* d_tc = nullptr;       // tcgen05 operands (split-TF32 real embeddings), see hhl_gemm_tc.cu
+  void* d_rot = nullptr;      // 2^n_c (cos(theta/2), sin(theta/2)) pairs, amplitude precision
+  double* d_scal = nullptr;   // device scalars: [0] |b|^2, [1..3] measure sums, [4] eps sum, [5] p_anc1
+  double* d_b = nullptr;      // N complex128: host-prepared b
+  void* d_scratch = nullptr;  // GEMM output rows: 2^(n_c-1) * N amplitudes
+  // Trotter (Toeplitz tridiagonal): per k the step count and the 2x2 blocks
+  std::vector<int> trot_r;
+  std::vector<double> trot_blocks;  // per k: E(tau/2), E(tau), O(tau): 3 x 8 doubles
+  double* d_trot = nullptr;
+  double trotter_dt = 1.0;
+  int trotter_max = 0;
+  uint64_t table_bytes = 0, workspace_bytes = 0;
+  double gemm_flops = 0;
+  int64_t trotter_passes = 0;
+  double plan_seconds = 0;
+  int device = 0;
+  size_t amp_bytes() const { return prec == HHL_PREC_C64 ? 8 : 16; }
+};
+
+// Launchers (host side of the kernels); all return HHL_OK or an error.
+hhl_status launch_bnorm(const double* b, int64_t N, double* acc, cudaStream_t st);
+hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStream_t st);
+hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st);
+hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st);
+hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st);
+hhl_status launch_dissipation(const Plan& p, const void* state, double* eps, double* u_dev, cudaStream_t st);
+hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st);
+hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_vi, const double* d_cos,
+                             const double* d_sin, double wgt, double2* d_u, cudaStream_t st);
+hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);
+hhl_status launch_trotter(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+hhl_status launch_interleave(const double* re, const double* im, int64_t n, double* out, cudaStream_t st);
+
+// tcgen05 GEMM (hhl_gemm_tc.cu)
+bool tc_supported(const Plan& p);
+hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t st);
+hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+void tc_free(Plan& p);
+
+}  // namespace hhl

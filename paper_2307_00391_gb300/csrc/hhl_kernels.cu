@@ -1,0 +1,619 @@
+// CUDA kernels of the HHL state-vector path (sm_103a): state preparation, the SIMT
+// controlled-U GEMM, the fused clock block (inverse QFT + eigenvalue-inversion RY + QFT),
+// clock Hadamards, QFT register blocks, postselection / dissipation reductions, and the
+// plan-time exponential exp(i Ahat t) from an eigendecomposition.
+//
+// State layout: S[anc][clk][sys] row-major, complex64 or complex128 interleaved; the
+// "active half" of a stage is S[0] or S[1], a row-major (2^n_c x N) matrix whose row c is
+// the system register for clock value c.
+#include <math.h>
+
+#include "hhl_common.cuh"
+
+namespace hhl {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV per-thread values over the block and add them to dst[0..NV) with one atomic each.
+template <int NV>
+__device__ void block_sum_atomic(const double (&v)[NV], double* dst) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) sh[i][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = lane < nw ? sh[i][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) atomicAdd(dst + i, s);
+    }
+  }
+}
+
+int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Subset index i -> row c of the 2^n_c rows whose bit k is 1.
+__device__ __forceinline__ int64_t row_with_bit(int64_t i, int k) {
+  return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
+}
+
+// ------------------------------------------------------------------------------ prep
+
+__global__ void k_bnorm(const double2* __restrict__ b, int64_t n, double* acc) {
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 z = b[i];
+    s[0] += z.x * z.x + z.y * z.y;
+  }
+  block_sum_atomic<1>(s, acc);
+}
+
+template <class R>
+__global__ void k_prep_fill(const double2* __restrict__ b, const double* __restrict__ acc,
+                            typename Cx<R>::T* __restrict__ st, int n_s, int n_c) {
+  const int64_t nmask = (1LL << n_s) - 1;
+  const int64_t half = 1LL << (n_s + n_c);
+  const double nb2 = acc[0];
+  const double scale = nb2 > 0.0 ? 1.0 / sqrt(nb2 * (double)(1LL << n_c)) : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * half; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < half) {
+      double2 z = b[i & nmask];
+      st[i] = mk<R>((R)(z.x * scale), (R)(z.y * scale));
+    } else {
+      st[i] = mk<R>((R)0, (R)0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ SIMT GEMM
+// out[i][n] = sum_m S[row(i)][m] * B[m][n] for the M_sub = 2^(n_c-1) rows with clock bit k
+// set; B = U_k^T (forward) or conj(U_k) (adjoint) so that out row = U row.
+template <class R, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_ctrl_gemm_simt(const typename Cx<R>::T* __restrict__ S,
+                                                        typename Cx<R>::T* __restrict__ out,
+                                                        const typename Cx<R>::T* __restrict__ B,
+                                                        int n_s, int k, int64_t m_sub) {
+  using T = typename Cx<R>::T;
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+  const int64_t N = 1LL << n_s;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  R accr[TM][TN], acci[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) { accr[a][c] = 0; acci[a][c] = 0; }
+
+  for (int64_t m0 = 0; m0 < N; m0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      const int r = e / BK, kk = e % BK;
+      const int64_t i = i0 + r, m = m0 + kk;
+      T v = mk<R>((R)0, (R)0);
+      if (i < m_sub && m < N) v = S[row_with_bit(i, k) * N + m];
+      As[kk][r] = v;
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      const int kk = e / BN, c = e % BN;
+      const int64_t m = m0 + kk, n = n0 + c;
+      T v = mk<R>((R)0, (R)0);
+      if (m < N && n < N) v = B[m * N + n];
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], bb[TN];
+#pragma unroll
+      for (int x = 0; x < TM; ++x) a[x] = As[kk][ty + 16 * x];
+#pragma unroll
+      for (int y = 0; y < TN; ++y) bb[y] = Bs[kk][tx + 16 * y];
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TN; ++y) {
+          accr[x][y] = fma(a[x].x, bb[y].x, accr[x][y]);
+          accr[x][y] = fma(-a[x].y, bb[y].y, accr[x][y]);
+          acci[x][y] = fma(a[x].x, bb[y].y, acci[x][y]);
+          acci[x][y] = fma(a[x].y, bb[y].x, acci[x][y]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+    const int64_t i = i0 + ty + 16 * x;
+    if (i >= m_sub) continue;
+#pragma unroll
+    for (int y = 0; y < TN; ++y) {
+      const int64_t n = n0 + tx + 16 * y;
+      if (n < N) out[i * N + n] = mk<R>(accr[x][y], acci[x][y]);
+    }
+  }
+}
+
+// S[row(i)][:] = out[i][:] for the rows with clock bit k set.
+template <class R>
+__global__ void k_rows_scatter(typename Cx<R>::T* __restrict__ S, const typename Cx<R>::T* __restrict__ out,
+                               int n_s, int k, int64_t m_sub) {
+  const int64_t N = 1LL << n_s;
+  const int64_t total = m_sub * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e >> n_s, m = e & (N - 1);
+    S[row_with_bit(i, k) * N + m] = out[e];
+  }
+}
+
+// ------------------------------------------------------------------------------ column FFTs
+// W columns of length L = 2^m live in shared memory as X[w*L + idx]. tw[j] = exp(-2 pi i j / L).
+
+template <class R>
+__device__ void fill_twiddles(typename Cx<R>::T* tw, int m) {
+  const int L = 1 << m;
+  for (int j = threadIdx.x; j < L / 2; j += blockDim.x) {
+    R s, c;
+    if constexpr (sizeof(R) == 4) {
+      sincospif(-2.0f * (float)j / (float)L, &s, &c);
+    } else {
+      sincospi(-2.0 * (double)j / (double)L, &s, &c);
+    }
+    tw[j] = mk<R>(c, s);
+  }
+}
+
+// Decimation in time: bit-reversed input, natural-order output.
+// conj_tw = false: out[y] = sum_c x[c] e^{-2 pi i c y/L}; true: e^{+2 pi i c y/L}.
+template <class T>
+__device__ void fft_dit(T* X, const T* tw, int m, int W, bool conj_tw) {
+  const int L = 1 << m, hl = L >> 1;
+  for (int s = 1; s <= m; ++s) {
+    const int half = 1 << (s - 1);
+    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
+      const int w = t / hl, b = t - w * hl;
+      const int g = b / half, j = b - g * half;
+      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
+      T f = tw[j << (m - s)];
+      if (conj_tw) f.y = -f.y;
+      T a = X[i0], c = cmul(X[i1], f);
+      X[i0] = cadd(a, c);
+      X[i1] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// Decimation in frequency: natural-order input, bit-reversed output.
+template <class T>
+__device__ void fft_dif(T* X, const T* tw, int m, int W, bool conj_tw) {
+  const int L = 1 << m, hl = L >> 1;
+  for (int s = m; s >= 1; --s) {
+    const int half = 1 << (s - 1);
+    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
+      const int w = t / hl, b = t - w * hl;
+      const int g = b / half, j = b - g * half;
+      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
+      T f = tw[j << (m - s)];
+      if (conj_tw) f.y = -f.y;
+      T a = X[i0], c = X[i1];
+      X[i0] = cadd(a, c);
+      X[i1] = cmul(csub(a, c), f);
+    }
+    __syncthreads();
+  }
+}
+
+// Walsh-Hadamard butterflies (one Hadamard per qubit, unnormalised).
+template <class T>
+__device__ void wht(T* X, int m, int W) {
+  const int L = 1 << m, hl = L >> 1;
+  for (int s = 1; s <= m; ++s) {
+    const int half = 1 << (s - 1);
+    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
+      const int w = t / hl, b = t - w * hl;
+      const int g = b / half, j = b - g * half;
+      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
+      T a = X[i0], c = X[i1];
+      X[i0] = cadd(a, c);
+      X[i1] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int x, int m) { return (int)(__brev((unsigned)x) >> (32 - m)); }
+
+// Fused clock block (a3 + a4 + the QFT of a5): per group of W system columns, load the
+// 2^n_c clock column of the anc = 0 half, inverse QFT, apply RY(theta_y) to the ancilla
+// (anc1 = sin(theta_y/2) x, anc0 = cos(theta_y/2) x), QFT, store the anc = 1 half. The
+// anc = 0 half is stored after the QFT as well when FULL, else as it is after the rotation.
+template <class R, bool FULL>
+__global__ void __launch_bounds__(512) k_clock_block(typename Cx<R>::T* __restrict__ S,
+                                                     const typename Cx<R>::T* __restrict__ rot,
+                                                     int n_s, int n_c, int W) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << n_c;
+  const int64_t N = 1LL << n_s;
+  const int64_t half = (int64_t)L * N;
+  T* tw = reinterpret_cast<T*>(smem_raw);
+  T* X = tw + L / 2;
+  T* Y = X + (size_t)W * L;
+  fill_twiddles<R>(tw, n_c);
+  const int64_t j0 = (int64_t)blockIdx.x * W;
+  T* S0 = S;
+  T* S1 = S + half;
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+    const int c = e / W, w = e - c * W;
+    X[w * L + bitrev(c, n_c)] = S0[(int64_t)c * N + j0 + w];
+  }
+  __syncthreads();
+  fft_dit(X, tw, n_c, W, false);
+  const R inv = (R)(1.0 / sqrt((double)L));
+  // y-major with w fastest, so that the anc = 0 stores of the early mode are contiguous.
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+    const int y = e / W, w = e - y * W;
+    const int idx = w * L + y;
+    const T r = rot[y];  // (cos(theta_y/2), sin(theta_y/2))
+    const T x = cscale(X[idx], inv);
+    if (FULL) Y[idx] = cscale(x, r.x);
+    else S0[(int64_t)y * N + j0 + w] = cscale(x, r.x);  // anc = 0 half left as rotated
+    X[idx] = cscale(x, r.y);
+  }
+  __syncthreads();
+  fft_dif(X, tw, n_c, W, true);
+  if (FULL) fft_dif(Y, tw, n_c, W, true);
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+    const int c = e / W, w = e - c * W;
+    const int src = w * L + bitrev(c, n_c);
+    S1[(int64_t)c * N + j0 + w] = cscale(X[src], inv);
+    if (FULL) S0[(int64_t)c * N + j0 + w] = cscale(Y[src], inv);
+  }
+}
+
+// Generic register transform on bits [lo, lo+m): mode 0 = QFT, 1 = inverse QFT,
+// 2 = Hadamard on each qubit. Column (o, g): elements base + c * 2^lo + w, base =
+// o * 2^(lo+m) + g * W, for w < W (W divides 2^lo).
+template <class R>
+__global__ void __launch_bounds__(512) k_register_transform(typename Cx<R>::T* __restrict__ S, int lo, int m,
+                                                            int W, int mode) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << m;
+  const int64_t inner = 1LL << lo;
+  T* tw = reinterpret_cast<T*>(smem_raw);
+  T* X = tw + L / 2;
+  if (mode != 2) fill_twiddles<R>(tw, m);
+  const int64_t groups = inner / W;
+  const int64_t o = blockIdx.x / groups, g = blockIdx.x - o * groups;
+  T* base = S + o * ((int64_t)L << lo) + g * W;
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+    const int c = e / W, w = e - c * W;
+    const int dst = (mode == 2) ? (w * L + c) : (w * L + bitrev(c, m));
+    X[dst] = base[(int64_t)c * inner + w];
+  }
+  __syncthreads();
+  if (mode == 2) wht(X, m, W);
+  else fft_dit(X, tw, m, W, mode == 0);
+  const R inv = (R)(1.0 / sqrt((double)L));
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+    const int c = e / W, w = e - c * W;
+    base[(int64_t)c * inner + w] = cscale(X[w * L + c], inv);
+  }
+}
+
+// ------------------------------------------------------------------------------ readout
+
+template <class R>
+__global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N, double* acc) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * half; i += (int64_t)gridDim.x * blockDim.x) {
+    const typename Cx<R>::T z = S[i];
+    const double p = (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+    if (i < half) {
+      v[0] += p;
+    } else {
+      v[1] += p;
+      if (i - half < N) v[2] += p;
+    }
+  }
+  block_sum_atomic<3>(v, acc);
+}
+
+// out = [p_success, p_anc1, norm, |b|, xhat (2N doubles)]
+template <class R>
+__global__ void k_measure_finish(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N,
+                                 const double* __restrict__ scal, double* __restrict__ out) {
+  const double ps = scal[3];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    out[0] = ps;
+    out[1] = scal[2];
+    out[2] = scal[1] + scal[2];
+    out[3] = sqrt(scal[0]);
+  }
+  const double inv = ps > 0.0 ? 1.0 / sqrt(ps) : 0.0;
+  for (int64_t j = i; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const typename Cx<R>::T z = S[half + j];
+    out[4 + 2 * j] = (double)z.x * inv;
+    out[5 + 2 * j] = (double)z.y * inv;
+  }
+}
+
+// Dissipation: sum over the N+1 cells of (u_{i+1} - u_i)^2 with walls at both ends.
+template <class R>
+__global__ void k_diss_sum(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N,
+                           const double* __restrict__ scal, double inv_c_lam, double wlo, double whi,
+                           double* acc, double* __restrict__ u_out) {
+  const double scale = sqrt(scal[0]) * inv_c_lam;
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double left = (i == 0) ? wlo : scale * (double)S[half + i - 1].x;
+    const double right = (i == N) ? whi : scale * (double)S[half + i].x;
+    const double d = right - left;
+    s[0] += d * d;
+    if (u_out != nullptr && i < N) u_out[i] = right;
+  }
+  block_sum_atomic<1>(s, acc);
+}
+
+__global__ void k_diss_finish(const double* __restrict__ acc, double nu_over_h, double* eps) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) eps[0] = nu_over_h * acc[0];
+}
+
+// ------------------------------------------------------------------------------ plan kernels
+// U[n][m] = wgt sum_j e^{i phi_j} (Vr + i Vi)[n][j] conj((Vr + i Vi)[m][j]), FP64.
+__global__ void __launch_bounds__(256) k_expm_eigen(int N, int J, const double* __restrict__ vr,
+                                                    const double* __restrict__ vi, const double* __restrict__ cph,
+                                                    const double* __restrict__ sph, double wgt, double2* __restrict__ U) {
+  __shared__ double ar[16][17], ai[16][17], br[16][17], bi[16][17], pc[16], ps[16];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int n = blockIdx.y * 16 + ty, m = blockIdx.x * 16 + tx;
+  double accr = 0.0, acci = 0.0;
+  for (int j0 = 0; j0 < J; j0 += 16) {
+    {
+      const int rn = blockIdx.y * 16 + ty, rm = blockIdx.x * 16 + ty, jj = j0 + tx;
+      ar[ty][tx] = (rn < N && jj < J) ? vr[(size_t)rn * J + jj] : 0.0;
+      ai[ty][tx] = (vi != nullptr && rn < N && jj < J) ? vi[(size_t)rn * J + jj] : 0.0;
+      br[ty][tx] = (rm < N && jj < J) ? vr[(size_t)rm * J + jj] : 0.0;
+      bi[ty][tx] = (vi != nullptr && rm < N && jj < J) ? vi[(size_t)rm * J + jj] : 0.0;
+      if (ty == 0) {
+        pc[tx] = jj < J ? cph[jj] : 0.0;
+        ps[tx] = jj < J ? sph[jj] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      // p = (ar + i ai)(br - i bi)
+      const double pr = ar[ty][jj] * br[tx][jj] + ai[ty][jj] * bi[tx][jj];
+      const double pi = ai[ty][jj] * br[tx][jj] - ar[ty][jj] * bi[tx][jj];
+      accr += pc[jj] * pr - ps[jj] * pi;
+      acci += pc[jj] * pi + ps[jj] * pr;
+    }
+    __syncthreads();
+  }
+  if (n < N && m < N) U[(size_t)n * N + m] = make_double2(wgt * accr, wgt * acci);
+}
+
+// B_fwd[m][n] = U[n][m], B_adj[m][n] = conj(U[m][n]) in the amplitude precision.
+template <class R>
+__global__ void k_store_operands(const double2* __restrict__ U, int64_t N, typename Cx<R>::T* __restrict__ bf,
+                                 typename Cx<R>::T* __restrict__ ba) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / N, n = e - m * N;
+    const double2 ut = U[n * N + m];
+    const double2 u = U[e];
+    bf[e] = mk<R>((R)ut.x, (R)ut.y);
+    ba[e] = mk<R>((R)u.x, (R)(-u.y));
+  }
+}
+
+// ------------------------------------------------------------------------------ smem sizing
+
+template <class R>
+int clock_block_width(int n_c, int64_t N, bool full, size_t* smem) {
+  const size_t sz = sizeof(typename Cx<R>::T);
+  const size_t L = (size_t)1 << n_c;
+  int W = 8;
+  while (W > 1 && (W > N || L / 2 * sz + (full ? 2 : 1) * (size_t)W * L * sz > 200 * 1024)) W >>= 1;
+  const size_t need = L / 2 * sz + (full ? 2 : 1) * (size_t)W * L * sz;
+  if (need > 200 * 1024) return 0;
+  *smem = need;
+  return W;
+}
+
+template <class R>
+hhl_status clock_block_impl(const Plan& p, void* state, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  size_t smem = 0;
+  const int W = clock_block_width<R>(p.n_c, p.N, p.full != 0, &smem);
+  if (W == 0) return fail(HHL_ERR_UNSUPPORTED, "clock register too large for one shared-memory block");
+  const int grid = (int)(p.N / W);
+  if (p.full) {
+    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HHL_PROF_BEGIN(st);
+    k_clock_block<R, true><<<grid, 512, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
+  } else {
+    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HHL_PROF_BEGIN(st);
+    k_clock_block<R, false><<<grid, 512, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
+  }
+  HHL_LAUNCH_CHECK("k_clock_block");
+  return HHL_OK;
+}
+
+template <class R>
+hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  const size_t sz = sizeof(T);
+  const size_t L = (size_t)1 << m;
+  const int64_t inner = 1LL << lo;
+  int W = 8;
+  while (W > 1 && (W > inner || L / 2 * sz + (size_t)W * L * sz > 200 * 1024)) W >>= 1;
+  const size_t smem = L / 2 * sz + (size_t)W * L * sz;
+  if (smem > 200 * 1024) return fail(HHL_ERR_UNSUPPORTED, "register too large for one shared-memory block");
+  const int64_t cols = (1LL << (n - m)) / W;
+  if (cols > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_register_transform<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_PROF_BEGIN(st);
+  k_register_transform<R><<<(int)cols, 512, smem, st>>>((T*)state, lo, m, W, mode);
+  HHL_LAUNCH_CHECK("k_register_transform");
+  return HHL_OK;
+}
+
+}  // namespace
+
+// ================================================================================ launchers
+
+hhl_status launch_bnorm(const double* b, int64_t N, double* acc, cudaStream_t st) {
+  HHL_PROF_BEGIN(st);
+  k_bnorm<<<grid_for(N, kThreads, 152), kThreads, 0, st>>>((const double2*)b, N, acc);
+  HHL_LAUNCH_CHECK("k_bnorm");
+  return HHL_OK;
+}
+
+hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStream_t st) {
+  const int64_t total = 2 * p.R * p.N;
+  const int g = grid_for(total, kThreads, 152 * 32);
+  if (p.prec == HHL_PREC_C64) {
+    HHL_PROF_BEGIN(st);
+    k_prep_fill<float><<<g, kThreads, 0, st>>>((const double2*)b, p.d_scal, (float2*)state, p.n_s, p.n_c);
+  } else {
+    HHL_PROF_BEGIN(st);
+    k_prep_fill<double><<<g, kThreads, 0, st>>>((const double2*)b, p.d_scal, (double2*)state, p.n_s, p.n_c);
+  }
+  HHL_LAUNCH_CHECK("k_prep_fill");
+  return HHL_OK;
+}
+
+hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
+  const int64_t m_sub = p.R / 2;
+  const int64_t N = p.N;
+  const size_t mat = (size_t)N * N;
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((m_sub + 63) / 64));
+  const int sg = grid_for(m_sub * N, kThreads, 152 * 32);
+  if (p.prec == HHL_PREC_C64) {
+    const float2* B = (const float2*)(adjoint ? p.d_badj : p.d_bfwd) + (size_t)k * mat;
+    HHL_PROF_BEGIN(st);
+    k_ctrl_gemm_simt<float, 64, 64, 16><<<grid, 256, 0, st>>>((const float2*)half, (float2*)p.d_scratch, B, p.n_s, k, m_sub);
+    HHL_LAUNCH_CHECK("k_ctrl_gemm_simt<f32>");
+    HHL_PROF_BEGIN(st);
+    k_rows_scatter<float><<<sg, kThreads, 0, st>>>((float2*)half, (const float2*)p.d_scratch, p.n_s, k, m_sub);
+  } else {
+    const double2* B = (const double2*)(adjoint ? p.d_badj : p.d_bfwd) + (size_t)k * mat;
+    HHL_PROF_BEGIN(st);
+    k_ctrl_gemm_simt<double, 64, 64, 8><<<grid, 256, 0, st>>>((const double2*)half, (double2*)p.d_scratch, B, p.n_s, k, m_sub);
+    HHL_LAUNCH_CHECK("k_ctrl_gemm_simt<f64>");
+    HHL_PROF_BEGIN(st);
+    k_rows_scatter<double><<<sg, kThreads, 0, st>>>((double2*)half, (const double2*)p.d_scratch, p.n_s, k, m_sub);
+  }
+  HHL_LAUNCH_CHECK("k_rows_scatter");
+  return HHL_OK;
+}
+
+hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
+  return p.prec == HHL_PREC_C64 ? clock_block_impl<float>(p, state, st) : clock_block_impl<double>(p, state, st);
+}
+
+hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
+  // Hadamards on bits [n_s, n_s + n_c): on the anc = 1 half, or on the whole state (full).
+  const int64_t half_amps = p.R * p.N;
+  void* base = p.full ? state : (void*)((char*)state + half_amps * p.amp_bytes());
+  const int n = p.full ? p.n : p.n - 1;
+  return p.prec == HHL_PREC_C64 ? register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st)
+                                : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
+}
+
+hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st) {
+  const int mode = inverse ? 1 : 0;
+  return prec == HHL_PREC_C64 ? register_transform_impl<float>(state, n, lo, m, mode, st)
+                              : register_transform_impl<double>(state, n, lo, m, mode, st);
+}
+
+hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st) {
+  const int64_t half = p.R * p.N;
+  HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal + 1, 0, 3 * sizeof(double), st));
+  const int g = grid_for(2 * half, kThreads, 152 * 8);
+  const int gf = grid_for(p.N, kThreads, 152 * 4);
+  if (p.prec == HHL_PREC_C64) {
+    HHL_PROF_BEGIN(st);
+    k_measure_sums<float><<<g, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal + 1);
+    HHL_LAUNCH_CHECK("k_measure_sums");
+    HHL_PROF_BEGIN(st);
+    k_measure_finish<float><<<gf, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal, out);
+  } else {
+    HHL_PROF_BEGIN(st);
+    k_measure_sums<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
+    HHL_LAUNCH_CHECK("k_measure_sums");
+    HHL_PROF_BEGIN(st);
+    k_measure_finish<double><<<gf, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, out);
+  }
+  HHL_LAUNCH_CHECK("k_measure_finish");
+  return HHL_OK;
+}
+
+hhl_status launch_dissipation(const Plan& p, const void* state, double* eps, double* u_dev, cudaStream_t st) {
+  const int64_t half = p.R * p.N;
+  HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal + 4, 0, sizeof(double), st));
+  const int g = grid_for(p.N + 1, kThreads, 152 * 4);
+  const double inv_c_lam = 1.0 / (p.C * p.lam_ub);
+  if (p.prec == HHL_PREC_C64) {
+    HHL_PROF_BEGIN(st);
+    k_diss_sum<float><<<g, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal, inv_c_lam, p.wall_lo,
+                                              p.wall_hi, p.d_scal + 4, u_dev);
+  } else {
+    HHL_PROF_BEGIN(st);
+    k_diss_sum<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, inv_c_lam, p.wall_lo,
+                                               p.wall_hi, p.d_scal + 4, u_dev);
+  }
+  HHL_LAUNCH_CHECK("k_diss_sum");
+  HHL_PROF_BEGIN(st);
+  k_diss_finish<<<1, 32, 0, st>>>(p.d_scal + 4, p.nu * (double)(p.N + 1), eps);
+  HHL_LAUNCH_CHECK("k_diss_finish");
+  return HHL_OK;
+}
+
+hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_vi, const double* d_cos,
+                             const double* d_sin, double wgt, double2* d_u, cudaStream_t st) {
+  dim3 grid((unsigned)((N + 15) / 16), (unsigned)((N + 15) / 16));
+  HHL_PROF_BEGIN(st);
+  k_expm_eigen<<<grid, 256, 0, st>>>(N, J, d_vr, d_vi, d_cos, d_sin, wgt, d_u);
+  HHL_LAUNCH_CHECK("k_expm_eigen");
+  return HHL_OK;
+}
+
+hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st) {
+  const size_t mat = (size_t)p.N * p.N;
+  const int g = grid_for((int64_t)mat, kThreads, 152 * 16);
+  if (p.prec == HHL_PREC_C64) {
+    HHL_PROF_BEGIN(st);
+    k_store_operands<float><<<g, kThreads, 0, st>>>(d_u, p.N, (float2*)p.d_bfwd + k * mat, (float2*)p.d_badj + k * mat);
+  } else {
+    HHL_PROF_BEGIN(st);
+    k_store_operands<double><<<g, kThreads, 0, st>>>(d_u, p.N, (double2*)p.d_bfwd + k * mat, (double2*)p.d_badj + k * mat);
+  }
+  HHL_LAUNCH_CHECK("k_store_operands");
+  return HHL_OK;
+}
+
+}  // namespace hhl

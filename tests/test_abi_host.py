@@ -1,0 +1,153 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every entry
+point include/hhl.h declares, and rejects invalid requests with status codes before any
+CUDA call is made."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_00391_gb300 import build
+    build.build()
+    from paper_2307_00391_gb300 import _ffi
+    return _ffi.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hhl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hhl_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2307_00391_gb300 import _ffi
+    syms = declared_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(lib, s), s
+    bound = {name for name, _, _ in _ffi.SIGNATURES}
+    assert set(syms) == bound, set(syms) ^ bound
+
+
+def test_version_status_strings_and_defaults(lib):
+    from paper_2307_00391_gb300 import _ffi
+    assert lib.hhl_api_version() == 1
+    for code in range(9):
+        assert lib.hhl_status_string(code)
+    p = _ffi.Params()
+    lib.hhl_params_default(ctypes.byref(p))
+    assert (p.n_clock, p.t0_rule, p.precision, p.expm_mode, p.full_uncompute) == (6, 2, 32, 0, 0)
+
+
+def _plan(lib, prob, par):
+    h = ctypes.c_void_p()
+    st = lib.hhl_plan_create(ctypes.byref(prob), ctypes.byref(par), ctypes.byref(h))
+    return st, lib.hhl_last_error().decode()
+
+
+def _tridiag(n_s, diag=None, off=None):
+    from paper_2307_00391_gb300 import _ffi
+    n = 1 << n_s
+    d = np.full(n, 2.0) if diag is None else diag
+    o = np.full(n - 1, -1.0) if off is None else off
+    prob = _ffi.Problem()
+    prob.kind = _ffi.MATRIX_TRIDIAG
+    prob.n_sys_qubits = n_s
+    prob.diag = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    prob.off = o.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return prob, (d, o)
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    from paper_2307_00391_gb300 import _ffi
+    par = _ffi.Params()
+    lib.hhl_params_default(ctypes.byref(par))
+    prob, keep = _tridiag(4)
+    h = ctypes.c_void_p()
+    assert lib.hhl_plan_create(None, ctypes.byref(par), ctypes.byref(h)) == 1
+    for field, value in (("n_clock", 0), ("n_clock", 14), ("precision", 16), ("expm_mode", 7),
+                         ("t0_rule", 9), ("gemm_impl", 5)):
+        bad = _ffi.Params.from_buffer_copy(par)
+        setattr(bad, field, value)
+        st, msg = _plan(lib, prob, bad)
+        assert st == 1, (field, st, msg)
+        assert msg
+    user = _ffi.Params.from_buffer_copy(par)
+    user.t0_rule = _ffi.T0_USER
+    user.t0 = -1.0
+    assert _plan(lib, prob, user)[0] == 1
+    big, keep2 = _tridiag(13)
+    assert _plan(lib, big, par)[0] == 1          # dense mode limited to 12 system qubits
+    nan_prob, keep3 = _tridiag(3, diag=np.array([2.0, np.nan, 2, 2, 2, 2, 2, 2]))
+    assert _plan(lib, nan_prob, par)[0] == 7
+    tc = _ffi.Params.from_buffer_copy(par)
+    tc.gemm_impl = _ffi.GEMM_TCGEN05
+    tc.precision = _ffi.PREC_C128
+    assert _plan(lib, prob, tc)[0] == 8
+
+
+def test_matrix_property_errors(lib):
+    from paper_2307_00391_gb300 import _ffi
+    par = _ffi.Params()
+    lib.hhl_params_default(ctypes.byref(par))
+    # singular: [[1, 1], [1, 1]] as a tridiagonal 2 x 2
+    sing, k1 = _tridiag(1, diag=np.array([1.0, 1.0]), off=np.array([1.0]))
+    assert _plan(lib, sing, par)[0] == 3
+    zero, k2 = _tridiag(2, diag=np.zeros(4), off=np.zeros(3))
+    assert _plan(lib, zero, par)[0] == 3
+    # indefinite: diag (1, -1)
+    indef, k3 = _tridiag(1, diag=np.array([1.0, -1.0]), off=np.array([0.0]))
+    assert _plan(lib, indef, par)[0] == 8
+    # dense, not Hermitian
+    a = np.array([[2.0, 1.0], [0.5, 2.0]])
+    prob = _ffi.Problem()
+    prob.kind = _ffi.MATRIX_DENSE
+    prob.n_sys_qubits = 1
+    prob.dense_re = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert _plan(lib, prob, par)[0] == 2
+    # Trotter mode needs a Toeplitz tridiagonal
+    tro = _ffi.Params.from_buffer_copy(par)
+    tro.expm_mode = _ffi.EXPM_TROTTER
+    nt, k4 = _tridiag(3, diag=np.arange(1.0, 9.0) + 4, off=np.full(7, -1.0))
+    assert _plan(lib, nt, tro)[0] == 8
+
+
+def test_null_handles_and_qft_arguments(lib):
+    assert lib.hhl_apply_circuit(None, None, None) == 1
+    assert lib.hhl_measure(None, None, None, None, None) == 1
+    assert lib.hhl_dissipation(None, None, None, None, None) == 1
+    assert lib.hhl_prepare_rhs(None, None, None, None) == 1
+    assert lib.hhl_apply_qft(None, 10, 0, 4, 0, 32, None) == 1
+    buf = ctypes.c_void_p(1)
+    assert lib.hhl_apply_qft(buf, 10, 8, 4, 0, 32, None) == 1   # lo + m > n
+    assert lib.hhl_apply_qft(buf, 40, 0, 4, 0, 32, None) == 1
+    assert lib.hhl_apply_qft(buf, 20, 0, 14, 0, 32, None) == 1
+    assert lib.hhl_apply_qft(buf, 20, 0, 4, 0, 33, None) == 1
+    assert lib.hhl_state_bytes(None) == 0
+
+
+def test_host_fault_injection_plan():
+    """HHL_FAULT=plan makes hhl_plan_create fail after validation, on the host."""
+    code = (
+        "import ctypes, numpy as np\n"
+        "from paper_2307_00391_gb300 import _ffi\n"
+        "lib = _ffi.load()\n"
+        "p = _ffi.Params(); lib.hhl_params_default(ctypes.byref(p))\n"
+        "d = np.full(4, 2.0); o = np.full(3, -1.0)\n"
+        "pr = _ffi.Problem(); pr.kind = 0; pr.n_sys_qubits = 2\n"
+        "pr.diag = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))\n"
+        "pr.off = o.ctypes.data_as(ctypes.POINTER(ctypes.c_double))\n"
+        "h = ctypes.c_void_p()\n"
+        "print(lib.hhl_plan_create(ctypes.byref(pr), ctypes.byref(p), ctypes.byref(h)), lib.hhl_last_error().decode())\n")
+    env = dict(os.environ, HHL_FAULT="plan", PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("1 injected planner failure"), out.stdout

@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (max absolute amplitude error): 1e-10 for complex128, 1e-5 for complex64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hhl_oracle as o
+from tests.oracle_stages import problem, run_stages
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def hhl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2307_00391_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def _oracle_plan(diag, off, n_c, rule="range_fill", t0=None, conv="total", C=None):
+    a = o.dense_from_tridiag(diag, off)
+    return o.plan(a, n_c, t0_rule=rule, t0=t0, t0_convention=conv, c_const=C)
+
+
+def _gpu_plan(hhl, diag, off, n_s, n_c, prec, **kw):
+    return hhl.HHLPlan(n_s, n_c, diag=diag, off=off, precision=prec, **kw)
+
+
+def _b_dev(b):
+    import torch
+    return torch.tensor(np.asarray(b, dtype=np.complex128), device="cuda")
+
+
+def _half(psi, n_s, n_c, anc):
+    return psi.reshape(2, 1 << n_c, 1 << n_s)[anc]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("full", [False, True])
+@pytest.mark.parametrize("flow,n_s,n_c,rule", [("poiseuille", 4, 6, "power_law"),   # the 11-qubit Poiseuille case
+                                               ("couette", 7, 8, "range_fill"),
+                                               ("poiseuille", 5, 3, "range_fill")])
+def test_stagewise_parity(hhl, prec, full, flow, n_s, n_c, rule):
+    import torch
+    diag, off, b, walls = problem(flow, n_s)
+    pl = _oracle_plan(diag, off, n_c, rule)
+    ref = run_stages(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, t0_rule=rule, full_uncompute=full, gemm="simt")
+    assert plan.info["t0"] == pytest.approx(pl["t0"], rel=1e-12)
+    st = plan.new_state()
+    plan.prepare_rhs(_b_dev(b), st)
+    tol = TOL[prec]
+    np.testing.assert_allclose(_np(st), ref["prep"], atol=tol)
+    plan.apply_stage("qpe_u", st)
+    np.testing.assert_allclose(_np(st), ref["qpe_u"], atol=tol)
+    plan.apply_stage("clock_block", st)
+    got = _np(st)
+    np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["clock_block"], n_s, n_c, 1), atol=tol)
+    anc0_ref = ref["clock_block"] if full else ref["rotated"]
+    np.testing.assert_allclose(_half(got, n_s, n_c, 0), _half(anc0_ref, n_s, n_c, 0), atol=tol)
+    plan.apply_stage("uncompute_u", st)
+    got = _np(st)
+    np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["uncompute_u"], n_s, n_c, 1), atol=tol)
+    if full:
+        np.testing.assert_allclose(got, ref["uncompute_u"], atol=tol)
+    plan.apply_stage("final_h", st)
+    got = _np(st)
+    np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["final_h"], n_s, n_c, 1), atol=tol)
+    if full:
+        np.testing.assert_allclose(got, ref["final_h"], atol=tol)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("flow", ["poiseuille", "couette"])
+def test_measure_and_dissipation_parity(hhl, prec, flow):
+    n_s, n_c = 6, 7
+    diag, off, b, walls = problem(flow, n_s)
+    nu = 0.05
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    psi = o.hhl_circuit(b, n_s, pl)
+    ref = o.postselect(psi, n_s, n_c)
+    u_ref = o.velocity(ref["v"], np.linalg.norm(b), pl["C"], pl["lam_ub"])
+    eps_ref = o.dissipation(u_ref, walls[0], walls[1], nu)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, nu=nu, walls=walls)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    m = plan.measure(st)
+    tol = TOL[prec]
+    assert m["p_success"] == pytest.approx(ref["p_success"], rel=1e-9 if prec == "c128" else 1e-4)
+    assert m["p_anc1"] == pytest.approx(ref["p_anc1"], rel=1e-9 if prec == "c128" else 1e-4)
+    assert m["b_norm"] == pytest.approx(np.linalg.norm(b), rel=1e-14)
+    # norm of the whole buffer: 1 (the early mode keeps the rotated anc = 0 half)
+    assert m["norm"] == pytest.approx(1.0, abs=1e-12 if prec == "c128" else 1e-5)
+    np.testing.assert_allclose(m["xhat"], ref["xhat"], atol=10 * tol)
+    eps, u = plan.dissipation(st, want_u=True)
+    np.testing.assert_allclose(u, u_ref, rtol=1e-9 if prec == "c128" else 2e-4,
+                               atol=1e-12 * np.abs(u_ref).max())
+    assert eps == pytest.approx(eps_ref, rel=1e-9 if prec == "c128" else 1e-3)
+
+
+def test_complex_rhs_and_user_t0_per_unit(hhl):
+    n_s, n_c = 5, 6
+    diag, off = o.laplacian_tridiag(32)
+    rng = np.random.default_rng(17)
+    b = rng.random(32) + 1j * rng.standard_normal(32)
+    pl = _oracle_plan(diag, off, n_c, "user", t0=1.7, conv="per_unit", C=0.05)
+    ref = o.hhl_circuit(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c128", t0_rule="user", t0=1.7, t0_convention="per_unit", C=0.05)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b.real.copy(), st, b_im=b.imag.copy())
+    plan.apply_circuit(st)
+    np.testing.assert_allclose(_half(_np(st), n_s, n_c, 1), _half(ref, n_s, n_c, 1), atol=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_dense_complex_hermitian(hhl, prec):
+    n_s, n_c = 3, 5
+    rng = np.random.default_rng(23)
+    q = np.linalg.qr(rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8)))[0]
+    a = q @ np.diag(rng.uniform(1.0, 9.0, 8)) @ q.conj().T
+    a = 0.5 * (a + a.conj().T)
+    b = rng.random(8)
+    pl = o.plan(a, n_c, t0_rule="range_fill")
+    ref = o.hhl_circuit(b, n_s, pl)
+    plan = hhl.HHLPlan(n_s, n_c, dense=a, precision=prec, full_uncompute=True)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    np.testing.assert_allclose(_np(st), ref, atol=TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_dense_real_general_tridiagonal(hhl, prec):
+    n_s, n_c = 4, 5
+    rng = np.random.default_rng(5)
+    diag = 4.0 + rng.random(16)
+    off = -rng.random(15)
+    b = rng.random(16)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    ref = o.hhl_circuit(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, full_uncompute=True)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    np.testing.assert_allclose(_np(st), ref, atol=TOL[prec])
+
+
+def test_smallest_registers(hhl):
+    """n_s = 1, n_c = 1: one system qubit, one clock qubit."""
+    diag, off = np.array([3.0, 3.0]), np.array([-1.0])
+    b = np.array([0.3, 0.8])
+    pl = _oracle_plan(diag, off, 1, "range_fill")
+    ref = o.hhl_circuit(b, 1, pl)
+    plan = _gpu_plan(hhl, diag, off, 1, 1, "c128", full_uncompute=True)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    np.testing.assert_allclose(_np(st), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,lo,m", [(6, 0, 6), (10, 3, 5), (12, 0, 7), (14, 4, 10), (16, 2, 13), (9, 8, 1)])
+def test_qft_register_blocks(hhl, prec, n, lo, m):
+    import torch
+    from synth_inputs import random_state
+    psi = random_state(n, seed_offset=n * 100 + lo)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    for inverse in (False, True):
+        st = torch.tensor(psi, dtype=dt, device="cuda")
+        hhl.apply_qft(st, n, lo, m, inverse)
+        ref = o.qft_register(psi, n, lo, m, inverse)
+        np.testing.assert_allclose(_np(st), ref, atol=TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("dt,r_max", [(3.0, 0), (0.5, 40), (50.0, 7)])
+def test_trotter_parity(hhl, prec, dt, r_max):
+    """Controlled Strang products (several passes, odd and even pass counts) against the
+    oracle's gate-by-gate Trotter circuit."""
+    n_s, n_c = 5, 4
+    diag, off, b, walls = problem("poiseuille", n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    lub = pl["lam_ub"]
+    tro = dict(diag=diag / lub, off=off / lub, dt=dt, r_max=r_max)
+    ref = run_stages(b, n_s, pl, trotter=tro)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, expm="trotter", trotter_dt=dt, trotter_steps_max=r_max,
+                     full_uncompute=True)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_stage("qpe_u", st)
+    tol = TOL[prec] * (4 if prec == "c64" else 1)
+    np.testing.assert_allclose(_np(st), ref["qpe_u"], atol=tol)
+    for stage in ("clock_block", "uncompute_u", "final_h"):
+        plan.apply_stage(stage, st)
+    np.testing.assert_allclose(_np(st), ref["final_h"], atol=tol)
+
+
+def test_trotter_large_row_spans_many_tiles(hhl):
+    """A 2^13-point system row spans 4 shared-memory tiles with halos; checked against the
+    oracle's dense Strang product on the controlled rows."""
+    import torch
+    n_s, n_c = 13, 2
+    n = n_s + n_c + 1
+    diag, off = o.laplacian_tridiag(1 << n_s)
+    lub = 4.0 * ((1 << n_s) + 1) ** 2      # Gershgorin bound of tridiag(-1, 2, -1)/h^2
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c128", expm="trotter", trotter_dt=0.25, trotter_steps_max=0,
+                     t0_rule="user", t0=8.0)
+    from synth_inputs import random_state
+    psi = random_state(n, seed_offset=77)
+    st = torch.tensor(psi, device="cuda")
+    plan.apply_stage("qpe_u", st)
+    ref = psi.copy()
+    t_k = [8.0 * (1 << k) / 4 for k in range(n_c)]
+    for k in range(n_c):
+        r = o.trotter_steps(t_k[k], 0.25, 0)
+        o.apply_trotter_controlled(ref, n, n_s, n_s + k, diag / lub, off / lub, t_k[k], r)
+    np.testing.assert_allclose(_np(st), ref, atol=1e-10)
+
+
+def test_apply_circuit_equals_stages_and_counts_launches(hhl):
+    n_s, n_c = 4, 6
+    diag, off, b, walls = problem("poiseuille", n_s)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64")
+    s1, s2 = plan.new_state(), plan.new_state()
+    plan.prepare_rhs_host(b, s1)
+    plan.prepare_rhs_host(b, s2)
+    before = hhl.kernel_launch_count()
+    plan.apply_circuit(s1)
+    launched = hhl.kernel_launch_count() - before
+    assert launched >= 2 * n_c + 2
+    for stage in ("qpe_u", "clock_block", "uncompute_u", "final_h"):
+        plan.apply_stage(stage, s2)
+    np.testing.assert_array_equal(_np(s1), _np(s2))
+
+
+def test_invalid_state_calls_return_status(hhl):
+    diag, off, b, walls = problem("poiseuille", 3)
+    plan = _gpu_plan(hhl, diag, off, 3, 3, "c64")
+    st = plan.new_state()
+    plan.prepare_rhs_host(np.zeros(8), st)
+    plan.apply_circuit(st)
+    with pytest.raises(hhl.HHLError) as e:
+        plan.measure(st)
+    assert e.value.status == 3
+    import ctypes
+    assert plan._lib.hhl_apply_stage(plan._h, 9, ctypes.c_void_p(st.data_ptr()), None) == 1
+
+
+# ----------------------------------------------------------------------------- full size
+
+
+@pytest.fixture(scope="module")
+def couette_1024_oracle():
+    """The 23-qubit Couette workload (N = 1024, n_c = 12) through the FP64 oracle (~30 s)."""
+    diag, off, b, walls = problem("couette", 10)
+    pl = _oracle_plan(diag, off, 12, "range_fill")
+    psi = o.hhl_circuit(b, 10, pl)
+    return dict(psi=psi, pl=pl, b=b, diag=diag, off=off, walls=walls, post=o.postselect(psi, 10, 12))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_couette_1024_full_size_parity(hhl, couette_1024_oracle, prec):
+    ref = couette_1024_oracle
+    plan = _gpu_plan(hhl, ref["diag"], ref["off"], 10, 12, prec, walls=ref["walls"])
+    st = plan.new_state()
+    plan.prepare_rhs_host(ref["b"], st)
+    plan.apply_circuit(st)
+    got = _np(st)
+    np.testing.assert_allclose(_half(got, 10, 12, 1), _half(ref["psi"], 10, 12, 1), atol=TOL[prec])
+    m = plan.measure(st)
+    np.testing.assert_allclose(m["xhat"], ref["post"]["xhat"], atol=10 * TOL[prec])
+    assert m["p_success"] == pytest.approx(ref["post"]["p_success"], rel=1e-8 if prec == "c128" else 1e-4)
+
+
+@pytest.mark.slow
+def test_couette_1024_c64_fidelity_against_c128(hhl, couette_1024_oracle):
+    """Fidelity of the complex64 postselected solution against the complex128 one."""
+    ref = couette_1024_oracle
+    xs = {}
+    for prec in ("c128", "c64"):
+        plan = _gpu_plan(hhl, ref["diag"], ref["off"], 10, 12, prec)
+        st = plan.new_state()
+        plan.prepare_rhs_host(ref["b"], st)
+        plan.apply_circuit(st)
+        xs[prec] = plan.measure(st)["xhat"]
+    f = abs(np.vdot(xs["c128"], xs["c64"]))
+    assert f >= 1 - 1e-6

@@ -407,3 +407,16 @@ def test_trotter_gate_sequence_matches_dense_product():
     np.testing.assert_allclose(got, ref, atol=1e-13)
     assert o.trotter_steps(10.0, 3.0, 0) == 4
     assert o.trotter_steps(10.0, 3.0, 2) == 2
+
+
+def test_stage_cuts_reproduce_whole_circuit():
+    from tests.oracle_stages import run_stages
+    diag, off = o.laplacian_tridiag(16)
+    pl = o.plan(o.dense_from_tridiag(diag, off), 5, t0_rule="power_law")
+    b = np.random.default_rng(2).random(16)
+    st = run_stages(b, 4, pl)
+    np.testing.assert_allclose(st["final_h"], o.hhl_circuit(b, 4, pl), atol=1e-13)
+    tro = dict(diag=diag / o.gershgorin_bound(o.dense_from_tridiag(diag, off)),
+               off=off / o.gershgorin_bound(o.dense_from_tridiag(diag, off)), dt=2.0, r_max=5)
+    st2 = run_stages(b, 4, pl, trotter=tro)
+    np.testing.assert_allclose(st2["final_h"], o.hhl_circuit(b, 4, pl, trotter=tro), atol=1e-13)
