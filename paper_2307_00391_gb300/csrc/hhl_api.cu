@@ -703,7 +703,10 @@ hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* 
   double sc[4];
   HHL_CUDA_TRY(cudaMemcpyAsync(sc, plan->d_meas, sizeof(sc), cudaMemcpyDeviceToHost, st));
   if (x_host) HHL_CUDA_TRY(cudaMemcpyAsync(x_host, (double*)plan->d_meas + 4, 2 * p.N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int tc_err = 0;
+  if (int* ef = hhl::tc_error_flag(p)) HHL_CUDA_TRY(cudaMemcpyAsync(&tc_err, ef, sizeof(int), cudaMemcpyDeviceToHost, st));
   HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  if (tc_err != 0) return fail(HHL_ERR_TIMEOUT, "a bounded wait in the tcgen05 GEMM ran out (stage " + std::to_string(tc_err) + ")");
   out->p_success = sc[0];
   out->p_anc1 = sc[1];
   out->norm = sc[2];

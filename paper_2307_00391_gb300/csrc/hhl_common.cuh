@@ -115,5 +115,6 @@ bool tc_supported(const Plan& p);
 hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t st);
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
 void tc_free(Plan& p);
+int* tc_error_flag(const Plan& p);  // device flag set when a bounded wait in the GEMM ran out
 
 }  // namespace hhl

@@ -1,15 +1,397 @@
-// tcgen05 controlled-U GEMM (complex64, split-TF32 on the 5th-generation tensor cores).
+// Controlled-U_k GEMM on the 5th-generation tensor cores (tcgen05, sm_103a), complex64.
+//
+// The controlled U_k multiplies every system-register row r (length N, complex) whose
+// clock bit k is set: r <- U_k r. In real arithmetic on interleaved (re, im) floats this is
+// one real GEMM  Y (M x 2N) = X (M x 2N) * E^T, with M = 2^(n_c-1) rows and the real
+// embedding E (2N x 2N):  E[2n][2m] = Re U[n][m], E[2n][2m+1] = -Im U[n][m],
+// E[2n+1][2m] = Im U[n][m], E[2n+1][2m+1] = Re U[n][m]. Its flops equal the complex GEMM's
+// 8 M N N.
+//
+// FP32 accuracy from TF32 tensor cores (split TF32): every operand is split as
+// v = hi + lo with hi = v truncated to TF32 and lo = v - hi, and the product is
+// X_hi E_hi + X_hi E_lo + X_lo E_hi, accumulated in FP32 in tensor memory (three
+// kind::tf32 MMAs per K step). The plan stores E_hi and E_lo (forward and adjoint) for
+// every k; a gather kernel copies the rows with bit k set into compact X_hi / X_lo arrays,
+// so the GEMM may write its result straight back into those state rows.
+//
+// Kernel: one CTA of 128 threads per 128 x 256 output tile. Warp 0 (one lane) issues TMA
+// loads (128-byte swizzle) into a 2-stage shared-memory ring, warp 1 (one lane) issues the
+// MMAs (M = 128, N = 256, K = 8) into a 256-column TMEM accumulator, and all four warps
+// drain TMEM with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. output rows) and
+// store the rows. Every mbarrier wait is bounded; on expiry the CTA records an error flag
+// (read back as HHL_ERR_TIMEOUT), skips the remaining work, frees its TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "hhl_common.cuh"
 
 namespace hhl {
 
-bool tc_supported(const Plan&) { return false; }
-hhl_status tc_prepare_operands(Plan&, const double2*, int, cudaStream_t) {
-  return fail(HHL_ERR_UNSUPPORTED, "tcgen05 GEMM not built");
+namespace {
+
+constexpr int kBM = 128;           // output rows per CTA (MMA M)
+constexpr int kBN = 256;           // output real columns per CTA (MMA N)
+constexpr int kBK = 32;            // fp32 K elements per stage (128 bytes: one swizzle row)
+constexpr int kStages = 2;
+constexpr int kTileA = kBM * kBK * 4;   // 16 KiB
+constexpr int kTileB = kBN * kBK * 4;   // 32 KiB
+constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+constexpr int kTmemCols = 256;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcState {
+  float* a_hi = nullptr;  // M_sub x 2N
+  float* a_lo = nullptr;
+  float* b = nullptr;     // n_c x {fwd_hi, fwd_lo, adj_hi, adj_lo} x (2N x 2N)
+  int* err = nullptr;     // device error flag
+  std::vector<CUtensorMap> maps;  // [0] A_hi, [1] A_lo, then per k: fwd_hi, fwd_lo, adj_hi, adj_lo
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-hhl_status launch_ctrl_u_tc(const Plan&, void*, int, bool, cudaStream_t) {
-  return fail(HHL_ERR_UNSUPPORTED, "tcgen05 GEMM not built");
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-void tc_free(Plan&) {}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false (and the error flag set) after
+// about two seconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err, int code) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int64_t row_with_bit_tc(int64_t i, int k) {
+  return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
+                   const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
+                   float* __restrict__ state_half, int n_s, int k, int k_iters, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int n0 = blockIdx.x * kBN;   // real output column
+  const int m0 = blockIdx.y * kBM;   // subset row
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads of the four operand tiles of each K step
+    for (int it = 0; it < k_iters; ++it) {
+      const int s = it % kStages;
+      if (!mbar_wait_bounded(&empty_bar[s], ((it / kStages) & 1) ^ 1, err, 1)) {
+        abort_flag = 1;
+        break;
+      }
+      const uint32_t st = base + s * kStageBytes;
+      mbar_expect_tx(&full_bar[s], kStageBytes);
+      const int kx = it * kBK;
+      tma_load_2d(st, &map_ahi, &full_bar[s], kx, m0);
+      tma_load_2d(st + kTileA, &map_alo, &full_bar[s], kx, m0);
+      tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
+      tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_tf32(kBM, kBN);
+    bool ok = true;
+    for (int it = 0; it < k_iters; ++it) {
+      const int s = it % kStages;
+      if (!mbar_wait_bounded(&full_bar[s], (it / kStages) & 1, err, 2)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + s * kStageBytes;
+      const uint32_t a_hi = st, a_lo = st + kTileA, b_hi = st + 2 * kTileA, b_lo = st + 2 * kTileA + kTileB;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzled row
+        const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
+        mma_tf32(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+        mma_tf32(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+      }
+      mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+    }
+    if (ok) mma_commit(&done_bar);
+    else abort_flag = 1;
+  }
+  __syncwarp();
+
+  // epilogue: all four warps drain their 32 TMEM lanes (= output rows)
+  if (!mbar_wait_bounded(&done_bar, 0, err, 3)) abort_flag = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (abort_flag == 0) {  // uniform across the CTA: tcgen05.ld is warp-collective
+    const int64_t N2 = 2LL << n_s;  // floats per state row
+    const int64_t i = m0 + warp * 32 + lane;
+    float* dst = state_half + row_with_bit_tc(i, k) * N2 + n0;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < kBN; c += 32) {
+      float v[32];
+      tmem_ld_32cols(lane_addr + c, v);
+      float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Rows with clock bit k set -> compact TF32 hi / lo arrays (M_sub x 2N floats).
+__global__ void k_tc_split_rows(const float4* __restrict__ half, float4* __restrict__ a_hi, float4* __restrict__ a_lo,
+                                int n_s, int k, int64_t m_sub) {
+  const int64_t row4 = (2LL << n_s) / 4;  // float4 per row
+  const int64_t total = m_sub * row4;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / row4, c = e - i * row4;
+    const float4 v = half[row_with_bit_tc(i, k) * row4 + c];
+    float4 h;
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    a_hi[e] = h;
+    a_lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  }
+}
+
+// Real embeddings of U_k (forward) and U_k^dagger (adjoint), split into TF32 hi / lo.
+// out layout: [fwd_hi | fwd_lo | adj_hi | adj_lo], each (2N x 2N) row-major with rows =
+// output real column, columns = input real index (K-major B operand).
+__global__ void k_tc_prep_b(const double2* __restrict__ U, int64_t N, float* __restrict__ out) {
+  const int64_t N2 = 2 * N, sz = N2 * N2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nr = e / N2, kr = e - nr * N2;
+    const int64_t n = nr >> 1, m = kr >> 1;
+    const int s = (int)(nr & 1), t = (int)(kr & 1);
+    const double2 uf = U[n * N + m];
+    const double2 ua = U[m * N + n];
+    const double ar = ua.x, ai = -ua.y;  // (U^dagger)[n][m] = conj(U[m][n])
+    const double vf = s == 0 ? (t == 0 ? uf.x : -uf.y) : (t == 0 ? uf.y : uf.x);
+    const double va = s == 0 ? (t == 0 ? ar : -ai) : (t == 0 ? ai : ar);
+    const float ff = (float)vf, fa = (float)va;
+    const float hf = __uint_as_float(__float_as_uint(ff) & 0xFFFFE000u);
+    const float ha = __uint_as_float(__float_as_uint(fa) & 0xFFFFE000u);
+    out[e] = hf;
+    out[sz + e] = (float)(vf - (double)hf);
+    out[2 * sz + e] = ha;
+    out[3 * sz + e] = (float)(va - (double)ha);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+hhl_status make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return fail(HHL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HHL_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return HHL_OK;
+}
+
+}  // namespace
+
+bool tc_supported(const Plan& p) {
+  if (p.prec != HHL_PREC_C64 || p.expm_mode != HHL_EXPM_DENSE) return false;
+  if (p.N < 128 || p.R / 2 < kBM) return false;  // at least one full 128 x 256 tile
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t st) {
+  TcState* t = static_cast<TcState*>(p.d_tc);
+  const int64_t N2 = 2 * p.N;
+  const size_t mat = (size_t)N2 * N2;
+  if (t == nullptr) {
+    t = new TcState();
+    p.d_tc = t;
+    const size_t abytes = (size_t)(p.R / 2) * N2 * sizeof(float);
+    if (cudaMalloc(&t->a_hi, abytes) != cudaSuccess || cudaMalloc(&t->a_lo, abytes) != cudaSuccess ||
+        cudaMalloc(&t->b, (size_t)p.n_c * 4 * mat * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&t->err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HHL_ERR_OOM, "tcgen05 operand allocation failed");
+    }
+    p.workspace_bytes += 2 * abytes;
+    p.table_bytes += (size_t)p.n_c * 4 * mat * sizeof(float);
+    HHL_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), st));
+    t->maps.resize(2 + 4 * (size_t)p.n_c);
+    hhl_status s = make_map(&t->maps[0], t->a_hi, N2, p.R / 2, kBM);
+    if (s == HHL_OK) s = make_map(&t->maps[1], t->a_lo, N2, p.R / 2, kBM);
+    for (int kk = 0; kk < p.n_c && s == HHL_OK; ++kk)
+      for (int j = 0; j < 4 && s == HHL_OK; ++j)
+        s = make_map(&t->maps[2 + 4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, kBN);
+    if (s != HHL_OK) return s;
+    HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  }
+  int g = (int)((mat + 255) / 256);
+  if (g > 152 * 16) g = 152 * 16;
+  HHL_PROF_BEGIN(st);
+  k_tc_prep_b<<<g, 256, 0, st>>>(d_u, p.N, t->b + (size_t)k * 4 * mat);
+  HHL_LAUNCH_CHECK("k_tc_prep_b");
+  return HHL_OK;
+}
+
+hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
+  const TcState* t = static_cast<const TcState*>(p.d_tc);
+  if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
+  const int64_t m_sub = p.R / 2;
+  const int64_t N2 = 2 * p.N;
+  const int64_t total4 = m_sub * N2 / 4;
+  int g = (int)((total4 + 255) / 256);
+  if (g > 152 * 16) g = 152 * 16;
+  HHL_PROF_BEGIN(st);
+  k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (float4*)t->a_hi, (float4*)t->a_lo, p.n_s, k, m_sub);
+  HHL_LAUNCH_CHECK("k_tc_split_rows");
+  const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
+  dim3 grid((unsigned)(N2 / kBN), (unsigned)(m_sub / kBM));
+  HHL_PROF_BEGIN(st);
+  k_ctrl_gemm_tc<<<grid, 128, kSmemBytes, st>>>(t->maps[0], t->maps[1], mb[0], mb[1], (float*)half, p.n_s, k,
+                                                (int)(N2 / kBK), t->err);
+  HHL_LAUNCH_CHECK("k_ctrl_gemm_tc");
+  return HHL_OK;
+}
+
+int* tc_error_flag(const Plan& p) {
+  const TcState* t = static_cast<const TcState*>(p.d_tc);
+  return t ? t->err : nullptr;
+}
+
+void tc_free(Plan& p) {
+  TcState* t = static_cast<TcState*>(p.d_tc);
+  if (t == nullptr) return;
+  if (t->a_hi) cudaFree(t->a_hi);
+  if (t->a_lo) cudaFree(t->a_lo);
+  if (t->b) cudaFree(t->b);
+  if (t->err) cudaFree(t->err);
+  delete t;
+  p.d_tc = nullptr;
+}
 
 }  // namespace hhl

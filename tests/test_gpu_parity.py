@@ -223,10 +223,11 @@ def test_trotter_large_row_spans_many_tiles(hhl):
     st = torch.tensor(psi, device="cuda")
     plan.apply_stage("qpe_u", st)
     ref = psi.copy()
+    anc0 = ref[: 1 << (n - 1)]          # the stage acts on the anc = 0 half only
     t_k = [8.0 * (1 << k) / 4 for k in range(n_c)]
     for k in range(n_c):
         r = o.trotter_steps(t_k[k], 0.25, 0)
-        o.apply_trotter_controlled(ref, n, n_s, n_s + k, diag / lub, off / lub, t_k[k], r)
+        o.apply_trotter_controlled(anc0, n - 1, n_s, n_s + k, diag / lub, off / lub, t_k[k], r)
     np.testing.assert_allclose(_np(st), ref, atol=1e-10)
 
 
@@ -299,3 +300,42 @@ def test_couette_1024_c64_fidelity_against_c128(hhl, couette_1024_oracle):
         xs[prec] = plan.measure(st)["xhat"]
     f = abs(np.vdot(xs["c128"], xs["c64"]))
     assert f >= 1 - 1e-6
+
+
+# ----------------------------------------------------------------------------- tcgen05 GEMM
+
+
+@pytest.mark.parametrize("n_s,n_c", [(7, 8), (8, 9), (9, 10)])
+def test_tcgen05_gemm_parity(hhl, n_s, n_c):
+    """Split-TF32 tcgen05 controlled-U GEMMs (1 to 4 tiles in each direction) against the
+    oracle, stage by stage, complex64 tolerance."""
+    diag, off, b, walls = problem("couette", n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    ref = run_stages(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64", gemm="tcgen05")
+    assert plan.info["gemm_impl"] == 2
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_stage("qpe_u", st)
+    np.testing.assert_allclose(_np(st), ref["qpe_u"], atol=1e-5)
+    for stage in ("clock_block", "uncompute_u", "final_h"):
+        plan.apply_stage(stage, st)
+    np.testing.assert_allclose(_half(_np(st), n_s, n_c, 1), _half(ref["final_h"], n_s, n_c, 1), atol=1e-5)
+    m = plan.measure(st)
+    assert m["norm"] == pytest.approx(1.0, abs=1e-5)
+
+
+def test_tcgen05_matches_simt_gemm(hhl):
+    """The tensor-core and CUDA-core GEMM paths agree to FP32 accuracy on a random state."""
+    import torch
+    from synth_inputs import random_state
+    n_s, n_c = 8, 9
+    diag, off, b, walls = problem("poiseuille", n_s)
+    psi = random_state(n_s + n_c + 1, seed_offset=5)
+    outs = []
+    for gemm in ("simt", "tcgen05"):
+        plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64", gemm=gemm)
+        st = torch.tensor(psi, dtype=torch.complex64, device="cuda")
+        plan.apply_stage("qpe_u", st)
+        outs.append(_np(st))
+    assert np.abs(outs[0] - outs[1]).max() < 2e-6
