@@ -8,7 +8,9 @@
 // 8 M N N.
 //
 // FP32 accuracy from TF32 tensor cores (split TF32): every operand is split as
-// v = hi + lo with hi = v truncated to TF32 and lo = v - hi, and the product is
+// v ~ hi + lo with hi = v rounded to nearest TF32 and lo = (v - hi) rounded to nearest TF32
+// (round-to-nearest keeps the splitting error unbiased, so the norm does not drift over
+// the 2 n_c controlled products), and the product is
 // X_hi E_hi + X_hi E_lo + X_lo E_hi, accumulated in FP32 in tensor memory (three
 // kind::tf32 MMAs per K step). The plan stores E_hi and E_lo (forward and adjoint) for
 // every k; a gather kernel copies the rows with bit k set into compact X_hi / X_lo arrays,
@@ -135,6 +137,13 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Round to the nearest TF32 value (10 explicit mantissa bits), ties away from zero.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ int64_t row_with_bit_tc(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
 }
@@ -252,13 +261,9 @@ __global__ void k_tc_split_rows(const float4* __restrict__ half, float4* __restr
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / row4, c = e - i * row4;
     const float4 v = half[row_with_bit_tc(i, k) * row4 + c];
-    float4 h;
-    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    const float4 h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
     a_hi[e] = h;
-    a_lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    a_lo[e] = make_float4(to_tf32(v.x - h.x), to_tf32(v.y - h.y), to_tf32(v.z - h.z), to_tf32(v.w - h.w));
   }
 }
 
@@ -276,13 +281,11 @@ __global__ void k_tc_prep_b(const double2* __restrict__ U, int64_t N, float* __r
     const double ar = ua.x, ai = -ua.y;  // (U^dagger)[n][m] = conj(U[m][n])
     const double vf = s == 0 ? (t == 0 ? uf.x : -uf.y) : (t == 0 ? uf.y : uf.x);
     const double va = s == 0 ? (t == 0 ? ar : -ai) : (t == 0 ? ai : ar);
-    const float ff = (float)vf, fa = (float)va;
-    const float hf = __uint_as_float(__float_as_uint(ff) & 0xFFFFE000u);
-    const float ha = __uint_as_float(__float_as_uint(fa) & 0xFFFFE000u);
+    const float hf = to_tf32((float)vf), ha = to_tf32((float)va);
     out[e] = hf;
-    out[sz + e] = (float)(vf - (double)hf);
+    out[sz + e] = to_tf32((float)(vf - (double)hf));
     out[2 * sz + e] = ha;
-    out[3 * sz + e] = (float)(va - (double)ha);
+    out[3 * sz + e] = to_tf32((float)(va - (double)ha));
   }
 }
 
