@@ -233,6 +233,23 @@ hhl_status hhl_apply_qft(void* state_dev, int32_t n_qubits, int32_t lo, int32_t 
 /* Number of kernels this library has launched since load (all entry points). */
 uint64_t hhl_kernel_launch_count(void);
 
+/* Clock-controlled U for callers that cannot allocate device memory while they run (the
+ * paper has no counterpart; this is an interface convenience). Hosts that hand all device
+ * memory to their own pool allocator, or loops that cannot afford the device-wide
+ * synchronisation cudaMalloc / cudaFree may cause, call this instead of a plan: it applies
+ * r <- U r (adjoint = 0) or r <- U^dagger r (adjoint = 1) to every row r of half_dev whose
+ * clock bit k is set, and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   u_dev:    DEVICE complex64, N x N row-major, U[n][m] at n*N + m (N = 2^n_sys_qubits).
+ *   half_dev: DEVICE complex64, one ancilla half: 2^n_clock rows of N (in place).
+ * The product rows are staged in one fixed 8 MiB device array inside the library (held on
+ * every GPU that loads it, until exit); requests needing more than 2^20 complex64 values
+ * (2^(n_clock-1) * N) are rejected with HHL_ERR_INVALID_ARG. The first call on each device
+ * looks up that array's device address (set-up), so make it before any stream capture.
+ * Each call overwrites the staging space before reading it; calls that may overlap on the
+ * GPU (unordered streams) share the array and race. Asynchronous on `stream`. */
+hhl_status hhl_controlled_u_noalloc(const void* u_dev, void* half_dev, int32_t n_sys_qubits, int32_t n_clock,
+                                    int32_t k, int32_t adjoint, void* stream);
+
 /* Per-kernel device timing (tracing). While enabled, every kernel launch is bracketed by
  * a pair of CUDA events on its stream; reading the profile waits for those events and
  * folds them into per-kernel totals (launch count, summed milliseconds). Process-wide,

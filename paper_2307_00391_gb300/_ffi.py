@@ -69,6 +69,7 @@ SIGNATURES = [
     ("hhl_dissipation", c_int32, [c_void_p, c_void_p, _DP, c_void_p, c_void_p]),
     ("hhl_apply_qft", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
+    ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_profile_enable", None, [c_int32]),
     ("hhl_profile_reset", None, []),
     ("hhl_profile_count", c_int32, []),
