@@ -466,6 +466,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
   HHL_ALLOC(p.d_scal, 16 * sizeof(double), &p.workspace_bytes);
   HHL_PLAN_CUDA(cudaMemsetAsync(p.d_scal, 0, 16 * sizeof(double), st));
   HHL_ALLOC(p.d_b, (size_t)N * 2 * sizeof(double), &p.workspace_bytes);
+  HHL_ALLOC(p.d_bs, (size_t)std::max<int64_t>(N, 2) * ab, &p.workspace_bytes);
   HHL_ALLOC(h->d_bsplit, (size_t)N * 2 * sizeof(double), &p.workspace_bytes);
   HHL_ALLOC(h->d_meas, (size_t)(4 + 2 * N) * sizeof(double), &p.workspace_bytes);
   HHL_ALLOC(h->d_u, (size_t)(N + 1) * sizeof(double), &p.workspace_bytes);
@@ -588,7 +589,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
 void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
-  void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_scratch, p.d_trot,
+  void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
                   plan->d_meas, plan->d_u, plan->d_bsplit};
   for (void* q : ptrs)
     if (q) cudaFree(q);

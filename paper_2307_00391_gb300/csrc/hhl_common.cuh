@@ -80,6 +80,7 @@ struct Plan {
   void* d_rot = nullptr;      // 2^n_c (cos(theta/2), sin(theta/2)) pairs, amplitude precision
   double* d_scal = nullptr;   // device scalars: [0] |b|^2, [1..3] measure sums, [4] eps sum, [5] p_anc1
   double* d_b = nullptr;      // N complex128: host-prepared b
+  void* d_bs = nullptr;       // N amplitudes: b / (|b| 2^(n_c/2)), one anc = 0 row
   void* d_scratch = nullptr;  // GEMM output rows: 2^(n_c-1) * N amplitudes
   // Trotter (Toeplitz tridiagonal): per k the step count and the 2x2 blocks
   std::vector<int> trot_r;

@@ -256,14 +256,30 @@ __global__ void __launch_bounds__(128, 1)
 // Rows with clock bit k set -> compact TF32 hi / lo arrays (M_sub x 2N floats).
 __global__ void k_tc_split_rows(const float4* __restrict__ half, float4* __restrict__ a_hi, float4* __restrict__ a_lo,
                                 int n_s, int k, int64_t m_sub) {
-  const int64_t row4 = (2LL << n_s) / 4;  // float4 per row
-  const int64_t total = m_sub * row4;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / row4, c = e - i * row4;
-    const float4 v = half[row_with_bit_tc(i, k) * row4 + c];
-    const float4 h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-    a_hi[e] = h;
-    a_lo[e] = make_float4(to_tf32(v.x - h.x), to_tf32(v.y - h.y), to_tf32(v.z - h.z), to_tf32(v.w - h.w));
+  const int row4_bits = n_s - 1;  // float4 per row = 2N/4 = 2^(n_s-1)
+  const int64_t total = m_sub << row4_bits;
+  constexpr int U = 4;  // loads in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total; e0 += U * stride) {
+    float4 v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t e = e0 + q * stride;
+      if (e < total) {
+        const int64_t i = e >> row4_bits, c = e & ((1LL << row4_bits) - 1);
+        v[q] = half[(row_with_bit_tc(i, k) << row4_bits) + c];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t e = e0 + q * stride;
+      if (e < total) {
+        const float4 h = make_float4(to_tf32(v[q].x), to_tf32(v[q].y), to_tf32(v[q].z), to_tf32(v[q].w));
+        a_hi[e] = h;
+        a_lo[e] = make_float4(to_tf32(v[q].x - h.x), to_tf32(v[q].y - h.y), to_tf32(v[q].z - h.z),
+                              to_tf32(v[q].w - h.w));
+      }
+    }
   }
 }
 

@@ -1,12 +1,14 @@
 // CUDA kernels of the HHL state-vector path (sm_103a): state preparation, the SIMT
-// controlled-U GEMM, the fused clock block (inverse QFT + eigenvalue-inversion RY + QFT),
-// clock Hadamards, QFT register blocks, postselection / dissipation reductions, and the
-// plan-time exponential exp(i Ahat t) from an eigendecomposition.
+// controlled-U GEMM, postselection / dissipation reductions, and the plan-time exponential
+// exp(i Ahat t) from an eigendecomposition. (Register blocks over the clock are in
+// hhl_fft.cu, the tensor-core GEMM in hhl_gemm_tc.cu, the Trotter passes in hhl_trotter.cu.)
 //
 // State layout: S[anc][clk][sys] row-major, complex64 or complex128 interleaved; the
 // "active half" of a stage is S[0] or S[1], a row-major (2^n_c x N) matrix whose row c is
 // the system register for clock value c.
 #include <math.h>
+
+#include <type_traits>
 
 #include "hhl_common.cuh"
 
@@ -67,21 +69,25 @@ __global__ void k_bnorm(const double2* __restrict__ b, int64_t n, double* acc) {
   block_sum_atomic<1>(s, acc);
 }
 
+// bs = b / (|b| 2^(n_c/2)) in the amplitude precision (one row of the anc = 0 half).
 template <class R>
-__global__ void k_prep_fill(const double2* __restrict__ b, const double* __restrict__ acc,
-                            typename Cx<R>::T* __restrict__ st, int n_s, int n_c) {
-  const int64_t nmask = (1LL << n_s) - 1;
-  const int64_t half = 1LL << (n_s + n_c);
+__global__ void k_prep_scale(const double2* __restrict__ b, const double* __restrict__ acc,
+                             typename Cx<R>::T* __restrict__ bs, int64_t N, int n_c) {
   const double nb2 = acc[0];
   const double scale = nb2 > 0.0 ? 1.0 / sqrt(nb2 * (double)(1LL << n_c)) : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * half; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < half) {
-      double2 z = b[i & nmask];
-      st[i] = mk<R>((R)(z.x * scale), (R)(z.y * scale));
-    } else {
-      st[i] = mk<R>((R)0, (R)0);
-    }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z = b[i];
+    bs[i] = mk<R>((R)(z.x * scale), (R)(z.y * scale));
   }
+}
+
+// Every clock row of the anc = 0 half gets bs, the anc = 1 half is zeroed: 16-byte stores.
+__global__ void k_prep_fill(const uint4* __restrict__ bs, uint4* __restrict__ st, int64_t row_units,
+                            int64_t half_units) {
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < 2 * half_units;
+       u += (int64_t)gridDim.x * blockDim.x)
+    st[u] = u < half_units ? bs[u & (row_units - 1)] : zero;
 }
 
 // ------------------------------------------------------------------------------ SIMT GEMM
@@ -164,179 +170,43 @@ __global__ void k_rows_scatter(typename Cx<R>::T* __restrict__ S, const typename
   }
 }
 
-// ------------------------------------------------------------------------------ column FFTs
-// W columns of length L = 2^m live in shared memory as X[w*L + idx]. tw[j] = exp(-2 pi i j / L).
-
-template <class R>
-__device__ void fill_twiddles(typename Cx<R>::T* tw, int m) {
-  const int L = 1 << m;
-  for (int j = threadIdx.x; j < L / 2; j += blockDim.x) {
-    R s, c;
-    if constexpr (sizeof(R) == 4) {
-      sincospif(-2.0f * (float)j / (float)L, &s, &c);
-    } else {
-      sincospi(-2.0 * (double)j / (double)L, &s, &c);
-    }
-    tw[j] = mk<R>(c, s);
-  }
-}
-
-// Decimation in time: bit-reversed input, natural-order output.
-// conj_tw = false: out[y] = sum_c x[c] e^{-2 pi i c y/L}; true: e^{+2 pi i c y/L}.
-template <class T>
-__device__ void fft_dit(T* X, const T* tw, int m, int W, bool conj_tw) {
-  const int L = 1 << m, hl = L >> 1;
-  for (int s = 1; s <= m; ++s) {
-    const int half = 1 << (s - 1);
-    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
-      const int w = t / hl, b = t - w * hl;
-      const int g = b / half, j = b - g * half;
-      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
-      T f = tw[j << (m - s)];
-      if (conj_tw) f.y = -f.y;
-      T a = X[i0], c = cmul(X[i1], f);
-      X[i0] = cadd(a, c);
-      X[i1] = csub(a, c);
-    }
-    __syncthreads();
-  }
-}
-
-// Decimation in frequency: natural-order input, bit-reversed output.
-template <class T>
-__device__ void fft_dif(T* X, const T* tw, int m, int W, bool conj_tw) {
-  const int L = 1 << m, hl = L >> 1;
-  for (int s = m; s >= 1; --s) {
-    const int half = 1 << (s - 1);
-    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
-      const int w = t / hl, b = t - w * hl;
-      const int g = b / half, j = b - g * half;
-      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
-      T f = tw[j << (m - s)];
-      if (conj_tw) f.y = -f.y;
-      T a = X[i0], c = X[i1];
-      X[i0] = cadd(a, c);
-      X[i1] = cmul(csub(a, c), f);
-    }
-    __syncthreads();
-  }
-}
-
-// Walsh-Hadamard butterflies (one Hadamard per qubit, unnormalised).
-template <class T>
-__device__ void wht(T* X, int m, int W) {
-  const int L = 1 << m, hl = L >> 1;
-  for (int s = 1; s <= m; ++s) {
-    const int half = 1 << (s - 1);
-    for (int t = threadIdx.x; t < hl * W; t += blockDim.x) {
-      const int w = t / hl, b = t - w * hl;
-      const int g = b / half, j = b - g * half;
-      const int i0 = w * L + g * 2 * half + j, i1 = i0 + half;
-      T a = X[i0], c = X[i1];
-      X[i0] = cadd(a, c);
-      X[i1] = csub(a, c);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ int bitrev(int x, int m) { return (int)(__brev((unsigned)x) >> (32 - m)); }
-
-// Fused clock block (a3 + a4 + the QFT of a5): per group of W system columns, load the
-// 2^n_c clock column of the anc = 0 half, inverse QFT, apply RY(theta_y) to the ancilla
-// (anc1 = sin(theta_y/2) x, anc0 = cos(theta_y/2) x), QFT, store the anc = 1 half. The
-// anc = 0 half is stored after the QFT as well when FULL, else as it is after the rotation.
-template <class R, bool FULL>
-__global__ void __launch_bounds__(512) k_clock_block(typename Cx<R>::T* __restrict__ S,
-                                                     const typename Cx<R>::T* __restrict__ rot,
-                                                     int n_s, int n_c, int W) {
-  using T = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = 1 << n_c;
-  const int64_t N = 1LL << n_s;
-  const int64_t half = (int64_t)L * N;
-  T* tw = reinterpret_cast<T*>(smem_raw);
-  T* X = tw + L / 2;
-  T* Y = X + (size_t)W * L;
-  fill_twiddles<R>(tw, n_c);
-  const int64_t j0 = (int64_t)blockIdx.x * W;
-  T* S0 = S;
-  T* S1 = S + half;
-  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-    const int c = e / W, w = e - c * W;
-    X[w * L + bitrev(c, n_c)] = S0[(int64_t)c * N + j0 + w];
-  }
-  __syncthreads();
-  fft_dit(X, tw, n_c, W, false);
-  const R inv = (R)(1.0 / sqrt((double)L));
-  // y-major with w fastest, so that the anc = 0 stores of the early mode are contiguous.
-  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-    const int y = e / W, w = e - y * W;
-    const int idx = w * L + y;
-    const T r = rot[y];  // (cos(theta_y/2), sin(theta_y/2))
-    const T x = cscale(X[idx], inv);
-    if (FULL) Y[idx] = cscale(x, r.x);
-    else S0[(int64_t)y * N + j0 + w] = cscale(x, r.x);  // anc = 0 half left as rotated
-    X[idx] = cscale(x, r.y);
-  }
-  __syncthreads();
-  fft_dif(X, tw, n_c, W, true);
-  if (FULL) fft_dif(Y, tw, n_c, W, true);
-  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-    const int c = e / W, w = e - c * W;
-    const int src = w * L + bitrev(c, n_c);
-    S1[(int64_t)c * N + j0 + w] = cscale(X[src], inv);
-    if (FULL) S0[(int64_t)c * N + j0 + w] = cscale(Y[src], inv);
-  }
-}
-
-// Generic register transform on bits [lo, lo+m): mode 0 = QFT, 1 = inverse QFT,
-// 2 = Hadamard on each qubit. Column (o, g): elements base + c * 2^lo + w, base =
-// o * 2^(lo+m) + g * W, for w < W (W divides 2^lo).
-template <class R>
-__global__ void __launch_bounds__(512) k_register_transform(typename Cx<R>::T* __restrict__ S, int lo, int m,
-                                                            int W, int mode) {
-  using T = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = 1 << m;
-  const int64_t inner = 1LL << lo;
-  T* tw = reinterpret_cast<T*>(smem_raw);
-  T* X = tw + L / 2;
-  if (mode != 2) fill_twiddles<R>(tw, m);
-  const int64_t groups = inner / W;
-  const int64_t o = blockIdx.x / groups, g = blockIdx.x - o * groups;
-  T* base = S + o * ((int64_t)L << lo) + g * W;
-  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-    const int c = e / W, w = e - c * W;
-    const int dst = (mode == 2) ? (w * L + c) : (w * L + bitrev(c, m));
-    X[dst] = base[(int64_t)c * inner + w];
-  }
-  __syncthreads();
-  if (mode == 2) wht(X, m, W);
-  else fft_dit(X, tw, m, W, mode == 0);
-  const R inv = (R)(1.0 / sqrt((double)L));
-  for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-    const int c = e / W, w = e - c * W;
-    base[(int64_t)c * inner + w] = cscale(X[w * L + c], inv);
-  }
-}
-
 // ------------------------------------------------------------------------------ readout
 
+// FP64 sums of |S0|^2, |S1|^2 and |v|^2 (v = first row of S1), read in 16-byte units; the
+// squares of one unit are added in the amplitude precision, the running sums are FP64.
 template <class R>
 __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N, double* acc) {
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * half; i += (int64_t)gridDim.x * blockDim.x) {
-    const typename Cx<R>::T z = S[i];
-    const double p = (double)z.x * (double)z.x + (double)z.y * (double)z.y;
-    if (i < half) {
-      v[0] += p;
-    } else {
-      v[1] += p;
-      if (i - half < N) v[2] += p;
+  constexpr int per = 16 / sizeof(typename Cx<R>::T);  // amplitudes per 16-byte unit
+  using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  const V* u = reinterpret_cast<const V*>(S);
+  const int64_t units = 2 * half / per, half_u = half / per, v_u = N / per;
+  double a[3] = {0.0, 0.0, 0.0};
+  constexpr int U = 4;  // loads in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < units; i0 += U * stride) {
+    V z[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i0 + k * stride < units) z[k] = u[i0 + k * stride];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i >= units) break;
+      double p;
+      if constexpr (sizeof(R) == 4) {
+        p = (double)(z[k].x * z[k].x + z[k].y * z[k].y + z[k].z * z[k].z + z[k].w * z[k].w);
+      } else {
+        p = z[k].x * z[k].x + z[k].y * z[k].y;
+      }
+      if (i < half_u) {
+        a[0] += p;
+      } else {
+        a[1] += p;
+        if (i - half_u < v_u) a[2] += p;
+      }
     }
   }
-  block_sum_atomic<3>(v, acc);
+  block_sum_atomic<3>(a, acc);
 }
 
 // out = [p_success, p_anc1, norm, |b|, xhat (2N doubles)]
@@ -428,59 +298,6 @@ __global__ void k_store_operands(const double2* __restrict__ U, int64_t N, typen
   }
 }
 
-// ------------------------------------------------------------------------------ smem sizing
-
-template <class R>
-int clock_block_width(int n_c, int64_t N, bool full, size_t* smem) {
-  const size_t sz = sizeof(typename Cx<R>::T);
-  const size_t L = (size_t)1 << n_c;
-  int W = 8;
-  while (W > 1 && (W > N || L / 2 * sz + (full ? 2 : 1) * (size_t)W * L * sz > 200 * 1024)) W >>= 1;
-  const size_t need = L / 2 * sz + (full ? 2 : 1) * (size_t)W * L * sz;
-  if (need > 200 * 1024) return 0;
-  *smem = need;
-  return W;
-}
-
-template <class R>
-hhl_status clock_block_impl(const Plan& p, void* state, cudaStream_t st) {
-  using T = typename Cx<R>::T;
-  size_t smem = 0;
-  const int W = clock_block_width<R>(p.n_c, p.N, p.full != 0, &smem);
-  if (W == 0) return fail(HHL_ERR_UNSUPPORTED, "clock register too large for one shared-memory block");
-  const int grid = (int)(p.N / W);
-  if (p.full) {
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HHL_PROF_BEGIN(st);
-    k_clock_block<R, true><<<grid, 512, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
-  } else {
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HHL_PROF_BEGIN(st);
-    k_clock_block<R, false><<<grid, 512, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
-  }
-  HHL_LAUNCH_CHECK("k_clock_block");
-  return HHL_OK;
-}
-
-template <class R>
-hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, cudaStream_t st) {
-  using T = typename Cx<R>::T;
-  const size_t sz = sizeof(T);
-  const size_t L = (size_t)1 << m;
-  const int64_t inner = 1LL << lo;
-  int W = 8;
-  while (W > 1 && (W > inner || L / 2 * sz + (size_t)W * L * sz > 200 * 1024)) W >>= 1;
-  const size_t smem = L / 2 * sz + (size_t)W * L * sz;
-  if (smem > 200 * 1024) return fail(HHL_ERR_UNSUPPORTED, "register too large for one shared-memory block");
-  const int64_t cols = (1LL << (n - m)) / W;
-  if (cols > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
-  HHL_CUDA_TRY(cudaFuncSetAttribute(k_register_transform<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  HHL_PROF_BEGIN(st);
-  k_register_transform<R><<<(int)cols, 512, smem, st>>>((T*)state, lo, m, W, mode);
-  HHL_LAUNCH_CHECK("k_register_transform");
-  return HHL_OK;
-}
-
 }  // namespace
 
 // ================================================================================ launchers
@@ -493,15 +310,20 @@ hhl_status launch_bnorm(const double* b, int64_t N, double* acc, cudaStream_t st
 }
 
 hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStream_t st) {
-  const int64_t total = 2 * p.R * p.N;
-  const int g = grid_for(total, kThreads, 152 * 32);
+  const int gs = grid_for(p.N, kThreads, 152);
   if (p.prec == HHL_PREC_C64) {
     HHL_PROF_BEGIN(st);
-    k_prep_fill<float><<<g, kThreads, 0, st>>>((const double2*)b, p.d_scal, (float2*)state, p.n_s, p.n_c);
+    k_prep_scale<float><<<gs, kThreads, 0, st>>>((const double2*)b, p.d_scal, (float2*)p.d_bs, p.N, p.n_c);
   } else {
     HHL_PROF_BEGIN(st);
-    k_prep_fill<double><<<g, kThreads, 0, st>>>((const double2*)b, p.d_scal, (double2*)state, p.n_s, p.n_c);
+    k_prep_scale<double><<<gs, kThreads, 0, st>>>((const double2*)b, p.d_scal, (double2*)p.d_bs, p.N, p.n_c);
   }
+  HHL_LAUNCH_CHECK("k_prep_scale");
+  const int64_t row_units = p.N * (int64_t)p.amp_bytes() / 16;
+  const int64_t half_units = p.R * row_units;
+  const int g = grid_for(2 * half_units, kThreads, 152 * 16);
+  HHL_PROF_BEGIN(st);
+  k_prep_fill<<<g, kThreads, 0, st>>>((const uint4*)p.d_bs, (uint4*)state, row_units, half_units);
   HHL_LAUNCH_CHECK("k_prep_fill");
   return HHL_OK;
 }
@@ -529,25 +351,6 @@ hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, c
   }
   HHL_LAUNCH_CHECK("k_rows_scatter");
   return HHL_OK;
-}
-
-hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
-  return p.prec == HHL_PREC_C64 ? clock_block_impl<float>(p, state, st) : clock_block_impl<double>(p, state, st);
-}
-
-hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
-  // Hadamards on bits [n_s, n_s + n_c): on the anc = 1 half, or on the whole state (full).
-  const int64_t half_amps = p.R * p.N;
-  void* base = p.full ? state : (void*)((char*)state + half_amps * p.amp_bytes());
-  const int n = p.full ? p.n : p.n - 1;
-  return p.prec == HHL_PREC_C64 ? register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st)
-                                : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
-}
-
-hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st) {
-  const int mode = inverse ? 1 : 0;
-  return prec == HHL_PREC_C64 ? register_transform_impl<float>(state, n, lo, m, mode, st)
-                              : register_transform_impl<double>(state, n, lo, m, mode, st);
 }
 
 hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st) {
