@@ -37,6 +37,10 @@ WORKLOADS = {
                               "dense controlled exp(i A t) as complex GEMMs"),
     "poiseuille_16": dict(flow="poiseuille", n_s=4, n_c=6, expm="dense", unit="HHL solves/s", t0_rule="power_law",
                           desc="Poiseuille flow, N=16, n_c=6, 11 qubits, T0 from the power law"),
+    "poiseuille_2p16": dict(flow="poiseuille", n_s=16, n_c=11, expm="trotter", unit="GB/s",
+                            trotter_dt=1024.0, trotter_steps_max=8,
+                            desc="Poiseuille flow, N=2^16, n_c=11, 28 qubits, Strang-Trotter exp(i A t) "
+                                 "(a 2 GiB case of the 32-qubit kernels, for profiling)"),
     "poiseuille_2p18": dict(flow="poiseuille", n_s=18, n_c=13, expm="trotter", unit="GB/s",
                             trotter_dt=1024.0, trotter_steps_max=8,
                             desc="Poiseuille flow, N=2^18, n_c=13, 32 qubits, Strang-Trotter exp(i A t)"),
@@ -216,7 +220,7 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_prep_fill": ("byte", 2.0 * half),
         "k_measure_sums": ("byte", 2.0 * half),
         "k_trotter_pass": ("byte", 2.0 * m_sub * N * prec_bytes),
-        "k_rows_copy_back": ("byte", 2.0 * m_sub * N * prec_bytes),
+        "k_trotter_edges": ("byte", 2.0 * m_sub * ((N + 479) // 480) * 32 * prec_bytes),
     }
 
 

@@ -488,7 +488,12 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
     }
   }
 
-  HHL_ALLOC(p.d_scratch, (size_t)(p.R / 2) * N * ab, &p.workspace_bytes);
+  {
+    // GEMM output rows (dense) or the Trotter pass's interior edges (32 per warp window)
+    size_t scratch_amps = (size_t)(p.R / 2) * N;
+    if (!dense) scratch_amps = std::max(scratch_amps, (size_t)(p.R / 2) * trotter_segments(N) * 32);
+    HHL_ALLOC(p.d_scratch, scratch_amps * ab, &p.workspace_bytes);
+  }
   if (dense) {
     p.gemm_impl = params->gemm_impl;
     if (p.gemm_impl == HHL_GEMM_AUTO) p.gemm_impl = tc_supported(p) ? HHL_GEMM_TCGEN05 : HHL_GEMM_SIMT;
@@ -552,14 +557,9 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
     const double dh = prob->diag[0] / p.lam_ub, oh = N > 1 ? prob->off[0] / p.lam_ub : 0.0;
     p.trot_r.resize(p.n_c);
     p.trot_blocks.assign((size_t)p.n_c * 24, 0.0);
-    auto blk = [](double* out, double s, double d, double o) {
-      // exp(i s [[d, o], [o, d]]) = e^{i s d} [[cos(s o), i sin(s o)], [i sin(s o), cos(s o)]]
-      const double cd = cos(s * d), sd = sin(s * d), co = cos(s * o), so = sin(s * o);
-      // entries (a00, a01) as complex: a00 = e^{isd} cos, a01 = e^{isd} i sin
-      out[0] = cd * co;  out[1] = sd * co;     // a00 = a11
-      out[2] = -sd * so; out[3] = cd * so;     // a01 = a10
-      out[4] = 0; out[5] = 0; out[6] = 0; out[7] = 0;
-    };
+    // exp(i s [[d, o], [o, d]]) = e^{i s d} R(s o) and exp(i s [[0, o], [o, 0]]) = R(s o),
+    // R(th) = [[cos th, i sin th], [i sin th, cos th]]. Per k: cos, sin of (tau/2) o and
+    // tau o, then tau and d (the E phases are applied once per pass).
     for (int k = 0; k < p.n_c; ++k) {
       const double t = p.t0 * (double)(1LL << k) / (double)p.R;
       int r = (int)std::ceil(t / p.trotter_dt);
@@ -567,9 +567,13 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       if (p.trotter_max > 0 && r > p.trotter_max) r = p.trotter_max;
       p.trot_r[k] = r;
       const double tau = t / r;
-      blk(&p.trot_blocks[(size_t)k * 24 + 0], tau / 2.0, dh, oh);
-      blk(&p.trot_blocks[(size_t)k * 24 + 8], tau, dh, oh);
-      blk(&p.trot_blocks[(size_t)k * 24 + 16], tau, 0.0, oh);
+      double* q = &p.trot_blocks[(size_t)k * 24];
+      q[0] = cos(0.5 * tau * oh);
+      q[1] = sin(0.5 * tau * oh);
+      q[2] = cos(tau * oh);
+      q[3] = sin(tau * oh);
+      q[4] = tau;
+      q[5] = dh;
       p.trotter_passes += (int64_t)r * (p.full ? 3 : 2);
     }
     HHL_ALLOC(p.d_trot, p.trot_blocks.size() * sizeof(double), &p.table_bytes);

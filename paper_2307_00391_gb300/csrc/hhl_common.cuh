@@ -109,6 +109,7 @@ hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_v
                              const double* d_sin, double wgt, double2* d_u, cudaStream_t st);
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);
 hhl_status launch_trotter(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+int64_t trotter_segments(int64_t N);  // warp windows per system row in a Trotter pass
 hhl_status launch_interleave(const double* re, const double* im, int64_t n, double* out, cudaStream_t st);
 
 // tcgen05 GEMM (hhl_gemm_tc.cu)

@@ -2,136 +2,141 @@
 // the clock block of the HHL circuit (inverse QFT + eigenvalue-inversion RY + QFT), the
 // Hadamard layer on the clock, and stand-alone QFT / inverse QFT blocks.
 //
-// A CTA holds W "columns" in shared memory, each the 2^m amplitudes that differ only in
-// the register's bits (stride 2^lo in the state), with W consecutive values of the lower
-// bits so that each global access covers W contiguous amplitudes. The transform of a
-// column is applied in passes of up to 4 qubits: a thread loads the 2^r amplitudes of one
-// group into registers, applies the r radix-2 stages (Hadamard + controlled-phase layers
-// of the QFT circuit, i.e. Cooley-Tukey butterflies) in registers, and stores them back,
-// so a 12-qubit register costs 3 shared-memory round trips instead of 12. Columns are
-// padded by one element per 16 to spread the strided group accesses over the banks.
+// A "column" is the 2^m amplitudes that differ only in the register's bits (stride 2^lo
+// in the state). A thread-block cluster of C = 2^CB CTAs holds W consecutive columns (so
+// every global access covers W contiguous amplitudes, up to 64 bytes): CTA r of the
+// cluster keeps the rows whose top CB register bits equal r, 2^m / C rows of W columns,
+// in its shared memory. The CB butterfly stages that pair rows held by different CTAs run
+// as one radix-C pass that reads the partners through distributed shared memory; the
+// other m - CB stages are local and run in passes of up to 4 stages: a thread loads the
+// 2^r amplitudes of one group into registers, applies the r radix-2 stages (the Hadamard
+// and controlled-phase layers of the QFT circuit, i.e. Cooley-Tukey butterflies), and
+// stores them back, so a 12-qubit register costs 3 shared-memory round trips instead of
+// 12. Rows are padded by one element per 16 to spread strided accesses over the banks;
+// twiddles come from two small tables (exp(-2 pi i q / L) = T1[q >> 6] T0[q & 63]).
 //
 // Orders: decimation in frequency (DIF) takes natural order and leaves the result in
 // bit-reversed order; decimation in time (DIT) takes bit-reversed order and returns natural
 // order. The clock block chains DIF (inverse QFT) -> rotation at bit-reversed positions ->
-// DIT (QFT), so no explicit bit-reversal permutation (the QFT's swap layer) is ever applied.
+// DIT (QFT), so no explicit bit-reversal permutation (the QFT's swap layer) is applied.
+#include <cooperative_groups.h>
+
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
 #include "hhl_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hhl {
 
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr size_t kFftSmemCap = 220 * 1024;
+constexpr size_t kFftSmemTarget = 140 * 1024;  // one CTA per SM at most this large
+constexpr size_t kFftSmemCap = 200 * 1024;
+constexpr int kUnroll = 8;                     // 16-byte loads in flight per thread
+constexpr int kCrossK = 4;                     // groups per thread per cross-CTA chunk
 
 __device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
 __device__ __forceinline__ int bitrev_m(int x, int m) { return (int)(__brev((unsigned)x) >> (32 - m)); }
 
-// Global <-> shared column blocks in 16-byte units with kUnroll loads in flight per thread.
-// Row c of the block holds W contiguous amplitudes at src + c * row_stride; they go to
-// X[w * Lp + pad16(pos(c))], pos = identity or bit reversal over m bits.
-constexpr int kUnroll = 8;
-
-// Element-wise form for blocks narrower than one 16-byte unit (W * sizeof(T) < 16).
 template <class T>
-__device__ void load_block_elems(T* X, int Lp, const T* src, int64_t row_stride, int L, int W, int m, bool rev) {
-  const int total = L * W;
-  for (int b = threadIdx.x; b < total; b += blockDim.x * kUnroll) {
-    T v[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int u = b + k * blockDim.x;
-      if (u < total) {
-        const int c = u / W, w = u - c * W;
-        v[k] = src[(int64_t)c * row_stride + w];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int u = b + k * blockDim.x;
-      if (u < total) {
-        const int c = u / W, w = u - c * W;
-        X[w * Lp + pad16(rev ? bitrev_m(c, m) : c)] = v[k];
-      }
-    }
+struct Twiddle {
+  const T* t0;  // exp(-2 pi i j / L), j < 64
+  const T* t1;  // exp(-2 pi i 64 j / L)
+  __device__ __forceinline__ T operator()(int q, bool conj) const {
+    T f = cmul(t1[q >> 6], t0[q & 63]);
+    if (conj) f.y = -f.y;
+    return f;
   }
-}
+};
 
-template <class T, class S>
-__device__ void store_block_elems(T* dst, int64_t row_stride, const T* X, int Lp, int L, int W, S scale) {
-  for (int u = threadIdx.x; u < L * W; u += blockDim.x) {
-    const int c = u / W, w = u - c * W;
-    dst[(int64_t)c * row_stride + w] = cscale(X[w * Lp + pad16(c)], scale);
-  }
-}
-
-template <class T>
-__device__ void load_block(T* X, int Lp, const T* src, int64_t row_stride, int L, int W, int m, bool rev) {
-  constexpr int per = 16 / sizeof(T);
-  const int upr = W / per;  // 16-byte units per row (W is a multiple of per)
-  const int total = L * upr;
-  for (int b = threadIdx.x; b < total; b += blockDim.x * kUnroll) {
-    uint4 v[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int u = b + k * blockDim.x;
-      if (u < total) {
-        const int c = u / upr, h = u - c * upr;
-        v[k] = *reinterpret_cast<const uint4*>(src + (int64_t)c * row_stride + h * per);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int u = b + k * blockDim.x;
-      if (u < total) {
-        const int c = u / upr, h = u - c * upr;
-        const int pos = pad16(rev ? bitrev_m(c, m) : c);
-        const T* t = reinterpret_cast<const T*>(&v[k]);
-#pragma unroll
-        for (int q = 0; q < per; ++q) X[(h * per + q) * Lp + pos] = t[q];
-      }
-    }
-  }
-}
-
-// dst row c (W contiguous amplitudes) = scale * X[w * Lp + pad16(c)].
-template <class T, class S>
-__device__ void store_block(T* dst, int64_t row_stride, const T* X, int Lp, int L, int W, S scale) {
-  constexpr int per = 16 / sizeof(T);
-  const int upr = W / per;
-  const int total = L * upr;
-  for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int c = u / upr, h = u - c * upr;
-    uint4 v;
-    T* t = reinterpret_cast<T*>(&v);
-#pragma unroll
-    for (int q = 0; q < per; ++q) t[q] = cscale(X[(h * per + q) * Lp + pad16(c)], scale);
-    *reinterpret_cast<uint4*>(dst + (int64_t)c * row_stride + h * per) = v;
-  }
-}
+__host__ __device__ constexpr int twiddle_entries(int m) { return 64 + ((1 << m) / 64 > 1 ? (1 << m) / 64 : 1); }
 
 template <class R>
-__device__ void fill_twiddles(typename Cx<R>::T* tw, int m) {
+__device__ void fill_twiddles(typename Cx<R>::T* t0, typename Cx<R>::T* t1, int m) {
   const int L = 1 << m;
-  for (int j = threadIdx.x; j < L / 2; j += blockDim.x) {
+  const int n1 = twiddle_entries(m) - 64;
+  for (int j = threadIdx.x; j < 64 + n1; j += blockDim.x) {
+    const int e = j < 64 ? j : 64 * (j - 64);
     R s, c;
     if constexpr (sizeof(R) == 4) {
-      sincospif(-2.0f * (float)j / (float)L, &s, &c);
+      sincospif(-2.0f * (float)(e & (L - 1)) / (float)L, &s, &c);
     } else {
-      sincospi(-2.0 * (double)j / (double)L, &s, &c);
+      sincospi(-2.0 * (double)(e & (L - 1)) / (double)L, &s, &c);
     }
-    tw[j] = mk<R>(c, s);
+    if (j < 64) t0[j] = mk<R>(c, s);
+    else t1[j - 64] = mk<R>(c, s);
   }
 }
 
-// One pass of RB radix-2 stages (global stages s0-RB+1 .. s0) on every group of every column.
-// MODE 0: DFT butterflies with twiddles tw[q] = exp(-2 pi i q / L) (conjugated if conj);
-// MODE 1: Hadamard butterflies (no twiddles). DIT selects the stage order and twiddle side.
+// e^{-2 pi i k / 16}, k < 16 (the in-group factors of the twiddles, see butterflies()).
+__constant__ double kRoot16[16][2] = {
+    {1.0, 0.0}, {0.92387953251128674, -0.38268343236508978}, {0.70710678118654752, -0.70710678118654752},
+    {0.38268343236508978, -0.92387953251128674}, {0.0, -1.0}, {-0.38268343236508978, -0.92387953251128674},
+    {-0.70710678118654752, -0.70710678118654752}, {-0.92387953251128674, -0.38268343236508978}, {-1.0, 0.0},
+    {-0.92387953251128674, 0.38268343236508978}, {-0.70710678118654752, 0.70710678118654752},
+    {-0.38268343236508978, 0.92387953251128674}, {0.0, 1.0}, {0.38268343236508978, 0.92387953251128674},
+    {0.70710678118654752, 0.70710678118654752}, {0.92387953251128674, 0.38268343236508978}};
+
+// The RB radix-2 stages of one group: v[x] = element lo + x * 2^lo_bits (+ a multiple of
+// 2^(lo_bits + RB)); local bit t is global stage s = t + 1 + lo_bits of an m-stage transform.
+// MODE 0: DFT butterflies, MODE 1: Hadamard butterflies. DIF runs t from high to low.
+// The twiddle of butterfly x at bit t, exp(-2 pi i ((x mod 2^t) 2^lo_bits + lo) 2^(m-s) / L),
+// factors into exp(-2 pi i lo 2^(m-s) / L) (one table lookup per stage) times
+// exp(-2 pi i (x mod 2^t) / 2^(t+1)) (a sixteenth root of unity, from constant memory).
 template <class T, int RB, bool DIT, int MODE>
-__device__ void radix_pass(T* X, int Lp, int W, const T* tw, int m, int s0, bool conj) {
+__device__ __forceinline__ void butterflies(T (&v)[1 << RB], int lo, int lo_bits, int m, const Twiddle<T>& tw,
+                                            bool conj) {
+  constexpr int G = 1 << RB;
+  using R = decltype(T().x);
+#pragma unroll
+  for (int tt = 0; tt < RB; ++tt) {
+    const int t = DIT ? tt : (RB - 1 - tt);
+    const int s = t + 1 + lo_bits;
+    T base;
+    if (MODE == 0) base = tw(lo << (m - s), conj);
+#pragma unroll
+    for (int x = 0; x < G; ++x) {
+      if (x & (1 << t)) continue;
+      const int x1 = x | (1 << t);
+      T a = v[x], b = v[x1];
+      if (MODE == 0) {
+        const int xr = x & ((1 << t) - 1);
+        T f = base;
+        if (xr != 0) {
+          const int k16 = xr << (3 - t);
+          T w;
+          w.x = (R)kRoot16[k16][0];
+          w.y = conj ? -(R)kRoot16[k16][1] : (R)kRoot16[k16][1];
+          f = cmul(base, w);
+        }
+        if (DIT) {
+          b = cmul(b, f);
+          v[x] = cadd(a, b);
+          v[x1] = csub(a, b);
+        } else {
+          v[x] = cadd(a, b);
+          v[x1] = cmul(csub(a, b), f);
+        }
+      } else {
+        v[x] = cadd(a, b);
+        v[x1] = csub(a, b);
+      }
+    }
+  }
+}
+
+// One local pass of RB stages (global stages s0-RB+1 .. s0 <= m_loc) on every group of the
+// W local columns of 2^m_loc rows.
+template <class T, int RB, bool DIT, int MODE>
+__device__ void radix_pass(T* X, int Lp, int W, const Twiddle<T>& tw, int m, int m_loc, int s0, bool conj) {
   constexpr int G = 1 << RB;
   const int lo_bits = s0 - RB;
-  const int gpc_bits = m - RB;  // groups per column = 2^(m - RB)
+  const int gpc_bits = m_loc - RB;
   const int total = W << gpc_bits;
   for (int g = threadIdx.x; g < total; g += blockDim.x) {
     const int w = g >> gpc_bits;
@@ -143,90 +148,195 @@ __device__ void radix_pass(T* X, int Lp, int W, const T* tw, int m, int s0, bool
     T v[G];
 #pragma unroll
     for (int x = 0; x < G; ++x) v[x] = col[pad16(base + (x << lo_bits))];
-#pragma unroll
-    for (int tt = 0; tt < RB; ++tt) {
-      const int t = DIT ? tt : (RB - 1 - tt);
-      const int s = t + 1 + lo_bits;  // global stage of this butterfly layer
-#pragma unroll
-      for (int x = 0; x < G; ++x) {
-        if (x & (1 << t)) continue;
-        const int x1 = x | (1 << t);
-        T a = v[x], b = v[x1];
-        if (MODE == 0) {
-          const int j = ((x & ((1 << t) - 1)) << lo_bits) + lo;
-          T f = tw[j << (m - s)];
-          if (conj) f.y = -f.y;
-          if (DIT) {
-            b = cmul(b, f);
-            v[x] = cadd(a, b);
-            v[x1] = csub(a, b);
-          } else {
-            v[x] = cadd(a, b);
-            v[x1] = cmul(csub(a, b), f);
-          }
-        } else {
-          v[x] = cadd(a, b);
-          v[x1] = csub(a, b);
-        }
-      }
-    }
+    butterflies<T, RB, DIT, MODE>(v, lo, lo_bits, m, tw, conj);
 #pragma unroll
     for (int x = 0; x < G; ++x) col[pad16(base + (x << lo_bits))] = v[x];
   }
 }
 
 template <class T, bool DIT, int MODE>
-__device__ void radix_dispatch(int r, T* X, int Lp, int W, const T* tw, int m, int s0, bool conj) {
-  switch (r) {
-    case 4: radix_pass<T, 4, DIT, MODE>(X, Lp, W, tw, m, s0, conj); break;
-    case 3: radix_pass<T, 3, DIT, MODE>(X, Lp, W, tw, m, s0, conj); break;
-    case 2: radix_pass<T, 2, DIT, MODE>(X, Lp, W, tw, m, s0, conj); break;
-    default: radix_pass<T, 1, DIT, MODE>(X, Lp, W, tw, m, s0, conj); break;
-  }
-}
-
-// Full transform of every column: DIF (natural -> bit-reversed) or DIT (bit-reversed ->
-// natural), in passes of <= 4 stages.
-template <class T, bool DIT, int MODE>
-__device__ void column_transform(T* X, int Lp, int W, const T* tw, int m, bool conj) {
-  const int npass = (m + 3) / 4;
+__device__ void local_stages(T* X, int Lp, int W, const Twiddle<T>& tw, int m, int m_loc, bool conj) {
+  const int npass = (m_loc + 3) / 4;
   int done = 0;
   for (int p = 0; p < npass; ++p) {
-    const int r = (m - done) / (npass - p);  // balanced pass sizes, each <= 4
-    const int s0 = DIT ? done + r : m - done;
-    radix_dispatch<T, DIT, MODE>(r, X, Lp, W, tw, m, s0, conj);
+    const int r = (m_loc - done) / (npass - p);  // balanced pass sizes, each <= 4
+    const int s0 = DIT ? done + r : m_loc - done;
+    switch (r) {
+      case 4: radix_pass<T, 4, DIT, MODE>(X, Lp, W, tw, m, m_loc, s0, conj); break;
+      case 3: radix_pass<T, 3, DIT, MODE>(X, Lp, W, tw, m, m_loc, s0, conj); break;
+      case 2: radix_pass<T, 2, DIT, MODE>(X, Lp, W, tw, m, m_loc, s0, conj); break;
+      default: radix_pass<T, 1, DIT, MODE>(X, Lp, W, tw, m, m_loc, s0, conj); break;
+    }
     done += r;
     __syncthreads();
   }
 }
 
-// Clock block (a3 + a4 + the QFT of a5).
-template <class R, bool FULL>
-__global__ void __launch_bounds__(kFftThreads) k_clock_block(typename Cx<R>::T* __restrict__ S,
+// The CB stages across the cluster (global stages m_loc+1 .. m): every CTA gathers the C
+// partners of each of its groups from all CTAs' shared memory, computes the butterflies
+// and keeps the output that belongs to its own rows. Chunks of kCrossK groups per thread;
+// a cluster barrier between the gathers and the write-back of each chunk keeps a CTA from
+// overwriting values another CTA has yet to read. Every CTA must have finished writing its
+// columns (cluster barrier) before this is called. X2 (may be null) is transformed alongside.
+template <class T, int CB, bool DIT, int MODE>
+__device__ void cross_stages(cg::cluster_group& cl, T* X, T* X2, int Lp, int W, const Twiddle<T>& tw, int m,
+                             bool conj) {
+  constexpr int C = 1 << CB;
+  const int m_loc = m - CB;
+  const int rank = (int)cl.block_rank();
+  const int total = W << m_loc;
+  for (int base = 0; base < total; base += blockDim.x * kCrossK) {
+    T keep[kCrossK], keep2[kCrossK];
+#pragma unroll
+    for (int kk = 0; kk < kCrossK; ++kk) {
+      const int g = base + kk * blockDim.x + threadIdx.x;
+      if (g < total) {
+        const int w = g >> m_loc, p = g & ((1 << m_loc) - 1);
+        const int off = w * Lp + pad16(p);
+        T v[C];
+#pragma unroll
+        for (int x = 0; x < C; ++x) v[x] = cl.map_shared_rank(X, x)[off];
+        butterflies<T, CB, DIT, MODE>(v, p, m_loc, m, tw, conj);
+#pragma unroll
+        for (int x = 0; x < C; ++x)
+          if (x == rank) keep[kk] = v[x];  // static indexing keeps v in registers
+        if (X2 != nullptr) {
+#pragma unroll
+          for (int x = 0; x < C; ++x) v[x] = cl.map_shared_rank(X2, x)[off];
+          butterflies<T, CB, DIT, MODE>(v, p, m_loc, m, tw, conj);
+#pragma unroll
+          for (int x = 0; x < C; ++x)
+            if (x == rank) keep2[kk] = v[x];
+        }
+      }
+    }
+    cl.sync();
+#pragma unroll
+    for (int kk = 0; kk < kCrossK; ++kk) {
+      const int g = base + kk * blockDim.x + threadIdx.x;
+      if (g < total) {
+        const int w = g >> m_loc, p = g & ((1 << m_loc) - 1);
+        const int off = w * Lp + pad16(p);
+        X[off] = keep[kk];
+        if (X2 != nullptr) X2[off] = keep2[kk];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Rows [0, Lc) of a W-column block (row c at src + c * row_stride) -> X[w * Lp + pad16(c)],
+// in 16-byte units with kUnroll loads in flight per thread (W * sizeof(T) >= 16), or
+// element by element otherwise.
+template <class T>
+__device__ void load_block(T* X, int Lp, const T* src, int64_t row_stride, int Lc, int W) {
+  constexpr int per = 16 / sizeof(T);
+  if (W % per == 0) {
+    const int upr = W / per;
+    const int total = Lc * upr;
+    for (int b = threadIdx.x; b < total; b += blockDim.x * kUnroll) {
+      uint4 v[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int u = b + k * blockDim.x;
+        if (u < total) {
+          const int c = u / upr, h = u - c * upr;
+          v[k] = *reinterpret_cast<const uint4*>(src + (int64_t)c * row_stride + h * per);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int u = b + k * blockDim.x;
+        if (u < total) {
+          const int c = u / upr, h = u - c * upr;
+          const T* t = reinterpret_cast<const T*>(&v[k]);
+#pragma unroll
+          for (int q = 0; q < per; ++q) X[(h * per + q) * Lp + pad16(c)] = t[q];
+        }
+      }
+    }
+  } else {
+    const int total = Lc * W;
+    for (int b = threadIdx.x; b < total; b += blockDim.x * kUnroll) {
+      T v[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int u = b + k * blockDim.x;
+        if (u < total) v[k] = src[(int64_t)(u / W) * row_stride + (u % W)];
+      }
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int u = b + k * blockDim.x;
+        if (u < total) X[(u % W) * Lp + pad16(u / W)] = v[k];
+      }
+    }
+  }
+}
+
+// dst row row_of(p) (W contiguous amplitudes) = scale * X[w * Lp + pad16(p)], p < Lc;
+// row_of(p) = p, or the bit reversal of (rank * Lc + p) over m bits when rev.
+template <class T, class S>
+__device__ void store_block(T* dst, int64_t row_stride, const T* X, int Lp, int Lc, int W, S scale, bool rev,
+                            int rank, int m) {
+  constexpr int per = 16 / sizeof(T);
+  if (W % per == 0) {
+    const int upr = W / per;
+    for (int u = threadIdx.x; u < Lc * upr; u += blockDim.x) {
+      const int p = u / upr, h = u - p * upr;
+      const int row = rev ? bitrev_m(rank * Lc + p, m) : p;
+      uint4 v;
+      T* t = reinterpret_cast<T*>(&v);
+#pragma unroll
+      for (int q = 0; q < per; ++q) t[q] = cscale(X[(h * per + q) * Lp + pad16(p)], scale);
+      *reinterpret_cast<uint4*>(dst + (int64_t)row * row_stride + h * per) = v;
+    }
+  } else {
+    for (int u = threadIdx.x; u < Lc * W; u += blockDim.x) {
+      const int p = u / W, w = u % W;
+      const int row = rev ? bitrev_m(rank * Lc + p, m) : p;
+      dst[(int64_t)row * row_stride + w] = cscale(X[w * Lp + pad16(p)], scale);
+    }
+  }
+}
+
+// Clock block (a3 + a4 + the QFT of a5) on a cluster of 2^CB CTAs.
+template <class R, bool FULL, int CB>
+__global__ void __launch_bounds__(kFftThreads, 2) k_clock_block(typename Cx<R>::T* __restrict__ S,
                                                              const typename Cx<R>::T* __restrict__ rot, int n_s,
                                                              int n_c, int W) {
   using T = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = 1 << n_c, Lp = L + L / 16;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = CB > 0 ? (int)cl.block_rank() : 0;
+  const int m = n_c, m_loc = n_c - CB;
+  const int Lc = 1 << m_loc, Lp = Lc + Lc / 16 + 1;
   const int64_t N = 1LL << n_s;
-  const int64_t half = (int64_t)L * N;
-  T* tw = reinterpret_cast<T*>(smem_raw);
-  T* X = tw + L / 2;
+  const int64_t half = (N << n_c);
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  T* X = t0 + twiddle_entries(m);
   T* Y = X + (size_t)W * Lp;
-  fill_twiddles<R>(tw, n_c);
-  const int64_t j0 = (int64_t)blockIdx.x * W;
+  fill_twiddles<R>(t0, t1, m);
+  const Twiddle<T> tw{t0, t1};
+  const int64_t j0 = (int64_t)(blockIdx.x >> CB) * W;
+  const int64_t row0 = (int64_t)rank * Lc;  // first clock row held by this CTA
   T* S0 = S;
   T* S1 = S + half;
-  load_block(X, Lp, S0 + j0, N, L, W, n_c, false);
-  __syncthreads();
-  column_transform<T, false, 0>(X, Lp, W, tw, n_c, false);  // inverse QFT, bit-reversed result
-  const R inv = (R)(1.0 / sqrt((double)L));
+  load_block(X, Lp, S0 + row0 * N + j0, N, Lc, W);
+  if (CB > 0) {
+    cl.sync();
+    cross_stages<T, CB, false, 0>(cl, X, (T*)nullptr, Lp, W, tw, m, false);  // inverse QFT, top stages
+  } else {
+    __syncthreads();
+  }
+  local_stages<T, false, 0>(X, Lp, W, tw, m, m_loc, false);  // inverse QFT, bit-reversed result
+  const R inv = (R)(1.0 / sqrt((double)(1 << m)));
   // rotation at bit-reversed positions, in 16-byte units of W/per consecutive columns
   constexpr int per = 16 / sizeof(T);
   const int upr = W / per;
-  for (int u = threadIdx.x; u < L * upr; u += blockDim.x) {
+  for (int u = threadIdx.x; u < Lc * upr; u += blockDim.x) {
     const int p = u / upr, h = u - p * upr;
-    const int y = bitrev_m(p, n_c);
+    const int y = bitrev_m((int)row0 + p, m);
     const T r = rot[y];  // (cos(theta_y/2), sin(theta_y/2))
     uint4 keep;
     T* kt = reinterpret_cast<T*>(&keep);
@@ -241,91 +351,166 @@ __global__ void __launch_bounds__(kFftThreads) k_clock_block(typename Cx<R>::T* 
     if (!FULL) *reinterpret_cast<uint4*>(S0 + (int64_t)y * N + j0 + h * per) = keep;  // anc = 0 half as rotated
   }
   __syncthreads();
-  column_transform<T, true, 0>(X, Lp, W, tw, n_c, true);  // QFT, natural order
-  if (FULL) column_transform<T, true, 0>(Y, Lp, W, tw, n_c, true);
-  store_block(S1 + j0, N, X, Lp, L, W, inv);
-  if (FULL) store_block(S0 + j0, N, Y, Lp, L, W, inv);
+  local_stages<T, true, 0>(X, Lp, W, tw, m, m_loc, true);  // QFT, lower stages
+  if (FULL) local_stages<T, true, 0>(Y, Lp, W, tw, m, m_loc, true);
+  if (CB > 0) {
+    cl.sync();
+    cross_stages<T, CB, true, 0>(cl, X, FULL ? Y : (T*)nullptr, Lp, W, tw, m, true);  // QFT, top stages
+  }
+  store_block(S1 + row0 * N + j0, N, X, Lp, Lc, W, inv, false, rank, m);
+  if (FULL) store_block(S0 + row0 * N + j0, N, Y, Lp, Lc, W, inv, false, rank, m);
 }
 
 // Register transform on bits [lo, lo+m): mode 0 = QFT, 1 = inverse QFT, 2 = Hadamards.
-template <class R>
-__global__ void __launch_bounds__(kFftThreads) k_register_transform(typename Cx<R>::T* __restrict__ S, int lo, int m,
+// DIF (natural in); QFT / inverse QFT results are stored from bit-reversed positions.
+template <class R, int CB>
+__global__ void __launch_bounds__(kFftThreads, 2) k_register_transform(typename Cx<R>::T* __restrict__ S, int lo, int m,
                                                                     int W, int mode) {
   using T = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = 1 << m, Lp = L + L / 16;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = CB > 0 ? (int)cl.block_rank() : 0;
+  const int m_loc = m - CB;
+  const int Lc = 1 << m_loc, Lp = Lc + Lc / 16 + 1;
   const int64_t inner = 1LL << lo;
-  T* tw = reinterpret_cast<T*>(smem_raw);
-  T* X = tw + L / 2;
-  if (mode != 2) fill_twiddles<R>(tw, m);
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  T* X = t0 + twiddle_entries(m);
+  if (mode != 2) fill_twiddles<R>(t0, t1, m);
+  const Twiddle<T> tw{t0, t1};
   const int64_t groups = inner / W;
-  const int64_t o = blockIdx.x / groups, g = blockIdx.x - o * groups;
-  T* base = S + o * ((int64_t)L << lo) + g * W;
-  constexpr int per = 16 / sizeof(T);
-  if (W % per == 0) load_block(X, Lp, base, inner, L, W, m, mode != 2);
-  else load_block_elems(X, Lp, base, inner, L, W, m, mode != 2);
-  __syncthreads();
-  if (mode == 2) column_transform<T, true, 1>(X, Lp, W, tw, m, false);
-  else column_transform<T, true, 0>(X, Lp, W, tw, m, mode == 0);
-  const R inv = (R)(1.0 / sqrt((double)L));
-  if (W % per == 0) store_block(base, inner, X, Lp, L, W, inv);
-  else store_block_elems(base, inner, X, Lp, L, W, inv);
+  const int64_t col = blockIdx.x >> CB;
+  const int64_t o = col / groups, g = col - o * groups;
+  T* base = S + o * ((int64_t)1 << (lo + m)) + g * W;
+  load_block(X, Lp, base + (int64_t)rank * Lc * inner, inner, Lc, W);
+  const bool conj = mode == 0;  // QFT: exp(+2 pi i x y / L)
+  if (CB > 0) {
+    cl.sync();
+    if (mode == 2) cross_stages<T, CB, false, 1>(cl, X, (T*)nullptr, Lp, W, tw, m, false);
+    else cross_stages<T, CB, false, 0>(cl, X, (T*)nullptr, Lp, W, tw, m, conj);
+  } else {
+    __syncthreads();
+  }
+  if (mode == 2) local_stages<T, false, 1>(X, Lp, W, tw, m, m_loc, false);
+  else local_stages<T, false, 0>(X, Lp, W, tw, m, m_loc, conj);
+  const R inv = (R)(1.0 / sqrt((double)(1 << m)));
+  if (mode == 2) store_block(base + (int64_t)rank * Lc * inner, inner, X, Lp, Lc, W, inv, false, rank, m);
+  else store_block(base, inner, X, Lp, Lc, W, inv, true, rank, m);
 }
 
 template <class R>
-size_t fft_smem(int m, int W, int buffers) {
+size_t fft_smem(int m, int cb, int W, int buffers) {
   const size_t sz = sizeof(typename Cx<R>::T);
-  const size_t L = (size_t)1 << m, Lp = L + L / 16;
-  return L / 2 * sz + (size_t)buffers * W * Lp * sz;
+  const size_t Lc = (size_t)1 << (m - cb), Lp = Lc + Lc / 16 + 1;
+  return (size_t)twiddle_entries(m) * sz + (size_t)buffers * W * Lp * sz;
 }
 
+// Pick the block width W and the smallest cluster (<= 8 CTAs) whose shared memory fits the
+// target (else the cap).
 template <class R>
+bool choose_shape(int m, int64_t limit, int buffers, int* W_out, int* cb_out, size_t* smem_out) {
+  // 32-byte row segments (W = 4 complex64 / 2 complex128): measured best on GB300 for the
+  // 12- and 13-qubit clocks; wider blocks need larger clusters, whose barriers cost more.
+  int W = (int)std::min<int64_t>(32 / (int)sizeof(typename Cx<R>::T), limit);
+  // tuning override "W,cb" (both powers of two; used when it fits the shared-memory cap)
+  if (const char* env = getenv("HHL_FFT_SHAPE")) {
+    int w = 0, c = -1;
+    if (sscanf(env, "%d,%d", &w, &c) == 2 && w >= 1 && w <= W && (w & (w - 1)) == 0 && c >= 0 && c <= 3 && c < m &&
+        fft_smem<R>(m, c, w, buffers) <= kFftSmemCap) {
+      *W_out = w;
+      *cb_out = c;
+      *smem_out = fft_smem<R>(m, c, w, buffers);
+      return true;
+    }
+  }
+  for (size_t cap : {kFftSmemTarget, kFftSmemCap}) {
+    for (int cb = 0; cb <= 3 && cb < m; ++cb) {
+      if (fft_smem<R>(m, cb, W, buffers) <= cap) {
+        *W_out = W;
+        *cb_out = cb;
+        *smem_out = fft_smem<R>(m, cb, W, buffers);
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+template <class Kern>
+hhl_status launch_cluster(Kern kernel, int grid, int cb, size_t smem, cudaStream_t st, const char* name,
+                          void** args) {
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kFftThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1u << cb;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HHL_PROF_BEGIN(st);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (g_prof_on.load(std::memory_order_relaxed)) prof_end(name);
+    return cuda_fail(e, name);
+  }
+  HHL_LAUNCH_CHECK(name);
+  return HHL_OK;
+}
+
+template <class R, bool FULL>
 hhl_status clock_block_impl(const Plan& p, void* state, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  const int bufs = p.full ? 2 : 1;
-  const int per = 16 / (int)sizeof(T);
-  int W = 8;
-  while (W > per && (W > p.N || fft_smem<R>(p.n_c, W, bufs) > kFftSmemCap)) W >>= 1;
-  if (W > p.N) return fail(HHL_ERR_UNSUPPORTED, "system register narrower than one 16-byte unit");
-  const size_t smem = fft_smem<R>(p.n_c, W, bufs);
-  if (smem > kFftSmemCap) return fail(HHL_ERR_UNSUPPORTED, "clock register too large for one shared-memory block");
-  const int grid = (int)(p.N / W);
-  if (p.full) {
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HHL_PROF_BEGIN(st);
-    k_clock_block<R, true><<<grid, kFftThreads, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
-  } else {
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_clock_block<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HHL_PROF_BEGIN(st);
-    k_clock_block<R, false><<<grid, kFftThreads, smem, st>>>((T*)state, (const T*)p.d_rot, p.n_s, p.n_c, W);
+  int W = 0, cb = 0;
+  size_t smem = 0;
+  if (!choose_shape<R>(p.n_c, p.N, FULL ? 2 : 1, &W, &cb, &smem))
+    return fail(HHL_ERR_UNSUPPORTED, "clock register too large for one cluster");
+  constexpr int per = 16 / sizeof(T);
+  if (W % per != 0) return fail(HHL_ERR_UNSUPPORTED, "system register narrower than one 16-byte unit");
+  const int grid = (int)((p.N / W) << cb);
+  T* S = (T*)state;
+  const T* rot = (const T*)p.d_rot;
+  int n_s = p.n_s, n_c = p.n_c;
+  void* args[] = {&S, &rot, &n_s, &n_c, &W};
+  switch (cb) {
+    case 0: return launch_cluster(k_clock_block<R, FULL, 0>, grid, cb, smem, st, "k_clock_block", args);
+    case 1: return launch_cluster(k_clock_block<R, FULL, 1>, grid, cb, smem, st, "k_clock_block", args);
+    case 2: return launch_cluster(k_clock_block<R, FULL, 2>, grid, cb, smem, st, "k_clock_block", args);
+    default: return launch_cluster(k_clock_block<R, FULL, 3>, grid, cb, smem, st, "k_clock_block", args);
   }
-  HHL_LAUNCH_CHECK("k_clock_block");
-  return HHL_OK;
 }
 
 template <class R>
 hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  const int64_t inner = 1LL << lo;
-  const int per = 16 / (int)sizeof(T);
-  int W = 8;
-  while (W > 1 && (W > inner || (W > per && fft_smem<R>(m, W, 1) > kFftSmemCap))) W >>= 1;
-  (void)per;
-  const size_t smem = fft_smem<R>(m, W, 1);
-  if (smem > kFftSmemCap) return fail(HHL_ERR_UNSUPPORTED, "register too large for one shared-memory block");
+  int W = 0, cb = 0;
+  size_t smem = 0;
+  if (!choose_shape<R>(m, 1LL << lo, 1, &W, &cb, &smem))
+    return fail(HHL_ERR_UNSUPPORTED, "register too large for one cluster");
   const int64_t cols = (1LL << (n - m)) / W;
-  if (cols > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
-  HHL_CUDA_TRY(cudaFuncSetAttribute(k_register_transform<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  HHL_PROF_BEGIN(st);
-  k_register_transform<R><<<(int)cols, kFftThreads, smem, st>>>((T*)state, lo, m, W, mode);
-  HHL_LAUNCH_CHECK("k_register_transform");
-  return HHL_OK;
+  if ((cols << cb) > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
+  const int grid = (int)(cols << cb);
+  T* S = (T*)state;
+  void* args[] = {&S, &lo, &m, &W, &mode};
+  switch (cb) {
+    case 0: return launch_cluster(k_register_transform<R, 0>, grid, cb, smem, st, "k_register_transform", args);
+    case 1: return launch_cluster(k_register_transform<R, 1>, grid, cb, smem, st, "k_register_transform", args);
+    case 2: return launch_cluster(k_register_transform<R, 2>, grid, cb, smem, st, "k_register_transform", args);
+    default: return launch_cluster(k_register_transform<R, 3>, grid, cb, smem, st, "k_register_transform", args);
+  }
 }
 
 }  // namespace
 
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
-  return p.prec == HHL_PREC_C64 ? clock_block_impl<float>(p, state, st) : clock_block_impl<double>(p, state, st);
+  if (p.prec == HHL_PREC_C64)
+    return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
+  return p.full ? clock_block_impl<double, true>(p, state, st) : clock_block_impl<double, false>(p, state, st);
 }
 
 hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {

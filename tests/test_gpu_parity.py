@@ -50,7 +50,8 @@ def _half(psi, n_s, n_c, anc):
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("flow,n_s,n_c,rule", [("poiseuille", 4, 6, "power_law"),   # the 11-qubit Poiseuille case
                                                ("couette", 7, 8, "range_fill"),
-                                               ("poiseuille", 5, 3, "range_fill")])
+                                               ("poiseuille", 5, 3, "range_fill"),
+                                               ("couette", 3, 12, "range_fill")])   # cluster-split clock
 def test_stagewise_parity(hhl, prec, full, flow, n_s, n_c, rule):
     import torch
     diag, off, b, walls = problem(flow, n_s)
@@ -341,3 +342,42 @@ def test_tcgen05_matches_simt_gemm(hhl):
         plan.apply_stage("qpe_u", st)
         outs.append(_np(st))
     assert np.abs(outs[0] - outs[1]).max() < 5e-6
+
+
+@pytest.mark.slow
+def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
+    """The 32-qubit Poiseuille workload (N = 2^18, n_c = 13, complex64, Strang-Trotter U_k, the
+    bench's step bounds). After the controlled products, clock row 0 still holds
+    bhat / 2^(n_c/2) and clock row 2^k holds U_k bhat / 2^(n_c/2); the oracle computes each
+    sampled U_k bhat with its own gate sequence on one system vector."""
+    import torch
+    from synth_inputs import rhs
+    n_s, n_c = 18, 13
+    N, R = 1 << n_s, 1 << n_c
+    diag, off = o.laplacian_tridiag(N)
+    b = rhs("poiseuille", N)
+    dt, r_max = 1024.0, 8
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64", expm="trotter", trotter_dt=dt, trotter_steps_max=r_max)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_stage("qpe_u", st)
+    torch.cuda.synchronize()
+    lub = 4.0 * (N + 1) ** 2
+    t0 = plan.info["t0"]
+    bhat = b / np.linalg.norm(b) / math.sqrt(R)
+    np.testing.assert_allclose(_np(st[:N]), bhat, rtol=1e-6, atol=0)
+    for k in (0, 4, 9, 11, 12):
+        t_k = t0 * (1 << k) / R
+        r = o.trotter_steps(t_k, dt, r_max)
+        psi = np.zeros(2 * N, dtype=np.complex128)
+        psi[N:] = bhat
+        o.apply_trotter_controlled(psi, n_s + 1, n_s, n_s, diag / lub, off / lub, t_k, r)
+        got = _np(st[(1 << k) * N:((1 << k) + 1) * N])
+        ref = psi[N:]
+        assert np.abs(got - ref).max() <= 1e-5
+        assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-4, k
+    out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
+    plan.measure_async(st, out)          # p_success is 0 before the inversion: read the norm only
+    assert out[2].item() == pytest.approx(1.0, abs=1e-4)
+    del st
+    torch.cuda.empty_cache()
