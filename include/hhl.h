@@ -123,6 +123,7 @@ typedef struct hhl_params {
   double trotter_dt;         /* Strang step bound: r_k = clamp(ceil(t_k / dt), 1, max) */
   int32_t trotter_steps_max; /* 0 = no cap */
   int32_t gemm_impl;         /* hhl_gemm_impl */
+  double t0_scale;           /* multiplies the T0 of the rule (0 or 1: unchanged) */
 } hhl_params;
 
 typedef struct hhl_plan_info {
@@ -222,6 +223,48 @@ hhl_status hhl_dissipation_async(hhl_plan_t plan, const void* state_dev, double*
 /* Synchronous form: *eps_out (HOST); if u_host != NULL also the N velocities (HOST). */
 hhl_status hhl_dissipation(hhl_plan_t plan, const void* state_dev, double* eps_out,
                            double* u_host, void* stream);
+
+/* ---------------------------------------------------------------------------------- batch
+ * Many HHL instances of uneven size in one CUDA graph (growth direction of the path: the
+ * paper's sweeps over T0, clock count and system size, Sec. VI, run as one batch). Every
+ * instance is the circuit of hhl_apply_circuit (complex64, postselect-early uncompute)
+ * followed by the readouts of hhl_measure_async and hhl_dissipation_async; A must be a
+ * Toeplitz tridiagonal matrix, because U_k is generated just in time from its analytic
+ * eigenbasis (U_k[n][m] = g_k(|n-m|) - g_k(n+m), an O(N^2) FP64 kernel per k) instead of
+ * being stored. */
+typedef struct hhl_batch_s* hhl_batch_t;
+
+typedef struct hhl_batch_info {
+  int32_t count;            /* instances */
+  int32_t streams;          /* worker streams of the graph */
+  uint64_t state_bytes;     /* all instance states (device) */
+  uint64_t workspace_bytes; /* per-stream operand and row buffers (device) */
+  double gemm_flops;        /* algorithmic flops of all controlled products of one run */
+  uint64_t graph_launches;  /* kernels in the graph (0 before the first run) */
+  int64_t b_doubles;        /* length of the packed right-hand-side array */
+  int64_t out_doubles;      /* length of the packed measurement array */
+} hhl_batch_info;
+
+/* probs[count], params[count] (HOST, read during the call). gemm_choice[count] (HOST, may be
+ * NULL): 0 = CUDA-core GEMM, 128 / 256 = tcgen05 GEMM with that tile width (ignored where the
+ * tile does not fit); NULL picks by size. streams: worker streams (<= 0: 8). Instances are
+ * assigned to streams by decreasing GEMM work. Allocates every state and workspace. */
+hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, int32_t count,
+                            const int32_t* gemm_choice, int32_t streams, hhl_batch_t* out);
+void hhl_batch_destroy(hhl_batch_t batch);
+hhl_status hhl_batch_get_info(hhl_batch_t batch, hhl_batch_info* info);
+/* Per instance: register sizes, chosen GEMM, offsets into the packed arrays, T0. */
+hhl_status hhl_batch_instance(hhl_batch_t batch, int32_t index, int32_t* n_sys_qubits, int32_t* n_clock,
+                              int32_t* gemm, int64_t* b_offset, int64_t* out_offset, double* t0);
+/* Run every instance. b_dev: DEVICE packed complex128 right-hand sides (instance i at its
+ * b_offset, N_i complex values). out_dev: DEVICE packed blocks of 4 + 2 N_i doubles in the
+ * layout of hhl_measure_async; eps_dev: DEVICE count doubles (dissipation). The first call
+ * captures the graph (so it must not itself be inside a stream capture); later calls replay
+ * it with one launch. Asynchronous on stream. */
+hhl_status hhl_batch_run(hhl_batch_t batch, const double* b_dev, double* out_dev, double* eps_dev, void* stream);
+/* As hhl_batch_run with HOST arrays (copies in and out on the stream, then synchronises). */
+hhl_status hhl_batch_run_host(hhl_batch_t batch, const double* b_host, double* out_host, double* eps_host,
+                              void* stream);
 
 /* Fused gate block: QFT (inverse = 0) or inverse QFT (inverse = 1) on the m-qubit
  * register of bits [lo, lo + m) of an n-qubit state, in place (the QFT / IQFT subroutine

@@ -13,7 +13,7 @@ import numpy as np
 from . import _ffi
 from ._ffi import HHLError, check, load
 
-__all__ = ["HHLPlan", "HHLError", "load", "apply_qft", "kernel_launch_count", "laplacian",
+__all__ = ["HHLPlan", "HHLBatch", "HHLError", "load", "apply_qft", "kernel_launch_count", "laplacian",
            "profile_enable", "profile_reset", "profile_read"]
 
 _PREC = {"c64": _ffi.PREC_C64, "c128": _ffi.PREC_C128}
@@ -214,3 +214,106 @@ def apply_qft(state, n_qubits: int, lo: int, m: int, inverse: bool, stream=None)
     prec = _ffi.PREC_C64 if state.dtype == torch.complex64 else _ffi.PREC_C128
     check(load().hhl_apply_qft(ctypes.c_void_p(state.data_ptr()), n_qubits, lo, m, int(inverse), prec,
                                ctypes.c_void_p(_stream_handle(stream))), "hhl_apply_qft")
+
+
+class HHLBatch:
+    """An hhl_batch_t: many uneven instances (Toeplitz tridiagonal A, complex64) run as one
+    CUDA graph. ``problems``: dicts with n_sys_qubits, n_clock, diag, off and optionally nu,
+    walls, t0_rule, t0, t0_convention, t0_scale, C. ``gemm_choice``: per instance 0 (CUDA
+    cores), 128 or 256 (tcgen05 tile width), or None for the library's size rule."""
+
+    def __init__(self, problems: list, gemm_choice=None, streams: int = 8):
+        lib = load()
+        self._lib = lib
+        n = len(problems)
+        probs = (_ffi.Problem * n)()
+        pars = (_ffi.Params * n)()
+        keep = []
+        for i, pr in enumerate(problems):
+            d = np.ascontiguousarray(pr["diag"], dtype=np.float64)
+            o = np.ascontiguousarray(pr["off"], dtype=np.float64)
+            keep += [d, o]
+            probs[i].kind = _ffi.MATRIX_TRIDIAG
+            probs[i].n_sys_qubits = pr["n_sys_qubits"]
+            probs[i].diag = _dptr(d)
+            probs[i].off = _dptr(o)
+            probs[i].nu = pr.get("nu", 0.1)
+            probs[i].wall_lo, probs[i].wall_hi = pr.get("walls", (0.0, 0.0))
+            lib.hhl_params_default(ctypes.byref(pars[i]))
+            pars[i].n_clock = pr["n_clock"]
+            pars[i].t0_rule = _RULE[pr.get("t0_rule", "power_law")]
+            pars[i].t0 = pr.get("t0", 0.0)
+            pars[i].t0_convention = _CONV[pr.get("t0_convention", "total")]
+            pars[i].t0_scale = pr.get("t0_scale", 1.0)
+            pars[i].C = pr.get("C", 0.0)
+            pars[i].precision = _ffi.PREC_C64
+        choice = None
+        if gemm_choice is not None:
+            choice = (ctypes.c_int32 * n)(*[int(c) for c in gemm_choice])
+        h = ctypes.c_void_p()
+        check(lib.hhl_batch_create(probs, pars, n, choice, streams, ctypes.byref(h)), "hhl_batch_create")
+        self._h = h
+        self.count = n
+        self.instances = []
+        for i in range(n):
+            ns, nc, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            bo, oo, t0 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+            check(lib.hhl_batch_instance(h, i, ctypes.byref(ns), ctypes.byref(nc), ctypes.byref(g), ctypes.byref(bo),
+                                         ctypes.byref(oo), ctypes.byref(t0)), "hhl_batch_instance")
+            self.instances.append(dict(n_s=ns.value, n_c=nc.value, gemm=g.value, b_offset=bo.value,
+                                       out_offset=oo.value, t0=t0.value, N=1 << ns.value))
+        del keep
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hhl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        inf = _ffi.BatchInfo()
+        check(self._lib.hhl_batch_get_info(self._h, ctypes.byref(inf)), "hhl_batch_get_info")
+        return {name: getattr(inf, name) for name, _ in _ffi.BatchInfo._fields_}
+
+    def pack_rhs(self, bs: list) -> np.ndarray:
+        """Packed complex128 (as interleaved float64) right-hand sides in instance order."""
+        out = np.zeros(self.info["b_doubles"], dtype=np.float64)
+        for inst, b in zip(self.instances, bs):
+            z = np.asarray(b, dtype=np.complex128)
+            o = inst["b_offset"]
+            out[o:o + 2 * inst["N"]:2] = z.real
+            out[o + 1:o + 2 * inst["N"]:2] = z.imag
+        return out
+
+    def unpack(self, out: np.ndarray) -> list:
+        """Per instance dict(p_success, p_anc1, norm, b_norm, xhat) from a packed result array."""
+        res = []
+        for inst in self.instances:
+            o, n = inst["out_offset"], inst["N"]
+            blk = out[o:o + 4 + 2 * n]
+            res.append(dict(p_success=blk[0], p_anc1=blk[1], norm=blk[2], b_norm=blk[3],
+                            xhat=blk[4::2] + 1j * blk[5::2]))
+        return res
+
+    def run(self, b_dev, out_dev, eps_dev, stream=None) -> None:
+        """Device arrays (torch float64): packed b, packed results, dissipation per instance."""
+        check(self._lib.hhl_batch_run(self._h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(out_dev.data_ptr()),
+                                      ctypes.c_void_p(eps_dev.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
+              "hhl_batch_run")
+
+    def run_host(self, b_packed, stream=None):
+        """Host arrays: packed b in (numpy or pinned torch float64); returns (packed results, eps)."""
+        inf = self.info
+        out = np.zeros(inf["out_doubles"], dtype=np.float64)
+        eps = np.zeros(self.count, dtype=np.float64)
+        bp = b_packed.data_ptr() if hasattr(b_packed, "data_ptr") else np.ascontiguousarray(b_packed).ctypes.data
+        check(self._lib.hhl_batch_run_host(self._h, ctypes.c_void_p(bp), ctypes.c_void_p(out.ctypes.data),
+                                           ctypes.c_void_p(eps.ctypes.data), ctypes.c_void_p(_stream_handle(stream))),
+              "hhl_batch_run_host")
+        return out, eps

@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n_clock", c_int32), ("t0_rule", c_int32), ("t0_convention", c_int32),
                 ("precision", c_int32), ("t0", c_double), ("C", c_double), ("expm_mode", c_int32),
                 ("full_uncompute", c_int32), ("trotter_dt", c_double), ("trotter_steps_max", c_int32),
-                ("gemm_impl", c_int32)]
+                ("gemm_impl", c_int32), ("t0_scale", c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -43,6 +43,12 @@ class PlanInfo(ctypes.Structure):
                 ("kappa", c_double), ("t0", c_double), ("C", c_double), ("state_bytes", c_uint64),
                 ("table_bytes", c_uint64), ("workspace_bytes", c_uint64), ("gemm_flops", c_double),
                 ("trotter_passes", c_int64), ("plan_seconds", c_double)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", c_int32), ("streams", c_int32), ("state_bytes", c_uint64), ("workspace_bytes", c_uint64),
+                ("gemm_flops", c_double), ("graph_launches", c_uint64), ("b_doubles", c_int64),
+                ("out_doubles", c_int64)]
 
 
 class Measurement(ctypes.Structure):
@@ -67,6 +73,13 @@ SIGNATURES = [
     ("hhl_measure", c_int32, [c_void_p, c_void_p, POINTER(Measurement), c_void_p, c_void_p]),
     ("hhl_dissipation_async", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_dissipation", c_int32, [c_void_p, c_void_p, _DP, c_void_p, c_void_p]),
+    ("hhl_batch_create", c_int32, [POINTER(Problem), POINTER(Params), c_int32, c_void_p, c_int32, POINTER(c_void_p)]),
+    ("hhl_batch_destroy", None, [c_void_p]),
+    ("hhl_batch_get_info", c_int32, [c_void_p, POINTER(BatchInfo)]),
+    ("hhl_batch_instance", c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
+                                     POINTER(c_int64), POINTER(c_int64), POINTER(c_double)]),
+    ("hhl_batch_run", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_batch_run_host", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_apply_qft", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
     ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),

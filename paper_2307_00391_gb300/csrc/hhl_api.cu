@@ -67,6 +67,11 @@ void prof_resolve() {
 }  // namespace
 
 void prof_begin(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    t_begin_ev = nullptr;  // launches captured into a graph are timed as a whole by the caller
+    return;
+  }
   t_begin_ev = pooled_event();
   t_begin_st = st;
   if (t_begin_ev) cudaEventRecord(t_begin_ev, st);
@@ -282,7 +287,91 @@ hhl_status eigen_of(const hhl_problem* pr, bool need_vectors, Plan& p, Eigen& eg
   return HHL_OK;
 }
 
+// Host part of the plan (a0): register sizes, lambda_ub, eigenvalues (and eigenvectors when
+// asked), kappa, T0, C and the rotation angles.
+hhl_status plan_host(const hhl_problem* prob, const hhl_params* params, Plan& p, Eigen& eg, bool need_vectors) {
+  p.n_s = prob->n_sys_qubits;
+  p.n_c = params->n_clock;
+  p.n = p.n_s + p.n_c + 1;
+  p.N = 1LL << p.n_s;
+  p.R = 1LL << p.n_c;
+  p.prec = params->precision;
+  p.expm_mode = params->expm_mode;
+  p.full = params->full_uncompute ? 1 : 0;
+  p.nu = prob->nu;
+  p.wall_lo = prob->wall_lo;
+  p.wall_hi = prob->wall_hi;
+  p.trotter_dt = params->trotter_dt;
+  p.trotter_max = params->trotter_steps_max;
+  cudaGetDevice(&p.device);
+
+  // lambda_ub: Gershgorin bound max_i sum_j |A_ij|
+  const int64_t N = p.N;
+  double lub = 0.0;
+  if (prob->kind == HHL_MATRIX_TRIDIAG) {
+    for (int64_t i = 0; i < N; ++i) {
+      double r = fabs(prob->diag[i]);
+      if (i > 0) r += fabs(prob->off[i - 1]);
+      if (i + 1 < N) r += fabs(prob->off[i]);
+      lub = std::max(lub, r);
+    }
+  } else {
+    for (int64_t i = 0; i < N; ++i) {
+      double r = 0.0;
+      for (int64_t j = 0; j < N; ++j) r += std::hypot(prob->dense_re[i * N + j], prob->dense_im ? prob->dense_im[i * N + j] : 0.0);
+      lub = std::max(lub, r);
+    }
+  }
+  if (!(lub > 0.0)) { return fail(HHL_ERR_SINGULAR, "A is zero"); }
+  p.lam_ub = lub;
+
+  const bool dense = p.expm_mode == HHL_EXPM_DENSE;
+  if (!dense && !(prob->kind == HHL_MATRIX_TRIDIAG && is_toeplitz(prob->diag, prob->off, N)))
+    return fail(HHL_ERR_UNSUPPORTED, "Trotter mode needs a Toeplitz tridiagonal A");
+  hhl_status s = eigen_of(prob, dense && need_vectors, p, eg);
+  if (s != HHL_OK) { return s; }
+  double lmin = 1e300, lmax = -1e300, amin = 1e300, amax = 0.0;
+  for (double l : eg.lam) {
+    lmin = std::min(lmin, l);
+    lmax = std::max(lmax, l);
+    amin = std::min(amin, fabs(l));
+    amax = std::max(amax, fabs(l));
+  }
+  if (amin <= 1e-14 * amax) { return fail(HHL_ERR_SINGULAR, "A is singular"); }
+  if (lmin <= 0.0) { return fail(HHL_ERR_UNSUPPORTED, "A must be positive definite (unsigned clock reading)"); }
+  p.lam_min = lmin;
+  p.lam_max = lmax;
+  p.kappa = amax / amin;
+
+  // T0 (total convention) and C
+  switch (params->t0_rule) {
+    case HHL_T0_RANGE_FILL: p.t0 = 2.0 * kPi * (double)(p.R - 1); break;
+    case HHL_T0_POWER_LAW: p.t0 = exp(0.918) * pow(p.kappa, -0.363) * (double)p.R; break;
+    default: p.t0 = params->t0_convention == HHL_T0_PER_UNIT ? params->t0 * (double)p.R : params->t0; break;
+  }
+  if (params->t0_scale > 0.0) p.t0 *= params->t0_scale;
+  p.C = params->C > 0.0 ? params->C : 2.0 * kPi / p.t0;
+  p.theta.assign(p.R, 0.0);
+  for (int64_t y = 1; y < p.R; ++y) {
+    const double lam = 2.0 * kPi * (double)y / p.t0;
+    p.theta[y] = 2.0 * asin(std::min(1.0, p.C / lam));
+  }
+
+  return HHL_OK;
+}
+
 }  // namespace
+
+hhl_status plan_scalars(const hhl_problem* prob, const hhl_params* params, Plan& p,
+                        std::vector<double>* eigenvalues) {
+  hhl_status s = validate(prob, params);
+  if (s != HHL_OK) return s;
+  Eigen eg;
+  s = plan_host(prob, params, p, eg, false);
+  if (s == HHL_OK && eigenvalues) *eigenvalues = eg.lam;
+  return s;
+}
+
 }  // namespace hhl
 
 using hhl::Plan;
@@ -372,74 +461,11 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
 
   hhl_plan_s* h = new hhl_plan_s();
   Plan& p = h->p;
-  p.n_s = prob->n_sys_qubits;
-  p.n_c = params->n_clock;
-  p.n = p.n_s + p.n_c + 1;
-  p.N = 1LL << p.n_s;
-  p.R = 1LL << p.n_c;
-  p.prec = params->precision;
-  p.expm_mode = params->expm_mode;
-  p.full = params->full_uncompute ? 1 : 0;
-  p.nu = prob->nu;
-  p.wall_lo = prob->wall_lo;
-  p.wall_hi = prob->wall_hi;
-  p.trotter_dt = params->trotter_dt;
-  p.trotter_max = params->trotter_steps_max;
-  cudaGetDevice(&p.device);
-
-  // lambda_ub: Gershgorin bound max_i sum_j |A_ij|
-  const int64_t N = p.N;
-  double lub = 0.0;
-  if (prob->kind == HHL_MATRIX_TRIDIAG) {
-    for (int64_t i = 0; i < N; ++i) {
-      double r = fabs(prob->diag[i]);
-      if (i > 0) r += fabs(prob->off[i - 1]);
-      if (i + 1 < N) r += fabs(prob->off[i]);
-      lub = std::max(lub, r);
-    }
-  } else {
-    for (int64_t i = 0; i < N; ++i) {
-      double r = 0.0;
-      for (int64_t j = 0; j < N; ++j) r += std::hypot(prob->dense_re[i * N + j], prob->dense_im ? prob->dense_im[i * N + j] : 0.0);
-      lub = std::max(lub, r);
-    }
-  }
-  if (!(lub > 0.0)) { delete h; return fail(HHL_ERR_SINGULAR, "A is zero"); }
-  p.lam_ub = lub;
-
-  const bool dense = p.expm_mode == HHL_EXPM_DENSE;
-  if (!dense && !(prob->kind == HHL_MATRIX_TRIDIAG && is_toeplitz(prob->diag, prob->off, N))) {
-    delete h;
-    return fail(HHL_ERR_UNSUPPORTED, "Trotter mode needs a Toeplitz tridiagonal A");
-  }
   Eigen eg;
-  s = eigen_of(prob, dense, p, eg);
+  s = plan_host(prob, params, p, eg, true);
   if (s != HHL_OK) { delete h; return s; }
-  double lmin = 1e300, lmax = -1e300, amin = 1e300, amax = 0.0;
-  for (double l : eg.lam) {
-    lmin = std::min(lmin, l);
-    lmax = std::max(lmax, l);
-    amin = std::min(amin, fabs(l));
-    amax = std::max(amax, fabs(l));
-  }
-  if (amin <= 1e-14 * amax) { delete h; return fail(HHL_ERR_SINGULAR, "A is singular"); }
-  if (lmin <= 0.0) { delete h; return fail(HHL_ERR_UNSUPPORTED, "A must be positive definite (unsigned clock reading)"); }
-  p.lam_min = lmin;
-  p.lam_max = lmax;
-  p.kappa = amax / amin;
-
-  // T0 (total convention) and C
-  switch (params->t0_rule) {
-    case HHL_T0_RANGE_FILL: p.t0 = 2.0 * kPi * (double)(p.R - 1); break;
-    case HHL_T0_POWER_LAW: p.t0 = exp(0.918) * pow(p.kappa, -0.363) * (double)p.R; break;
-    default: p.t0 = params->t0_convention == HHL_T0_PER_UNIT ? params->t0 * (double)p.R : params->t0; break;
-  }
-  p.C = params->C > 0.0 ? params->C : 2.0 * kPi / p.t0;
-  p.theta.assign(p.R, 0.0);
-  for (int64_t y = 1; y < p.R; ++y) {
-    const double lam = 2.0 * kPi * (double)y / p.t0;
-    p.theta[y] = 2.0 * asin(std::min(1.0, p.C / lam));
-  }
+  const int64_t N = p.N;
+  const bool dense = p.expm_mode == HHL_EXPM_DENSE;
 
   // device buffers
   cudaStream_t st = nullptr;

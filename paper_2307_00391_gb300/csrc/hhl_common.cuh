@@ -96,10 +96,16 @@ struct Plan {
   size_t amp_bytes() const { return prec == HHL_PREC_C64 ? 8 : 16; }
 };
 
+// Validation and the host part of planning (a0) without device work; the eigenvalues of A
+// are returned when asked (analytic for a Toeplitz tridiagonal A).
+hhl_status plan_scalars(const hhl_problem* prob, const hhl_params* params, Plan& p, std::vector<double>* eigenvalues);
+
 // Launchers (host side of the kernels); all return HHL_OK or an error.
 hhl_status launch_bnorm(const double* b, int64_t N, double* acc, cudaStream_t st);
 hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStream_t st);
 hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+// SIMT controlled product with an explicit operand B[m][n] (U^T forward, conj(U) adjoint).
+hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, cudaStream_t st);
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st);
@@ -118,5 +124,16 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
 void tc_free(Plan& p);
 int* tc_error_flag(const Plan& p);  // device flag set when a bounded wait in the GEMM ran out
+}  // namespace hhl
+#include <cuda.h>
+namespace hhl {
+// The split-TF32 tcgen05 GEMM with explicit operands (row gather + GEMM of one controlled
+// product): bn = 128 or 256 output real columns per CTA; the maps describe a_hi / a_lo
+// (M_sub x 2N) and the embedded operand hi / lo (2N x 2N) with boxes (32 x 128) and (32 x bn).
+hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi, float* a_lo,
+                          const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
+                          const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
+hhl_status tc_make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows);
+hhl_status tc_init_kernels();
 
 }  // namespace hhl

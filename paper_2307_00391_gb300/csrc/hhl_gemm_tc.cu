@@ -32,14 +32,16 @@ namespace hhl {
 namespace {
 
 constexpr int kBM = 128;           // output rows per CTA (MMA M)
-constexpr int kBN = 256;           // output real columns per CTA (MMA N)
+constexpr int kBN = 256;           // output real columns per CTA (MMA N), plan path
 constexpr int kBK = 32;            // fp32 K elements per stage (128 bytes: one swizzle row)
 constexpr int kStages = 2;
 constexpr int kTileA = kBM * kBK * 4;   // 16 KiB
-constexpr int kTileB = kBN * kBK * 4;   // 32 KiB
-constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
-constexpr int kTmemCols = 256;
+template <int BN> struct TcShape {
+  static constexpr int kTileB = BN * kBK * 4;                     // 32 KiB at BN = 256
+  static constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;     // A_hi, A_lo, B_hi, B_lo
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+  static constexpr int kTmemCols = BN;                            // fp32 accumulator columns
+};
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcState {
@@ -148,6 +150,7 @@ __device__ __forceinline__ int64_t row_with_bit_tc(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                    const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
@@ -161,7 +164,9 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const int n0 = blockIdx.x * kBN;   // real output column
+  constexpr int kTileB = TcShape<BN>::kTileB, kStageBytes = TcShape<BN>::kStageBytes;
+  constexpr int kTmemCols = TcShape<BN>::kTmemCols;
+  const int n0 = blockIdx.x * BN;   // real output column
   const int m0 = blockIdx.y * kBM;   // subset row
 
   if (threadIdx.x == 0) {
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = idesc_tf32(kBM, kBN);
+    constexpr uint32_t idesc = idesc_tf32(kBM, BN);
     bool ok = true;
     for (int it = 0; it < k_iters; ++it) {
       const int s = it % kStages;
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(128, 1)
     float* dst = state_half + row_with_bit_tc(i, k) * N2 + n0;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c = 0; c < kBN; c += 32) {
+    for (int c = 0; c < BN; c += 32) {
       float v[32];
       tmem_ld_32cols(lane_addr + c, v);
       float4* d4 = reinterpret_cast<float4*>(dst + c);
@@ -367,7 +372,8 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
       for (int j = 0; j < 4 && s == HHL_OK; ++j)
         s = make_map(&t->maps[2 + 4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, kBN);
     if (s != HHL_OK) return s;
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<kBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TcShape<kBN>::kSmemBytes));
   }
   int g = (int)((mat + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
@@ -380,21 +386,45 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
   const TcState* t = static_cast<const TcState*>(p.d_tc);
   if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
-  const int64_t m_sub = p.R / 2;
-  const int64_t N2 = 2 * p.N;
+  const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
+  return launch_tc_gemm(p.n_s, p.R / 2, k, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], kBN, t->err, st);
+}
+
+hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi, float* a_lo, const CUtensorMap& map_ahi,
+                          const CUtensorMap& map_alo, const CUtensorMap& map_bhi, const CUtensorMap& map_blo, int bn,
+                          int* err, cudaStream_t st) {
+  const int64_t N2 = 2LL << n_s;
   const int64_t total4 = m_sub * N2 / 4;
   int g = (int)((total4 + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
   HHL_PROF_BEGIN(st);
-  k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (float4*)t->a_hi, (float4*)t->a_lo, p.n_s, k, m_sub);
+  k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (float4*)a_hi, (float4*)a_lo, n_s, k, m_sub);
   HHL_LAUNCH_CHECK("k_tc_split_rows");
-  const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
-  dim3 grid((unsigned)(N2 / kBN), (unsigned)(m_sub / kBM));
-  HHL_PROF_BEGIN(st);
-  k_ctrl_gemm_tc<<<grid, 128, kSmemBytes, st>>>(t->maps[0], t->maps[1], mb[0], mb[1], (float*)half, p.n_s, k,
-                                                (int)(N2 / kBK), t->err);
+  if (bn == 256) {
+    dim3 grid((unsigned)(N2 / 256), (unsigned)(m_sub / kBM));
+    HHL_PROF_BEGIN(st);
+    k_ctrl_gemm_tc<256><<<grid, 128, TcShape<256>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
+                                                                     n_s, k, (int)(N2 / kBK), err);
+  } else {
+    dim3 grid((unsigned)(N2 / 128), (unsigned)(m_sub / kBM));
+    HHL_PROF_BEGIN(st);
+    k_ctrl_gemm_tc<128><<<grid, 128, TcShape<128>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
+                                                                     n_s, k, (int)(N2 / kBK), err);
+  }
   HHL_LAUNCH_CHECK("k_ctrl_gemm_tc");
   return HHL_OK;
+}
+
+hhl_status tc_init_kernels() {
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcShape<256>::kSmemBytes));
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcShape<128>::kSmemBytes));
+  return HHL_OK;
+}
+
+hhl_status tc_make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  return make_map(map, base, cols, rows, box_rows);
 }
 
 int* tc_error_flag(const Plan& p) {

@@ -329,22 +329,28 @@ hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStr
 }
 
 hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
+  const size_t mat = (size_t)p.N * p.N;
+  const size_t off = (size_t)k * mat * p.amp_bytes();
+  const void* B = (const char*)(adjoint ? p.d_badj : p.d_bfwd) + off;
+  return launch_ctrl_u_simt(p, half, k, B, st);
+}
+
+hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, cudaStream_t st) {
   const int64_t m_sub = p.R / 2;
   const int64_t N = p.N;
-  const size_t mat = (size_t)N * N;
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((m_sub + 63) / 64));
   const int sg = grid_for(m_sub * N, kThreads, 152 * 32);
   if (p.prec == HHL_PREC_C64) {
-    const float2* B = (const float2*)(adjoint ? p.d_badj : p.d_bfwd) + (size_t)k * mat;
     HHL_PROF_BEGIN(st);
-    k_ctrl_gemm_simt<float, 64, 64, 16><<<grid, 256, 0, st>>>((const float2*)half, (float2*)p.d_scratch, B, p.n_s, k, m_sub);
+    k_ctrl_gemm_simt<float, 64, 64, 16><<<grid, 256, 0, st>>>((const float2*)half, (float2*)p.d_scratch,
+                                                              (const float2*)B, p.n_s, k, m_sub);
     HHL_LAUNCH_CHECK("k_ctrl_gemm_simt<f32>");
     HHL_PROF_BEGIN(st);
     k_rows_scatter<float><<<sg, kThreads, 0, st>>>((float2*)half, (const float2*)p.d_scratch, p.n_s, k, m_sub);
   } else {
-    const double2* B = (const double2*)(adjoint ? p.d_badj : p.d_bfwd) + (size_t)k * mat;
     HHL_PROF_BEGIN(st);
-    k_ctrl_gemm_simt<double, 64, 64, 8><<<grid, 256, 0, st>>>((const double2*)half, (double2*)p.d_scratch, B, p.n_s, k, m_sub);
+    k_ctrl_gemm_simt<double, 64, 64, 8><<<grid, 256, 0, st>>>((const double2*)half, (double2*)p.d_scratch,
+                                                              (const double2*)B, p.n_s, k, m_sub);
     HHL_LAUNCH_CHECK("k_ctrl_gemm_simt<f64>");
     HHL_PROF_BEGIN(st);
     k_rows_scatter<double><<<sg, kThreads, 0, st>>>((double2*)half, (const double2*)p.d_scratch, p.n_s, k, m_sub);
