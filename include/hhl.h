@@ -262,6 +262,10 @@ hhl_status hhl_batch_instance(hhl_batch_t batch, int32_t index, int32_t* n_sys_q
  * captures the graph (so it must not itself be inside a stream capture); later calls replay
  * it with one launch. Asynchronous on stream. */
 hhl_status hhl_batch_run(hhl_batch_t batch, const double* b_dev, double* out_dev, double* eps_dev, void* stream);
+/* The same work enqueued launch by launch on the worker streams instead of replaying the
+ * graph (for per-kernel timing with hhl_profile_*): reads the right-hand sides already in
+ * the batch's device buffer (from the last run) and leaves the results there. */
+hhl_status hhl_batch_run_eager(hhl_batch_t batch, void* stream);
 /* As hhl_batch_run with HOST arrays (copies in and out on the stream, then synchronises). */
 hhl_status hhl_batch_run_host(hhl_batch_t batch, const double* b_host, double* out_host, double* eps_host,
                               void* stream);

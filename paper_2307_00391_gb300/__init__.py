@@ -307,6 +307,10 @@ class HHLBatch:
                                       ctypes.c_void_p(eps_dev.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
               "hhl_batch_run")
 
+    def run_eager(self, stream=None) -> None:
+        """The same work launch by launch (for per-kernel timing), on the inputs of the last run."""
+        check(self._lib.hhl_batch_run_eager(self._h, ctypes.c_void_p(_stream_handle(stream))), "hhl_batch_run_eager")
+
     def run_host(self, b_packed, stream=None):
         """Host arrays: packed b in (numpy or pinned torch float64); returns (packed results, eps)."""
         inf = self.info

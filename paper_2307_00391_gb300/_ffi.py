@@ -79,6 +79,7 @@ SIGNATURES = [
     ("hhl_batch_instance", c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
                                      POINTER(c_int64), POINTER(c_int64), POINTER(c_double)]),
     ("hhl_batch_run", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_batch_run_eager", c_int32, [c_void_p, c_void_p]),
     ("hhl_batch_run_host", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_apply_qft", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),

@@ -38,7 +38,7 @@ constexpr double kPiB = 3.14159265358979323846;
 // g_k(d) for d in [0, 2N+2) and every k: block (x = d chunk, y = k).
 __global__ void __launch_bounds__(256) k_ugen_g(int N, const double2* __restrict__ ph /* n_c x N */,
                                                const double* __restrict__ cos_tab /* 2N+2 */,
-                                               double2* __restrict__ g /* n_c x (2N+2) */) {
+                                               float4* __restrict__ g /* n_c x (2N+2) */) {
   extern __shared__ double2 sh_ph[];
   const int k = blockIdx.y;
   const int M = 2 * N + 2;
@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(256) k_ugen_g(int N, const double2* __restrict
       re = fma(c, p.x, re);
       im = fma(c, p.y, im);
     }
-    g[(size_t)k * M + d] = make_double2(re * inv, im * inv);
+    // double-float (hi + lo) in FP32, so that the expansion below runs in FP32 arithmetic
+    const double gr = re * inv, gi = im * inv;
+    const float rh = (float)gr, ih = (float)gi;
+    g[(size_t)k * M + d] = make_float4(rh, (float)(gr - (double)rh), ih, (float)(gi - (double)ih));
   }
 }
 
@@ -66,33 +69,44 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// U_k[n][m] = g(|n-m|) - g(n+m+2) (0-based n, m) from the double-float table, in FP32: the
+// difference of the high parts is exact for close values and the low parts restore the rest.
+__device__ __forceinline__ float2 u_elem(const float4* __restrict__ g, int n, int m) {
+  const float4 a = g[n > m ? n - m : m - n], b = g[n + m + 2];
+  return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
+}
+
 // Split-TF32 real embedding of U_k (adjoint: U_k^dagger = conj(U_k), A real symmetric):
-// hi / lo (2N x 2N), rows = output real column, columns = input real index.
-__global__ void k_ugen_embed_tc(int N, const double2* __restrict__ g, int adjoint, float* __restrict__ hi,
+// hi / lo (2N x 2N), rows = output real column, columns = input real index. One thread per
+// (n, m) writes the 2 x 2 block [[Re, -Im], [Im, Re]] at rows 2n, 2n+1 and columns 2m, 2m+1.
+__global__ void k_ugen_embed_tc(int n_s, const float4* __restrict__ g, int adjoint, float* __restrict__ hi,
                                 float* __restrict__ lo) {
-  const int64_t N2 = 2LL * N, sz = N2 * N2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sz; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t nr = e / N2, kr = e - nr * N2;
-    const int64_t n = nr >> 1, m = kr >> 1;
-    const int s = (int)(nr & 1), t = (int)(kr & 1);
-    const int64_t dd = n > m ? n - m : m - n;
-    const double2 a = g[dd], b = g[n + m + 2];
-    const double ur = a.x - b.x, ui = adjoint ? -(a.y - b.y) : (a.y - b.y);
-    const double v = s == 0 ? (t == 0 ? ur : -ui) : (t == 0 ? ui : ur);
-    const float h = tf32_rna((float)v);
-    hi[e] = h;
-    lo[e] = tf32_rna((float)(v - (double)h));
+  const int N = 1 << n_s;
+  const int64_t N2 = 2LL * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e >> n_s), m = (int)(e & (N - 1));
+    float2 u = u_elem(g, n, m);
+    if (adjoint) u.y = -u.y;
+    const float hr = tf32_rna(u.x), hi_ = tf32_rna(u.y);
+    const float lr = tf32_rna(u.x - hr), li = tf32_rna(u.y - hi_);
+    const int64_t r0 = (2LL * n) * N2 + 2LL * m, r1 = r0 + N2;
+    *reinterpret_cast<float2*>(hi + r0) = make_float2(hr, -hi_);
+    *reinterpret_cast<float2*>(hi + r1) = make_float2(hi_, hr);
+    *reinterpret_cast<float2*>(lo + r0) = make_float2(lr, -li);
+    *reinterpret_cast<float2*>(lo + r1) = make_float2(li, lr);
   }
 }
 
 // Complex64 operand of the CUDA-core GEMM: B[m][n] = U_k[n][m] (= U_k[m][n]) or conj.
-__global__ void k_ugen_embed_simt(int N, const double2* __restrict__ g, int adjoint, float2* __restrict__ B) {
-  const int64_t sz = (int64_t)N * N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sz; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = e / N, n = e - m * N;
-    const int64_t dd = n > m ? n - m : m - n;
-    const double2 a = g[dd], b = g[n + m + 2];
-    B[e] = make_float2((float)(a.x - b.x), (float)(adjoint ? -(a.y - b.y) : (a.y - b.y)));
+__global__ void k_ugen_embed_simt(int n_s, const float4* __restrict__ g, int adjoint, float2* __restrict__ B) {
+  const int N = 1 << n_s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e >> n_s), n = (int)(e & (N - 1));
+    float2 u = u_elem(g, n, m);
+    if (adjoint) u.y = -u.y;
+    B[e] = u;
   }
 }
 
@@ -134,7 +148,7 @@ struct hhl_batch_s {
   void* d_rot = nullptr;       // packed R complex64 (cos, sin) per instance
   double2* d_ph = nullptr;     // packed n_c x N phases per instance
   double* d_cos = nullptr;     // packed 2N+2 cosines per instance
-  double2* d_g = nullptr;      // packed n_c x (2N+2) per instance
+  float4* d_g = nullptr;       // packed n_c x (2N+2) per instance (double-float)
   int* d_err = nullptr;
   size_t state_bytes = 0, work_bytes = 0;
   double gemm_flops = 0;
@@ -189,20 +203,20 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
   }
   const int M = (int)(2 * p.N + 2);
   auto product = [&](int k, bool adjoint) -> hhl_status {
-    const double2* gk = B->d_g + B->g_off[i] + (size_t)k * M;
+    const float4* gk = B->d_g + B->g_off[i] + (size_t)k * M;
     const int64_t N2 = 2 * p.N;
     if (B->gemm[i] == 0) {
       int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
       HHL_PROF_BEGIN(st);
-      k_ugen_embed_simt<<<g, 256, 0, st>>>((int)p.N, gk, adjoint ? 1 : 0, (float2*)w.ubuf);
+      k_ugen_embed_simt<<<g, 256, 0, st>>>(p.n_s, gk, adjoint ? 1 : 0, (float2*)w.ubuf);
       HHL_LAUNCH_CHECK("k_ugen_embed_simt");
       return launch_ctrl_u_simt(p, adjoint ? (void*)s1 : (void*)s0, k, w.ubuf, st);
     }
     float* hi = (float*)w.ubuf;
     float* lo = hi + N2 * N2;
-    int g = (int)std::min<int64_t>((N2 * N2 + 255) / 256, 152 * 16);
+    int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
     HHL_PROF_BEGIN(st);
-    k_ugen_embed_tc<<<g, 256, 0, st>>>((int)p.N, gk, adjoint ? 1 : 0, hi, lo);
+    k_ugen_embed_tc<<<g, 256, 0, st>>>(p.n_s, gk, adjoint ? 1 : 0, hi, lo);
     HHL_LAUNCH_CHECK("k_ugen_embed_tc");
     const CUtensorMap* mp = &B->maps[(size_t)i * 4];
     return launch_tc_gemm(p.n_s, p.R / 2, k, adjoint ? (void*)s1 : (void*)s0, w.a_hi, w.a_lo, mp[0], mp[1], mp[2],
@@ -345,7 +359,7 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
             alloc((void**)&B->d_scal, (size_t)count * 16 * sizeof(double)) &&
             alloc(&B->d_bs, (bo / 2) * sizeof(float2)) && alloc(&B->d_rot, ro * sizeof(float2)) &&
             alloc((void**)&B->d_ph, po * sizeof(double2)) && alloc((void**)&B->d_cos, co * sizeof(double)) &&
-            alloc((void**)&B->d_g, go * sizeof(double2)) && alloc((void**)&B->d_err, sizeof(int));
+            alloc((void**)&B->d_g, go * sizeof(float4)) && alloc((void**)&B->d_err, sizeof(int));
   for (auto& w : B->work) {
     if (!ok) break;
     const int64_t N2 = 2 * w.capN;
@@ -473,6 +487,24 @@ hhl_status hhl_batch_run(hhl_batch_t b, const double* b_dev, double* out_dev, do
   HHL_CUDA_TRY(cudaMemcpyAsync(out_dev, b->d_out, oo * sizeof(double), cudaMemcpyDeviceToDevice, st));
   HHL_CUDA_TRY(cudaMemcpyAsync(eps_dev, b->d_eps, b->count * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return HHL_OK;
+}
+
+hhl_status hhl_batch_run_eager(hhl_batch_t b, void* stream) {
+  using namespace hhl;
+  if (b == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t fork = nullptr;
+  HHL_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  HHL_CUDA_TRY(cudaEventRecord(fork, st));
+  for (auto& w : b->work) HHL_CUDA_TRY(cudaStreamWaitEvent(w.s, fork, 0));
+  hhl_status s = HHL_OK;
+  for (int i = 0; i < b->count && s == HHL_OK; ++i) s = enqueue_instance(b, i);
+  for (auto& w : b->work) {
+    HHL_CUDA_TRY(cudaEventRecord(w.done, w.s));
+    HHL_CUDA_TRY(cudaStreamWaitEvent(st, w.done, 0));
+  }
+  cudaEventDestroy(fork);
+  return s;
 }
 
 hhl_status hhl_batch_run_host(hhl_batch_t b, const double* b_host, double* out_host, double* eps_host, void* stream) {

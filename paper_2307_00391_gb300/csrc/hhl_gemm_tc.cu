@@ -24,6 +24,7 @@
 // (read back as HHL_ERR_TIMEOUT), skips the remaining work, frees its TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <stdlib.h>
 
 #include "hhl_common.cuh"
 
@@ -49,6 +50,7 @@ struct TcState {
   float* a_lo = nullptr;
   float* b = nullptr;     // n_c x {fwd_hi, fwd_lo, adj_hi, adj_lo} x (2N x 2N)
   int* err = nullptr;     // device error flag
+  int bn = kBN;           // output tile width (128 or 256)
   std::vector<CUtensorMap> maps;  // [0] A_hi, [1] A_lo, then per k: fwd_hi, fwd_lo, adj_hi, adj_lo
 };
 
@@ -365,15 +367,18 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
     p.workspace_bytes += 2 * abytes;
     p.table_bytes += (size_t)p.n_c * 4 * mat * sizeof(float);
     HHL_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), st));
+    // tile width: 256 unless HHL_TC_BN=128 (tuning) or the operand is narrower
+    if (const char* env = getenv("HHL_TC_BN")) t->bn = atoi(env) == 128 ? 128 : 256;
+    if (N2 < t->bn) t->bn = 128;
     t->maps.resize(2 + 4 * (size_t)p.n_c);
     hhl_status s = make_map(&t->maps[0], t->a_hi, N2, p.R / 2, kBM);
     if (s == HHL_OK) s = make_map(&t->maps[1], t->a_lo, N2, p.R / 2, kBM);
     for (int kk = 0; kk < p.n_c && s == HHL_OK; ++kk)
       for (int j = 0; j < 4 && s == HHL_OK; ++j)
-        s = make_map(&t->maps[2 + 4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, kBN);
+        s = make_map(&t->maps[2 + 4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, t->bn);
     if (s != HHL_OK) return s;
-    HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<kBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TcShape<kBN>::kSmemBytes));
+    s = tc_init_kernels();
+    if (s != HHL_OK) return s;
   }
   int g = (int)((mat + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
@@ -387,7 +392,7 @@ hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cuda
   const TcState* t = static_cast<const TcState*>(p.d_tc);
   if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
   const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
-  return launch_tc_gemm(p.n_s, p.R / 2, k, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], kBN, t->err, st);
+  return launch_tc_gemm(p.n_s, p.R / 2, k, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn, t->err, st);
 }
 
 hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi, float* a_lo, const CUtensorMap& map_ahi,
