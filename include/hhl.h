@@ -270,6 +270,37 @@ hhl_status hhl_batch_run_eager(hhl_batch_t batch, void* stream);
 hhl_status hhl_batch_run_host(hhl_batch_t batch, const double* b_host, double* out_host, double* eps_host,
                               void* stream);
 
+/* ------------------------------------------------------------------- learned T0 predictor
+ * A 6 -> 128 -> 128 -> 2 perceptron (tanh hidden layers) that maps features of the linear
+ * system and the clock budget (kappa, N, the eigenvalue bounds and Q_PE that Sec. VI relates
+ * to the optimal simulation time T0*) to (log of T0* over the power-law value, recommended
+ * clock count), both standardised by the caller. BF16 weights with FP32 accumulation;
+ * trained on the GPU by these entry points (forward, mean-squared-error loss, backward,
+ * Adam). The parameter vector (HHL_MLP_PARAMS floats, host) is W1[128][6], b1[128],
+ * W2[128][128], b2[128], W3[2][128], b3[2]. */
+#define HHL_MLP_IN 6
+#define HHL_MLP_HIDDEN 128
+#define HHL_MLP_OUT 2
+#define HHL_MLP_PARAMS 17666
+typedef struct hhl_mlp_s* hhl_mlp_t;
+hhl_status hhl_mlp_create(hhl_mlp_t* out);  /* parameters zero until hhl_mlp_set_params */
+void hhl_mlp_destroy(hhl_mlp_t mlp);
+/* Set the FP32 master parameters (HOST), reset the Adam state, refresh the BF16 copy. */
+hhl_status hhl_mlp_set_params(hhl_mlp_t mlp, const float* host_params, void* stream);
+hhl_status hhl_mlp_get_params(hhl_mlp_t mlp, float* host_params, void* stream);
+/* y_dev[rows][2] = network(x_dev[rows][6]) (DEVICE, FP32). */
+hhl_status hhl_mlp_forward(hhl_mlp_t mlp, const float* x_dev, int32_t rows, float* y_dev, void* stream);
+/* The same network as the T0 predictor of the plan stage (features, outputs as above). */
+hhl_status hhl_t0_predict(hhl_mlp_t mlp, const float* features_dev, int32_t rows, float* out_dev, void* stream);
+/* Gradient of loss = mean((y - t)^2) over rows and outputs with respect to the parameters
+ * (through the BF16 weights): grad_dev[HHL_MLP_PARAMS], loss_dev[1] (DEVICE). */
+hhl_status hhl_mlp_gradients(hhl_mlp_t mlp, const float* x_dev, const float* t_dev, int32_t rows, float* grad_dev,
+                             float* loss_dev, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on that loss; loss_dev[1]
+ * receives the loss before the step. */
+hhl_status hhl_mlp_train_step(hhl_mlp_t mlp, const float* x_dev, const float* t_dev, int32_t rows, float lr,
+                              float* loss_dev, void* stream);
+
 /* Fused gate block: QFT (inverse = 0) or inverse QFT (inverse = 1) on the m-qubit
  * register of bits [lo, lo + m) of an n-qubit state, in place (the QFT / IQFT subroutine
  * of the algorithm library, App. B; the circuit of the Fig. 1c scaling experiment).

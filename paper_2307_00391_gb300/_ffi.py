@@ -81,6 +81,14 @@ SIGNATURES = [
     ("hhl_batch_run", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_batch_run_eager", c_int32, [c_void_p, c_void_p]),
     ("hhl_batch_run_host", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_mlp_create", c_int32, [POINTER(c_void_p)]),
+    ("hhl_mlp_destroy", None, [c_void_p]),
+    ("hhl_mlp_set_params", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("hhl_mlp_get_params", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("hhl_mlp_forward", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    ("hhl_t0_predict", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    ("hhl_mlp_gradients", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    ("hhl_mlp_train_step", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float, c_void_p, c_void_p]),
     ("hhl_apply_qft", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
     ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),

@@ -420,3 +420,35 @@ def test_stage_cuts_reproduce_whole_circuit():
                off=off / o.gershgorin_bound(o.dense_from_tridiag(diag, off)), dt=2.0, r_max=5)
     st2 = run_stages(b, 4, pl, trotter=tro)
     np.testing.assert_allclose(st2["final_h"], o.hhl_circuit(b, 4, pl, trotter=tro), atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- T0 network
+
+
+def test_mlp_oracle_gradient_matches_central_differences():
+    from oracle import mlp_oracle as m
+    rng = np.random.default_rng(12)
+    p = rng.standard_normal(m.N_PARAMS) * 0.2
+    x = rng.standard_normal((5, 6))
+    t = rng.standard_normal((5, 2))
+    loss, g = m.loss_and_grad(p, x, t)
+    idx = rng.choice(m.N_PARAMS, 60, replace=False)
+    idx = np.concatenate([idx, [0, 767, 768, 895, 896, 17279, 17280, 17407, 17408, 17663, 17664, 17665]])
+    for i in idx:
+        e = np.zeros(m.N_PARAMS)
+        e[i] = 1e-6
+        fd = (m.loss_and_grad(p + e, x, t)[0] - m.loss_and_grad(p - e, x, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(fd), i
+
+
+def test_mlp_oracle_special_cases():
+    from oracle import mlp_oracle as m
+    assert m.N_PARAMS == 17666
+    p = np.zeros(m.N_PARAMS)
+    p[-2:] = [0.5, -1.5]                      # only b3: the output is the bias
+    y, _ = m.forward(p, np.ones((3, 6)))
+    np.testing.assert_allclose(y, [[0.5, -1.5]] * 3)
+    loss, g = m.loss_and_grad(p, np.ones((3, 6)), np.zeros((3, 2)))
+    assert loss == pytest.approx((0.25 + 2.25) / 2)
+    np.testing.assert_allclose(g[-2:], [0.5, -1.5])   # d/db3 of mean (b3)^2 over 2 outputs
+    np.testing.assert_allclose(g[:-2], 0.0)
