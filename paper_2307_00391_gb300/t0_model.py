@@ -10,8 +10,8 @@ forward / backward / Adam kernels) learns
               clock budget n_c, right-hand-side kind)
     -> (ln(T0* / T0_power_law), recommended clock count).
 
-The power law stays the fallback: ``predict`` returns the power-law T0 when no network is
-given.
+The power law stays the fallback: ``choose_t0`` returns the power-law T0 (scale 1) and the
+given clock budget when no network is given.
 """
 from __future__ import annotations
 
@@ -123,6 +123,15 @@ class T0Net:
         y = torch.empty((Xs.shape[0], 2), dtype=torch.float32, device="cuda")
         self.forward_dev(Xs, y)
         return y.cpu().numpy() * self.y_std + self.y_mean
+
+
+def choose_t0(diag: float, off: float, n_points: int, n_clock: int, flow: str, net: "T0Net | None" = None):
+    """(T0 scale relative to the power law, recommended clock count) for one problem: from the
+    network when given, else the power law itself (scale 1) and the budget."""
+    if net is None:
+        return 1.0, n_clock
+    y = net.predict(features(diag, off, n_points, n_clock, flow)[None, :])[0]
+    return float(math.exp(y[0])), int(min(max(round(float(y[1])), 1), n_clock))
 
 
 def features(diag: float, off: float, n_points: int, n_clock: int, flow: str) -> np.ndarray:
