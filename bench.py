@@ -266,6 +266,12 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_rows_scatter": ("byte", 2.0 * m_sub * N * prec_bytes),
         "k_clock_block": ("byte", 3.0 * half),
         "k_register_transform": ("byte", 2.0 * half),
+        # split register passes: the stage's single-pass minimum spread over its launches
+        # (clock block: read anc = 0, write both halves, 3 passes; Hadamard layer: 2 passes)
+        "k_clock_pass_a": ("byte", 3.0 * half / 3),
+        "k_clock_pass_b": ("byte", 3.0 * half / 3),
+        "k_clock_pass_c": ("byte", 3.0 * half / 3),
+        "k_hadamard_pass": ("byte", 2.0 * half / 2),
         "k_prep_fill": ("byte", 2.0 * half),
         "k_measure_sums": ("byte", 2.0 * half),
         "k_trotter_pass": ("byte", 2.0 * m_sub * N * prec_bytes),

@@ -505,11 +505,310 @@ hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, 
   }
 }
 
+// ------------------------------------------------------------------ split register passes
+// For a large state the clock transforms above are bounded by DRAM efficiency, not by the
+// butterflies: a column block of W = 4 complex64 amplitudes is a 32-byte segment per row,
+// and row segments that short reach about a quarter of the copy bandwidth on GB300 (128-byte
+// segments reach over 90%). A whole 2^13-row column block of 256-byte segments (2 MiB) does
+// not fit one SM, so for large states the register transform is split over its bits: the
+// register index c = c_lo + 2^m_lo c_hi is transformed by one pass over the m_hi high bits
+// (tile: all c_hi rows of W columns at a fixed c_lo) and one over the m_lo low bits (tile:
+// all c_lo rows at fixed high bits), each tile at most 128 rows x 256 bytes in shared memory.
+// Radix-2 DIF and DIT stages only need the index bits below their own bit for the twiddle,
+// so running the high-bit stages in one pass and the low-bit stages in the other is the same
+// sequence of butterflies as the single-pass transform.
+//
+// Clock block (a3 + a4 + the QFT of a5) as three passes:
+//   A  inverse-QFT DIF stages on the high bits: anc = 0 half -> anc = 1 half (same rows; the
+//      anc = 1 half is overwritten by this stage in every mode, so it serves as scratch),
+//   B  inverse-QFT DIF stages on the low bits, the rotation at the bit-reversed frequency,
+//      QFT DIT stages on the low bits: reads the anc = 1 half; writes cos(theta_y / 2) x_y to
+//      the anc = 0 half at row y (or, when both halves are uncomputed, the cos part after the
+//      same low stages at the tile's own rows) and the sin part back in place,
+//   C  QFT DIT stages on the high bits, in place (anc = 1 half, or both halves).
+// Pass B's write of row y = bitrev(p) goes to the anc = 0 half, which no pass reads after A,
+// so the bit-reversed scatter cannot race with another tile's reads.
+enum SplitOp { kSplitDif = 0, kSplitMid = 1, kSplitDit = 2, kSplitHad = 3 };
+
+constexpr int kSplitThreads = 256;
+constexpr int kSplitSegBytes = 256;  // bytes per row segment of a tile
+constexpr int kSplitMaxBits = 7;     // tile rows <= 128
+constexpr int kSplitUnroll = 4;     // 16-byte tile loads in flight per thread
+constexpr int kSplitMaxRadix = 3;    // stages per shared-memory round trip (registers: 3 CTAs per SM)
+
+struct SplitArgs {
+  void* src;           // tiles are read here ...
+  void* dst;           // ... and written back here at the same rows
+  void* dst_cos;       // pass B: cos part (anc = 0 half)
+  const void* rot;     // pass B: (cos(theta_y / 2), sin(theta_y / 2)) per y
+  long long tiles;     // tiles in the launch
+  long long region;    // amplitudes per outer block (2^(lo + m))
+  int lo, m, b0, nb;   // register at index bits [lo, lo + m); this pass: register bits [b0, b0 + nb)
+  int log_w, log_cb;   // W = 2^log_w columns per tile; 2^log_cb column blocks per row
+  double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
+};
+
+// One radix-2^RB pass over tile bits [tb, tb + RB) of a row-major tile X[row * W + w]. The
+// register index of tile row j is lo_fixed + (j << b0) + (fixed bits above b0 + nb).
+template <class T, int RB, bool DIT, int MODE>
+__device__ void tile_pass(T* X, int log_w, int nb, int tb, int b0, int lo_fixed, int m, const Twiddle<T>& tw,
+                          bool conj) {
+  constexpr int G = 1 << RB;
+  const int W = 1 << log_w;
+  const int total = W << (nb - RB);
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    const int w = g & (W - 1);
+    const int gg = g >> log_w;
+    const int lo = gg & ((1 << tb) - 1);
+    const int row0 = ((gg >> tb) << (tb + RB)) + lo;
+    T v[G];
+#pragma unroll
+    for (int x = 0; x < G; ++x) v[x] = X[((row0 + (x << tb)) << log_w) + w];
+    butterflies<T, RB, DIT, MODE>(v, lo_fixed + (lo << b0), b0 + tb, m, tw, conj);
+#pragma unroll
+    for (int x = 0; x < G; ++x) X[((row0 + (x << tb)) << log_w) + w] = v[x];
+  }
+}
+
+// All nb stages of a tile in passes of at most kSplitMaxRadix bits (DIF: high bits first).
+template <class T, bool DIT, int MODE>
+__device__ void tile_stages(T* X, int log_w, int nb, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
+  constexpr int kMaxR = kSplitMaxRadix;
+  const int npass = (nb + kMaxR - 1) / kMaxR;
+  int done = 0;
+  for (int q = 0; q < npass; ++q) {
+    const int r = (nb - done) / (npass - q);
+    const int tb = DIT ? done : nb - done - r;
+    switch (r) {
+      case 3: tile_pass<T, 3, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
+      case 2: tile_pass<T, 2, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
+      default: tile_pass<T, 1, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
+    }
+    done += r;
+    __syncthreads();
+  }
+}
+
+// Tile rows <-> shared memory in 16-byte units (a row segment is kSplitSegBytes).
+template <class T>
+__device__ __forceinline__ void tile_load(T* X, const T* base, long long row_stride_units, int rows, int lo_fixed,
+                                          int b0, long long hi_off) {
+  constexpr int upr = kSplitSegBytes / 16;
+  const int total = rows * upr;
+  const uint4* src = reinterpret_cast<const uint4*>(base);
+  uint4* dst = reinterpret_cast<uint4*>(X);
+  for (int u0 = threadIdx.x; u0 < total; u0 += blockDim.x * kSplitUnroll) {
+    uint4 v[kSplitUnroll];
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const int u = u0 + k * blockDim.x;
+      if (u < total) {
+        const int j = u / upr, h = u - j * upr;
+        v[k] = src[((long long)lo_fixed + ((long long)j << b0) + hi_off) * row_stride_units + h];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const int u = u0 + k * blockDim.x;
+      if (u < total) dst[u] = v[k];
+    }
+  }
+}
+
+template <class T, class S>
+__device__ __forceinline__ void tile_store(T* base, const T* X, long long row_stride_units, int rows, int lo_fixed,
+                                           int b0, long long hi_off, S scale, bool scaled) {
+  constexpr int upr = kSplitSegBytes / 16;
+  constexpr int per = 16 / sizeof(T);
+  const int total = rows * upr;
+  uint4* dst = reinterpret_cast<uint4*>(base);
+  const uint4* src = reinterpret_cast<const uint4*>(X);
+  for (int u = threadIdx.x; u < total; u += blockDim.x) {
+    const int j = u / upr, h = u - j * upr;
+    uint4 v = src[u];
+    if (scaled) {
+      T* t = reinterpret_cast<T*>(&v);
+#pragma unroll
+      for (int q = 0; q < per; ++q) t[q] = cscale(t[q], scale);
+    }
+    dst[((long long)lo_fixed + ((long long)j << b0) + hi_off) * row_stride_units + h] = v;
+  }
+}
+
+template <class R, int OP, bool FULL>
+__global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  T* X = t0 + twiddle_entries(a.m);
+  T* Y = X + ((size_t)1 << (a.nb + a.log_w));
+  if (OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
+  const Twiddle<T> tw{t0, t1};
+  const int rows = 1 << a.nb;
+  const int other = a.m - a.nb;
+  const long long row_units = ((long long)1 << a.lo) * (long long)sizeof(T) / 16;  // 16-byte units per row
+  constexpr int upr = kSplitSegBytes / 16;
+  for (long long t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+    const long long ib = t & (((long long)1 << a.log_cb) - 1);
+    const long long rest = t >> a.log_cb;
+    const int f = (int)(rest & ((1LL << other) - 1));
+    const long long o = rest >> other;
+    const int lo_fixed = f & ((1 << a.b0) - 1);
+    const int hi_fixed = f >> a.b0;
+    const long long hi_off = (long long)hi_fixed << (a.b0 + a.nb);
+    const long long base_amp = o * a.region + ib * upr * (16 / (long long)sizeof(T));
+    const T* src = static_cast<const T*>(a.src) + base_amp;
+    T* dst = static_cast<T*>(a.dst) + base_amp;
+    __syncthreads();  // the previous tile's smem reads are done
+    tile_load(X, src, row_units, rows, lo_fixed, a.b0, hi_off);
+    __syncthreads();
+    if (OP == kSplitDif) {
+      tile_stages<T, false, 0>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, false);
+      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)1, false);
+    } else if (OP == kSplitDit) {
+      tile_stages<T, true, 0>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, true);
+      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)1, false);
+    } else if (OP == kSplitHad) {
+      tile_stages<T, false, 1>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, false);
+      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)a.scale, a.scale != 1.0);
+    } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << nb
+      tile_stages<T, false, 0>(X, a.log_w, a.nb, 0, 0, a.m, tw, false);
+      const R s = (R)a.scale;
+      const T* rot = static_cast<const T*>(a.rot);
+      T* cos_out = static_cast<T*>(a.dst_cos) + base_amp;
+      constexpr int per = 16 / sizeof(T);
+      for (int u = threadIdx.x; u < rows * upr; u += blockDim.x) {
+        const int j = u / upr, h = u - j * upr;
+        const int y = bitrev_m(j + (hi_fixed << a.nb), a.m);
+        const T r = rot[y];
+        uint4 keep;
+        T* kt = reinterpret_cast<T*>(&keep);
+        T* xs = X + (size_t)u * per;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+          const T x = cscale(xs[q], s);
+          if (FULL) Y[(size_t)u * per + q] = cscale(x, r.x * s);
+          else kt[q] = cscale(x, r.x);
+          xs[q] = cscale(x, r.y * s);
+        }
+        if (!FULL)
+          reinterpret_cast<uint4*>(cos_out)[(long long)y * row_units + h] = keep;
+      }
+      __syncthreads();
+      tile_stages<T, true, 0>(X, a.log_w, a.nb, 0, 0, a.m, tw, true);
+      if (FULL) tile_stages<T, true, 0>(Y, a.log_w, a.nb, 0, 0, a.m, tw, true);
+      tile_store(dst, X, row_units, rows, 0, 0, hi_off, (R)1, false);
+      if (FULL) tile_store(cos_out, Y, row_units, rows, 0, 0, hi_off, (R)1, false);
+    }
+  }
+}
+
+template <class R>
+int split_log_w() {
+  int lw = 0;
+  while ((1 << (lw + 1)) * (int)sizeof(typename Cx<R>::T) <= kSplitSegBytes) ++lw;
+  return lw;  // W * sizeof(T) = kSplitSegBytes
+}
+
+// The split path serves registers of 8..14 bits whose rows hold at least one 256-byte segment,
+// in states too large for L2 (the single-pass kernels are faster on L2-resident states).
+template <class R>
+bool split_applies(int lo, int m, long long region_amps) {
+  const size_t sz = sizeof(typename Cx<R>::T);
+  if (m < 8 || (m + 1) / 2 > kSplitMaxBits) return false;
+  if (((size_t)1 << lo) * sz < (size_t)kSplitSegBytes) return false;
+  if (getenv("HHL_FFT_SPLIT") != nullptr) return atoi(getenv("HHL_FFT_SPLIT")) != 0;  // tuning override
+  return (size_t)region_amps * sz > ((size_t)256 << 20);
+}
+
+template <class R, int OP, bool FULL>
+hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* name) {
+  using T = typename Cx<R>::T;
+  a.log_w = split_log_w<R>();
+  a.log_cb = a.lo - a.log_w;
+  a.region = 1LL << (a.lo + a.m);
+  a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
+  const size_t tile = ((size_t)1 << (a.nb + a.log_w)) * sizeof(T);
+  const size_t smem = (size_t)twiddle_entries(a.m) * sizeof(T) + ((OP == kSplitMid && FULL) ? 2 : 1) * tile;
+  auto kern = k_split_pass<R, OP, FULL>;
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  HHL_CUDA_TRY(cudaGetDevice(&dev));
+  HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSplitThreads, smem));
+  if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "split register pass does not fit an SM");
+  const long long grid = std::min<long long>(a.tiles, (long long)occ * sms);
+  HHL_PROF_BEGIN(st);
+  kern<<<(unsigned)grid, kSplitThreads, smem, st>>>(a);
+  HHL_LAUNCH_CHECK(name);
+  return HHL_OK;
+}
+
+template <class R, bool FULL>
+hhl_status clock_block_split(const Plan& p, void* state, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  const int m = p.n_c, m_lo = m / 2, m_hi = m - m_lo;
+  T* S0 = static_cast<T*>(state);
+  T* S1 = S0 + p.R * p.N;
+  SplitArgs a = {};
+  a.lo = p.n_s;
+  a.m = m;
+  a.rot = p.d_rot;
+  // A: inverse-QFT stages on the high bits, anc = 0 -> anc = 1
+  a.src = S0;
+  a.dst = S1;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  hhl_status s = launch_split<R, kSplitDif, FULL>(a, 1, st, "k_clock_pass_a");
+  if (s != HHL_OK) return s;
+  // B: low-bit stages, rotation, low-bit QFT stages
+  a.src = S1;
+  a.dst = S1;
+  a.dst_cos = S0;
+  a.b0 = 0;
+  a.nb = m_lo;
+  a.scale = 1.0 / sqrt((double)p.R);
+  s = launch_split<R, kSplitMid, FULL>(a, 1, st, "k_clock_pass_b");
+  if (s != HHL_OK) return s;
+  // C: QFT stages on the high bits, in place (both halves when both are uncomputed)
+  a.src = FULL ? S0 : S1;
+  a.dst = a.src;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  return launch_split<R, kSplitDit, FULL>(a, FULL ? 2 : 1, st, "k_clock_pass_c");
+}
+
+template <class R>
+hhl_status hadamard_split(void* base, int lo, int m, int outer, cudaStream_t st) {
+  const int m_lo = m / 2, m_hi = m - m_lo;
+  SplitArgs a = {};
+  a.src = base;
+  a.dst = base;
+  a.lo = lo;
+  a.m = m;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  a.scale = 1.0;
+  hhl_status s = launch_split<R, kSplitHad, false>(a, outer, st, "k_hadamard_pass");
+  if (s != HHL_OK) return s;
+  a.b0 = 0;
+  a.nb = m_lo;
+  a.scale = 1.0 / sqrt((double)(1LL << m));
+  return launch_split<R, kSplitHad, false>(a, outer, st, "k_hadamard_pass");
+}
+
 }  // namespace
 
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
-  if (p.prec == HHL_PREC_C64)
+  const long long half = p.R * p.N;
+  if (p.prec == HHL_PREC_C64) {
+    if (split_applies<float>(p.n_s, p.n_c, half))
+      return p.full ? clock_block_split<float, true>(p, state, st) : clock_block_split<float, false>(p, state, st);
     return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
+  }
+  if (split_applies<double>(p.n_s, p.n_c, half))
+    return p.full ? clock_block_split<double, true>(p, state, st) : clock_block_split<double, false>(p, state, st);
   return p.full ? clock_block_impl<double, true>(p, state, st) : clock_block_impl<double, false>(p, state, st);
 }
 
@@ -518,8 +817,12 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
   const int64_t half_amps = p.R * p.N;
   void* base = p.full ? state : (void*)((char*)state + half_amps * p.amp_bytes());
   const int n = p.full ? p.n : p.n - 1;
-  return p.prec == HHL_PREC_C64 ? register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st)
-                                : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
+  const int outer = p.full ? 2 : 1;
+  if (p.prec == HHL_PREC_C64)
+    return split_applies<float>(p.n_s, p.n_c, half_amps) ? hadamard_split<float>(base, p.n_s, p.n_c, outer, st)
+                                                         : register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
+  return split_applies<double>(p.n_s, p.n_c, half_amps) ? hadamard_split<double>(base, p.n_s, p.n_c, outer, st)
+                                                        : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
 }
 
 hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st) {

@@ -188,23 +188,30 @@ __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t 
 #pragma unroll
     for (int k = 0; k < U; ++k)
       if (i0 + k * stride < units) z[k] = u[i0 + k * stride];
+    // The U units of one batch are summed in the amplitude precision (at most 4U squares)
+    // and added to the FP64 totals once: GB300's FP64 rate is far below its FP32 rate, and
+    // one FP64 conversion and add per unit would bound the pass.
+    R s[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int64_t i = i0 + k * stride;
       if (i >= units) break;
-      double p;
+      R p;
       if constexpr (sizeof(R) == 4) {
-        p = (double)(z[k].x * z[k].x + z[k].y * z[k].y + z[k].z * z[k].z + z[k].w * z[k].w);
+        p = fmaf(z[k].x, z[k].x, fmaf(z[k].y, z[k].y, fmaf(z[k].z, z[k].z, z[k].w * z[k].w)));
       } else {
         p = z[k].x * z[k].x + z[k].y * z[k].y;
       }
       if (i < half_u) {
-        a[0] += p;
+        s[0] += p;
       } else {
-        a[1] += p;
-        if (i - half_u < v_u) a[2] += p;
+        s[1] += p;
+        if (i - half_u < v_u) s[2] += p;
       }
     }
+    a[0] += (double)s[0];
+    a[1] += (double)s[1];
+    a[2] += (double)s[2];
   }
   block_sum_atomic<3>(a, acc);
 }

@@ -363,7 +363,8 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
     plan.apply_stage("qpe_u", st)
     torch.cuda.synchronize()
     lub = 4.0 * (N + 1) ** 2
-    t0 = plan.info["t0"]
+    t0 = o.t0_total("range_fill", n_c)
+    assert plan.info["t0"] == pytest.approx(t0, rel=1e-12)
     bhat = b / np.linalg.norm(b) / math.sqrt(R)
     np.testing.assert_allclose(_np(st[:N]), bhat, rtol=1e-6, atol=0)
     for k in (0, 4, 9, 11, 12):
@@ -379,5 +380,72 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
     out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
     plan.measure_async(st, out)          # p_success is 0 before the inversion: read the norm only
     assert out[2].item() == pytest.approx(1.0, abs=1e-4)
+    # The clock block and the Hadamard layer at full size (split register passes) on a seeded
+    # random state: every system column j is transformed on its own, so the oracle checks
+    # sampled columns one by one.
+    g = torch.Generator(device="cuda")
+    g.manual_seed(20230701)
+    view = st.view(2, R, N)
+    torch.view_as_real(view[0]).normal_(generator=g)
+    cols = [0, 1, 77, N // 2 + 5, N - 1]
+    before = [_np(view[0, :, j]) for j in cols]
+    plan.apply_stage("clock_block", st)
+    theta = o.rotation_angles(n_c, t0)
+    for j, x in zip(cols, before):
+        psi = np.zeros(2 * R, dtype=np.complex128)
+        psi[:R] = x
+        o.qft(psi, n_c + 1, 0, n_c, inverse=True)
+        o.apply_clock_controlled_ry(psi, 0, n_c, theta)
+        rotated0 = psi[:R].copy()
+        o.qft(psi, n_c + 1, 0, n_c, inverse=False)
+        scale = np.abs(x).max()
+        assert np.abs(_np(view[0, :, j]) - rotated0).max() <= 2e-5 * scale, j
+        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= 2e-5 * scale, j
+    torch.view_as_real(view[1]).normal_(generator=g)
+    before1 = [_np(view[1, :, j]) for j in cols]
+    plan.apply_stage("final_h", st)
+    for j, x in zip(cols, before1):
+        psi = x.copy()
+        for q in range(n_c):
+            o.apply_1q(psi, n_c, q, o.H_GATE)
+        assert np.abs(_np(view[1, :, j]) - psi).max() <= 2e-5 * np.abs(x).max(), j
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("full", [False, True])
+@pytest.mark.parametrize("flow,n_s,n_c", [("couette", 5, 8), ("poiseuille", 6, 9), ("couette", 7, 11)])
+def test_split_register_passes_parity(hhl, monkeypatch, prec, full, flow, n_s, n_c):
+    """The clock block and the Hadamard layer as split register passes (the path large states
+    take), forced on small states, stage by stage against the oracle."""
+    import torch
+    monkeypatch.setenv("HHL_FFT_SPLIT", "1")
+    diag, off, b, walls = problem(flow, n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    ref = run_stages(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, full_uncompute=full, gemm="simt")
+    st = plan.new_state()
+    plan.prepare_rhs(_b_dev(b), st)
+    plan.apply_stage("qpe_u", st)
+    tol = TOL[prec]
+    hhl.profile_reset()
+    hhl.profile_enable(True)
+    try:
+        plan.apply_stage("clock_block", st)
+        got = _np(st)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["clock_block"], n_s, n_c, 1), atol=tol)
+        anc0_ref = ref["clock_block"] if full else ref["rotated"]
+        np.testing.assert_allclose(_half(got, n_s, n_c, 0), _half(anc0_ref, n_s, n_c, 0), atol=tol)
+        plan.apply_stage("uncompute_u", st)
+        plan.apply_stage("final_h", st)
+        got = _np(st)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["final_h"], n_s, n_c, 1), atol=tol)
+        if full:
+            np.testing.assert_allclose(got, ref["final_h"], atol=tol)
+        torch.cuda.synchronize()
+        prof = hhl.profile_read()
+    finally:
+        hhl.profile_enable(False)
+    assert all(prof[f"k_clock_pass_{x}"][0] == 1 for x in "abc") and "k_clock_block" not in prof
+    assert prof["k_hadamard_pass"][0] == 2 and "k_register_transform" not in prof
