@@ -259,6 +259,8 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
     N, R = 1 << n_s, 1 << n_c
     half = R * N * prec_bytes
     m_sub = R // 2
+    passes = plan_info.get("trotter_passes", 0)
+    tb_launch = plan_info.get("trotter_bytes", 0.0) / passes if passes else 0.0
     return {
         "k_ctrl_gemm_simt<f32>": ("flop", 8.0 * m_sub * N * N),
         "k_ctrl_gemm_simt<f64>": ("flop", 8.0 * m_sub * N * N),
@@ -274,8 +276,9 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_hadamard_pass": ("byte", 2.0 * half / 2),
         "k_prep_fill": ("byte", 2.0 * half),
         "k_measure_sums": ("byte", 2.0 * half),
-        "k_trotter_pass": ("byte", 2.0 * m_sub * N * prec_bytes),
-        "k_trotter_edges": ("byte", 2.0 * m_sub * ((N + 479) // 480) * 32 * prec_bytes),
+        # grouped Trotter passes change different row counts: the plan's total over its passes
+        "k_trotter_pass": ("byte", tb_launch),
+        "k_trotter_edges": ("byte", tb_launch * ((N + 479) // 480) * 32 / N),
     }
 
 

@@ -138,8 +138,10 @@ typedef struct hhl_plan_info {
   uint64_t table_bytes;   /* device bytes of U_k / Trotter / angle tables */
   uint64_t workspace_bytes;
   double gemm_flops;      /* algorithmic flops of the controlled-U GEMMs of one circuit */
-  int64_t trotter_passes; /* Strang steps of one circuit (Trotter mode) */
+  int64_t trotter_passes; /* Trotter mode: HBM passes (k_trotter_pass launches) of one circuit */
   double plan_seconds;    /* wall time of hhl_plan_create */
+  double trotter_bytes;   /* Trotter mode: algorithmic HBM bytes (read + write) of those passes:
+                             every system row a pass changes, read and written once */
 } hhl_plan_info;
 
 typedef struct hhl_measurement {

@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
                 ("lambda_ub", c_double), ("lambda_min", c_double), ("lambda_max", c_double),
                 ("kappa", c_double), ("t0", c_double), ("C", c_double), ("state_bytes", c_uint64),
                 ("table_bytes", c_uint64), ("workspace_bytes", c_uint64), ("gemm_flops", c_double),
-                ("trotter_passes", c_int64), ("plan_seconds", c_double)]
+                ("trotter_passes", c_int64), ("plan_seconds", c_double), ("trotter_bytes", c_double)]
 
 
 class BatchInfo(ctypes.Structure):

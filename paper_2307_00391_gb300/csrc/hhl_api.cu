@@ -517,7 +517,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
   {
     // GEMM output rows (dense) or the Trotter pass's interior edges (32 per warp window)
     size_t scratch_amps = (size_t)(p.R / 2) * N;
-    if (!dense) scratch_amps = std::max(scratch_amps, (size_t)(p.R / 2) * trotter_segments(N) * 32);
+    if (!dense) scratch_amps = (size_t)p.R * trotter_segments(N) * 32;
     HHL_ALLOC(p.d_scratch, scratch_amps * ab, &p.workspace_bytes);
   }
   if (dense) {
@@ -600,11 +600,22 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       q[3] = sin(tau * oh);
       q[4] = tau;
       q[5] = dh;
-      p.trotter_passes += (int64_t)r * (p.full ? 3 : 2);
     }
+    p.trot_diag_hat = dh;
+    p.trot_off_hat = oh;
     HHL_ALLOC(p.d_trot, p.trot_blocks.size() * sizeof(double), &p.table_bytes);
     HHL_PLAN_CUDA(cudaMemcpyAsync(p.d_trot, p.trot_blocks.data(), p.trot_blocks.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, st));
+    std::vector<unsigned char> lists;
+    hhl::trotter_build_passes(p, &lists);
+    p.trotter_passes = (int64_t)p.trot_pass[0].size() + (int64_t)p.trot_pass[1].size() * (p.full ? 2 : 1);
+    for (int dir = 0; dir < 2; ++dir)
+      for (const TrotPassDesc& d : p.trot_pass[dir]) {
+        const double rows = d.single_k >= 0 ? (double)(p.R / 2) : (double)p.R * (1.0 - 1.0 / (double)(1 << d.gbits));
+        p.trotter_bytes += (dir == 1 && p.full ? 2.0 : 1.0) * 2.0 * rows * (double)N * (double)ab;
+      }
+    HHL_ALLOC(p.d_trot_lists, lists.size(), &p.table_bytes);
+    HHL_PLAN_CUDA(cudaMemcpyAsync(p.d_trot_lists, lists.data(), lists.size(), cudaMemcpyHostToDevice, st));
     HHL_PLAN_CUDA(cudaStreamSynchronize(st));
   }
   cudaStreamDestroy(st);
@@ -620,7 +631,7 @@ void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
   void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
-                  plan->d_meas, plan->d_u, plan->d_bsplit};
+                  p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_bsplit};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   hhl::tc_free(p);
@@ -648,6 +659,7 @@ hhl_status hhl_plan_get_info(hhl_plan_t plan, hhl_plan_info* info) {
   info->workspace_bytes = p.workspace_bytes;
   info->gemm_flops = p.gemm_flops;
   info->trotter_passes = p.trotter_passes;
+  info->trotter_bytes = p.trotter_bytes;
   info->plan_seconds = p.plan_seconds;
   return HHL_OK;
 }
@@ -680,7 +692,6 @@ hhl_status hhl_prepare_rhs_host(hhl_plan_t plan, const double* b_re, const doubl
 }
 
 static hhl_status ctrl_u(const Plan& p, void* half, int k, bool adj, cudaStream_t st) {
-  if (p.expm_mode == HHL_EXPM_TROTTER) return hhl::launch_trotter(p, half, k, adj, st);
   if (p.gemm_impl == HHL_GEMM_TCGEN05) return hhl::launch_ctrl_u_tc(p, half, k, adj, st);
   return hhl::launch_ctrl_u_dense(p, half, k, adj, st);
 }
@@ -695,11 +706,17 @@ hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void
   hhl_status s = HHL_OK;
   switch (stage) {
     case HHL_STAGE_QPE_U:
+      if (p.expm_mode == HHL_EXPM_TROTTER) return hhl::launch_trotter(p, s0, false, st);
       for (int k = 0; k < p.n_c && s == HHL_OK; ++k) s = ctrl_u(p, s0, k, false, st);
       return s;
     case HHL_STAGE_CLOCK_BLOCK:
       return hhl::launch_clock_block(p, state_dev, st);
     case HHL_STAGE_UNCOMPUTE_U:
+      if (p.expm_mode == HHL_EXPM_TROTTER) {
+        s = hhl::launch_trotter(p, s1, true, st);
+        if (s == HHL_OK && p.full) s = hhl::launch_trotter(p, s0, true, st);
+        return s;
+      }
       for (int k = p.n_c - 1; k >= 0 && s == HHL_OK; --k) {
         s = ctrl_u(p, s1, k, true, st);
         if (s == HHL_OK && p.full) s = ctrl_u(p, s0, k, true, st);

@@ -62,6 +62,13 @@ template <class T> __host__ __device__ __forceinline__ T cconjmul(T a, T b) {  /
 template <class T, class S> __host__ __device__ __forceinline__ T cscale(T a, S s) { T z; z.x = a.x * s; z.y = a.y * s; return z; }
 
 // ------------------------------------------------------------------ the plan
+// One Trotter pass: clock bits [kb, kb + gbits) (single_k >= 0: the one bit single_k, rows
+// with that bit set) and the offset of its per-row-pattern layer lists in the plan's table.
+struct TrotPassDesc {
+  int kb = 0, gbits = 0, single_k = -1, max_layers = 0;
+  int64_t list_off = 0;
+};
+
 struct Plan {
   int n_s = 0, n_c = 0, n = 0;
   int prec = HHL_PREC_C64;
@@ -86,11 +93,15 @@ struct Plan {
   std::vector<int> trot_r;
   std::vector<double> trot_blocks;  // per k: E(tau/2), E(tau), O(tau): 3 x 8 doubles
   double* d_trot = nullptr;
+  double trot_diag_hat = 0, trot_off_hat = 0;  // the Toeplitz Ahat's diagonal and off-diagonal
+  std::vector<TrotPassDesc> trot_pass[2];     // QPE (forward) and uncompute (adjoint) passes
+  void* d_trot_lists = nullptr;               // the passes' layer lists
   double trotter_dt = 1.0;
   int trotter_max = 0;
   uint64_t table_bytes = 0, workspace_bytes = 0;
   double gemm_flops = 0;
   int64_t trotter_passes = 0;
+  double trotter_bytes = 0;
   double plan_seconds = 0;
   int device = 0;
   size_t amp_bytes() const { return prec == HHL_PREC_C64 ? 8 : 16; }
@@ -114,7 +125,11 @@ hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, 
 hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_vi, const double* d_cos,
                              const double* d_sin, double wgt, double2* d_u, cudaStream_t st);
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);
-hhl_status launch_trotter(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
+// All controlled products of QPE (adjoint: of the uncompute) on one half, in grouped passes.
+hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t st);
+// Plan time: group the clock bits into passes, fill p.trot_pass and the layer-list table
+// (bytes, to be uploaded to p.d_trot_lists); returns the number of lists.
+size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table);
 int64_t trotter_segments(int64_t N);  // warp windows per system row in a Trotter pass
 hhl_status launch_interleave(const double* re, const double* im, int64_t n, double* out, cudaStream_t st);
 

@@ -532,9 +532,9 @@ enum SplitOp { kSplitDif = 0, kSplitMid = 1, kSplitDit = 2, kSplitHad = 3 };
 
 constexpr int kSplitThreads = 256;
 constexpr int kSplitSegBytes = 256;  // bytes per row segment of a tile
+constexpr int kSplitMinBits = 4;     // tile rows >= 16
 constexpr int kSplitMaxBits = 7;     // tile rows <= 128
-constexpr int kSplitUnroll = 4;     // 16-byte tile loads in flight per thread
-constexpr int kSplitMaxRadix = 3;    // stages per shared-memory round trip (registers: 3 CTAs per SM)
+constexpr int kSplitUnroll = 8;      // 16-byte tile loads in flight per thread (at most)
 
 struct SplitArgs {
   void* src;           // tiles are read here ...
@@ -544,111 +544,162 @@ struct SplitArgs {
   long long tiles;     // tiles in the launch
   long long region;    // amplitudes per outer block (2^(lo + m))
   int lo, m, b0, nb;   // register at index bits [lo, lo + m); this pass: register bits [b0, b0 + nb)
-  int log_w, log_cb;   // W = 2^log_w columns per tile; 2^log_cb column blocks per row
+  int log_cb;          // 2^log_cb column blocks (tiles) per row
   double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
 };
 
-// One radix-2^RB pass over tile bits [tb, tb + RB) of a row-major tile X[row * W + w]. The
-// register index of tile row j is lo_fixed + (j << b0) + (fixed bits above b0 + nb).
-template <class T, int RB, bool DIT, int MODE>
-__device__ void tile_pass(T* X, int log_w, int nb, int tb, int b0, int lo_fixed, int m, const Twiddle<T>& tw,
-                          bool conj) {
-  constexpr int G = 1 << RB;
-  const int W = 1 << log_w;
-  const int total = W << (nb - RB);
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
-    const int w = g & (W - 1);
-    const int gg = g >> log_w;
-    const int lo = gg & ((1 << tb) - 1);
-    const int row0 = ((gg >> tb) << (tb + RB)) + lo;
-    T v[G];
-#pragma unroll
-    for (int x = 0; x < G; ++x) v[x] = X[((row0 + (x << tb)) << log_w) + w];
-    butterflies<T, RB, DIT, MODE>(v, lo_fixed + (lo << b0), b0 + tb, m, tw, conj);
-#pragma unroll
-    for (int x = 0; x < G; ++x) X[((row0 + (x << tb)) << log_w) + w] = v[x];
-  }
-}
-
-// All nb stages of a tile in passes of at most kSplitMaxRadix bits (DIF: high bits first).
-template <class T, bool DIT, int MODE>
-__device__ void tile_stages(T* X, int log_w, int nb, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
-  constexpr int kMaxR = kSplitMaxRadix;
-  const int npass = (nb + kMaxR - 1) / kMaxR;
-  int done = 0;
-  for (int q = 0; q < npass; ++q) {
-    const int r = (nb - done) / (npass - q);
-    const int tb = DIT ? done : nb - done - r;
-    switch (r) {
-      case 3: tile_pass<T, 3, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
-      case 2: tile_pass<T, 2, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
-      default: tile_pass<T, 1, DIT, MODE>(X, log_w, nb, tb, b0, lo_fixed, m, tw, conj); break;
-    }
-    done += r;
-    __syncthreads();
-  }
-}
-
-// Tile rows <-> shared memory in 16-byte units (a row segment is kSplitSegBytes).
 template <class T>
-__device__ __forceinline__ void tile_load(T* X, const T* base, long long row_stride_units, int rows, int lo_fixed,
-                                          int b0, long long hi_off) {
-  constexpr int upr = kSplitSegBytes / 16;
-  const int total = rows * upr;
-  const uint4* src = reinterpret_cast<const uint4*>(base);
-  uint4* dst = reinterpret_cast<uint4*>(X);
-  for (int u0 = threadIdx.x; u0 < total; u0 += blockDim.x * kSplitUnroll) {
-    uint4 v[kSplitUnroll];
+struct SplitGeom {
+  static constexpr int LW = sizeof(T) == 8 ? 5 : 4;  // W = 2^LW amplitudes = kSplitSegBytes
+  static constexpr int MR = sizeof(T) == 8 ? 4 : 3;  // radix bits per shared-memory round trip
+};
+
+// The RB radix-2 stages of one group (same arithmetic as butterflies() above), with the
+// twiddles of each stage formed once per distinct value: stage t needs 2^t factors
+// base_t * exp(-2 pi i xr / 2^(t+1)), xr < 2^t.
+template <class T, int RB, bool DIT, int MODE>
+__device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int lo_bits, int m, const Twiddle<T>& tw,
+                                                  bool conj) {
+  constexpr int G = 1 << RB;
+  using R = decltype(T().x);
 #pragma unroll
-    for (int k = 0; k < kSplitUnroll; ++k) {
-      const int u = u0 + k * blockDim.x;
-      if (u < total) {
-        const int j = u / upr, h = u - j * upr;
-        v[k] = src[((long long)lo_fixed + ((long long)j << b0) + hi_off) * row_stride_units + h];
+  for (int tt = 0; tt < RB; ++tt) {
+    const int t = DIT ? tt : (RB - 1 - tt);
+    T f[1 << (RB - 1)];
+    if (MODE == 0) {
+      const int s = t + 1 + lo_bits;
+      const T base = tw(lo << (m - s), conj);
+      f[0] = base;
+#pragma unroll
+      for (int xr = 1; xr < (1 << t); ++xr) {
+        const int k16 = xr << (3 - t);
+        T w;
+        w.x = (R)kRoot16[k16][0];
+        w.y = conj ? -(R)kRoot16[k16][1] : (R)kRoot16[k16][1];
+        f[xr] = cmul(base, w);
       }
     }
 #pragma unroll
-    for (int k = 0; k < kSplitUnroll; ++k) {
-      const int u = u0 + k * blockDim.x;
-      if (u < total) dst[u] = v[k];
+    for (int x = 0; x < G; ++x) {
+      if (x & (1 << t)) continue;
+      const int x1 = x | (1 << t);
+      T a = v[x], b = v[x1];
+      if (MODE == 0) {
+        const T fx = f[x & ((1 << t) - 1)];
+        if (DIT) {
+          b = cmul(b, fx);
+          v[x] = cadd(a, b);
+          v[x1] = csub(a, b);
+        } else {
+          v[x] = cadd(a, b);
+          v[x1] = cmul(csub(a, b), fx);
+        }
+      } else {
+        v[x] = cadd(a, b);
+        v[x1] = csub(a, b);
+      }
     }
   }
 }
 
-template <class T, class S>
-__device__ __forceinline__ void tile_store(T* base, const T* X, long long row_stride_units, int rows, int lo_fixed,
-                                           int b0, long long hi_off, S scale, bool scaled) {
+// One radix-2^RB pass over tile bits [TB, TB + RB) of the row-major tile X[row * W + w]
+// (2^NB rows). Tile row j is register index lo_fixed + (j << b0) + (fixed bits above).
+template <class T, int NB, int TB, int RB, bool DIT, int MODE>
+__device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
+  constexpr int LW = SplitGeom<T>::LW, W = 1 << LW, G = 1 << RB;
+  constexpr int total = W << (NB - RB);
+#pragma unroll 1
+  for (int g = threadIdx.x; g < total; g += kSplitThreads) {
+    const int w = g & (W - 1);
+    const int gg = g >> LW;
+    const int lo = gg & ((1 << TB) - 1);
+    const int row0 = ((gg >> TB) << (TB + RB)) + lo;
+    T* q = X + (row0 << LW) + w;
+    T v[G];
+#pragma unroll
+    for (int x = 0; x < G; ++x) v[x] = q[x << (TB + LW)];
+    group_butterflies<T, RB, DIT, MODE>(v, lo_fixed + (lo << b0), b0 + TB, m, tw, conj);
+#pragma unroll
+    for (int x = 0; x < G; ++x) q[x << (TB + LW)] = v[x];
+  }
+}
+
+// All NB stages of a tile in passes of at most MR bits (DIF: high bits first), a barrier
+// after each pass.
+template <class T, int NB, bool DIT, int MODE, int Q = 0, int DONE = 0>
+__device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
+  constexpr int MR = SplitGeom<T>::MR;
+  constexpr int NPASS = (NB + MR - 1) / MR;
+  if constexpr (Q < NPASS) {
+    constexpr int RB = (NB - DONE) / (NPASS - Q);
+    constexpr int TB = DIT ? DONE : NB - DONE - RB;
+    tile_pass<T, NB, TB, RB, DIT, MODE>(X, b0, lo_fixed, m, tw, conj);
+    __syncthreads();
+    tile_stages<T, NB, DIT, MODE, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj);
+  }
+}
+
+// Tile rows <-> shared memory in 16-byte units. Thread t moves the units t + k * 256: its
+// column unit h = t & 15 is fixed and its row advances by 16 per k, so the global address
+// advances by a constant stride.
+template <class T, int NB>
+__device__ __forceinline__ void tile_load(T* X, const T* base, long long row_units, long long row0, int b0) {
+  constexpr int upr = kSplitSegBytes / 16;
+  constexpr int total = (1 << NB) * upr;
+  constexpr int per_thread = total / kSplitThreads;
+  static_assert(total % kSplitThreads == 0, "tile units must be a multiple of the block");
+  const int h = threadIdx.x & (upr - 1), j0 = threadIdx.x / upr;
+  const uint4* src = reinterpret_cast<const uint4*>(base) + (row0 + ((long long)j0 << b0)) * row_units + h;
+  const long long step = ((long long)(kSplitThreads / upr) << b0) * row_units;
+  uint4* dst = reinterpret_cast<uint4*>(X) + threadIdx.x;
+  constexpr int U = per_thread < kSplitUnroll ? per_thread : kSplitUnroll;
+#pragma unroll
+  for (int k0 = 0; k0 < per_thread; k0 += U) {
+    uint4 v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) v[k] = src[(k0 + k) * step];
+#pragma unroll
+    for (int k = 0; k < U; ++k) dst[(k0 + k) * kSplitThreads] = v[k];
+  }
+}
+
+template <class T, int NB, class S>
+__device__ __forceinline__ void tile_store(T* base, const T* X, long long row_units, long long row0, int b0, S scale,
+                                           bool scaled) {
   constexpr int upr = kSplitSegBytes / 16;
   constexpr int per = 16 / sizeof(T);
-  const int total = rows * upr;
-  uint4* dst = reinterpret_cast<uint4*>(base);
-  const uint4* src = reinterpret_cast<const uint4*>(X);
-  for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int j = u / upr, h = u - j * upr;
-    uint4 v = src[u];
+  constexpr int per_thread = (1 << NB) * upr / kSplitThreads;
+  const int h = threadIdx.x & (upr - 1), j0 = threadIdx.x / upr;
+  uint4* dst = reinterpret_cast<uint4*>(base) + (row0 + ((long long)j0 << b0)) * row_units + h;
+  const long long step = ((long long)(kSplitThreads / upr) << b0) * row_units;
+  const uint4* src = reinterpret_cast<const uint4*>(X) + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < per_thread; ++k) {
+    uint4 v = src[k * kSplitThreads];
     if (scaled) {
       T* t = reinterpret_cast<T*>(&v);
 #pragma unroll
       for (int q = 0; q < per; ++q) t[q] = cscale(t[q], scale);
     }
-    dst[((long long)lo_fixed + ((long long)j << b0) + hi_off) * row_stride_units + h] = v;
+    dst[k * step] = v;
   }
 }
 
-template <class R, int OP, bool FULL>
+template <class R, int OP, bool FULL, int NB>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
+  constexpr int LW = SplitGeom<T>::LW;
+  constexpr int upr = kSplitSegBytes / 16;
+  constexpr int per = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t0 = reinterpret_cast<T*>(smem_raw);
   T* t1 = t0 + 64;
   T* X = t0 + twiddle_entries(a.m);
-  T* Y = X + ((size_t)1 << (a.nb + a.log_w));
+  T* Y = X + ((size_t)1 << (NB + LW));
   if (OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
   const Twiddle<T> tw{t0, t1};
-  const int rows = 1 << a.nb;
-  const int other = a.m - a.nb;
-  const long long row_units = ((long long)1 << a.lo) * (long long)sizeof(T) / 16;  // 16-byte units per row
-  constexpr int upr = kSplitSegBytes / 16;
+  const int other = a.m - NB;
+  const long long row_units = ((long long)1 << a.lo) / per;  // 16-byte units per row
   for (long long t = blockIdx.x; t < a.tiles; t += gridDim.x) {
     const long long ib = t & (((long long)1 << a.log_cb) - 1);
     const long long rest = t >> a.log_cb;
@@ -656,59 +707,54 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
     const long long o = rest >> other;
     const int lo_fixed = f & ((1 << a.b0) - 1);
     const int hi_fixed = f >> a.b0;
-    const long long hi_off = (long long)hi_fixed << (a.b0 + a.nb);
-    const long long base_amp = o * a.region + ib * upr * (16 / (long long)sizeof(T));
+    const long long row0 = lo_fixed + ((long long)hi_fixed << (a.b0 + NB));
+    const long long base_amp = o * a.region + (ib << LW);
     const T* src = static_cast<const T*>(a.src) + base_amp;
     T* dst = static_cast<T*>(a.dst) + base_amp;
-    __syncthreads();  // the previous tile's smem reads are done
-    tile_load(X, src, row_units, rows, lo_fixed, a.b0, hi_off);
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    tile_load<T, NB>(X, src, row_units, row0, a.b0);
     __syncthreads();
     if (OP == kSplitDif) {
-      tile_stages<T, false, 0>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, false);
-      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)1, false);
+      tile_stages<T, NB, false, 0>(X, a.b0, lo_fixed, a.m, tw, false);
+      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)1, false);
     } else if (OP == kSplitDit) {
-      tile_stages<T, true, 0>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, true);
-      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)1, false);
+      tile_stages<T, NB, true, 0>(X, a.b0, lo_fixed, a.m, tw, true);
+      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)1, false);
     } else if (OP == kSplitHad) {
-      tile_stages<T, false, 1>(X, a.log_w, a.nb, a.b0, lo_fixed, a.m, tw, false);
-      tile_store(dst, X, row_units, rows, lo_fixed, a.b0, hi_off, (R)a.scale, a.scale != 1.0);
-    } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << nb
-      tile_stages<T, false, 0>(X, a.log_w, a.nb, 0, 0, a.m, tw, false);
+      tile_stages<T, NB, false, 1>(X, a.b0, lo_fixed, a.m, tw, false);
+      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)a.scale, a.scale != 1.0);
+    } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
+      tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
       const R s = (R)a.scale;
       const T* rot = static_cast<const T*>(a.rot);
-      T* cos_out = static_cast<T*>(a.dst_cos) + base_amp;
-      constexpr int per = 16 / sizeof(T);
-      for (int u = threadIdx.x; u < rows * upr; u += blockDim.x) {
+      uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + base_amp);
+      for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
         const int j = u / upr, h = u - j * upr;
-        const int y = bitrev_m(j + (hi_fixed << a.nb), a.m);
+        const int y = bitrev_m(j + (hi_fixed << NB), a.m);
         const T r = rot[y];
-        uint4 keep;
+        uint4 xv = reinterpret_cast<uint4*>(X)[u];
+        uint4 keep, yv;
+        T* xt = reinterpret_cast<T*>(&xv);
         T* kt = reinterpret_cast<T*>(&keep);
-        T* xs = X + (size_t)u * per;
+        T* yt = reinterpret_cast<T*>(&yv);
 #pragma unroll
         for (int q = 0; q < per; ++q) {
-          const T x = cscale(xs[q], s);
-          if (FULL) Y[(size_t)u * per + q] = cscale(x, r.x * s);
+          const T x = cscale(xt[q], s);
+          if (FULL) yt[q] = cscale(x, r.x * s);
           else kt[q] = cscale(x, r.x);
-          xs[q] = cscale(x, r.y * s);
+          xt[q] = cscale(x, r.y * s);
         }
-        if (!FULL)
-          reinterpret_cast<uint4*>(cos_out)[(long long)y * row_units + h] = keep;
+        reinterpret_cast<uint4*>(X)[u] = xv;
+        if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
+        else cos_out[(long long)y * row_units + h] = keep;
       }
       __syncthreads();
-      tile_stages<T, true, 0>(X, a.log_w, a.nb, 0, 0, a.m, tw, true);
-      if (FULL) tile_stages<T, true, 0>(Y, a.log_w, a.nb, 0, 0, a.m, tw, true);
-      tile_store(dst, X, row_units, rows, 0, 0, hi_off, (R)1, false);
-      if (FULL) tile_store(cos_out, Y, row_units, rows, 0, 0, hi_off, (R)1, false);
+      tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
+      if (FULL) tile_stages<T, NB, true, 0>(Y, 0, 0, a.m, tw, true);
+      tile_store<T, NB>(dst, X, row_units, row0, 0, (R)1, false);
+      if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, row0, 0, (R)1, false);
     }
   }
-}
-
-template <class R>
-int split_log_w() {
-  int lw = 0;
-  while ((1 << (lw + 1)) * (int)sizeof(typename Cx<R>::T) <= kSplitSegBytes) ++lw;
-  return lw;  // W * sizeof(T) = kSplitSegBytes
 }
 
 // The split path serves registers of 8..14 bits whose rows hold at least one 256-byte segment,
@@ -716,22 +762,18 @@ int split_log_w() {
 template <class R>
 bool split_applies(int lo, int m, long long region_amps) {
   const size_t sz = sizeof(typename Cx<R>::T);
-  if (m < 8 || (m + 1) / 2 > kSplitMaxBits) return false;
+  if (m < 2 * kSplitMinBits || (m + 1) / 2 > kSplitMaxBits) return false;
   if (((size_t)1 << lo) * sz < (size_t)kSplitSegBytes) return false;
   if (getenv("HHL_FFT_SPLIT") != nullptr) return atoi(getenv("HHL_FFT_SPLIT")) != 0;  // tuning override
   return (size_t)region_amps * sz > ((size_t)256 << 20);
 }
 
-template <class R, int OP, bool FULL>
-hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* name) {
+template <class R, int OP, bool FULL, int NB>
+hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
-  a.log_w = split_log_w<R>();
-  a.log_cb = a.lo - a.log_w;
-  a.region = 1LL << (a.lo + a.m);
-  a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
-  const size_t tile = ((size_t)1 << (a.nb + a.log_w)) * sizeof(T);
+  const size_t tile = ((size_t)1 << (NB + SplitGeom<T>::LW)) * sizeof(T);
   const size_t smem = (size_t)twiddle_entries(a.m) * sizeof(T) + ((OP == kSplitMid && FULL) ? 2 : 1) * tile;
-  auto kern = k_split_pass<R, OP, FULL>;
+  auto kern = k_split_pass<R, OP, FULL, NB>;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
@@ -743,6 +785,21 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   kern<<<(unsigned)grid, kSplitThreads, smem, st>>>(a);
   HHL_LAUNCH_CHECK(name);
   return HHL_OK;
+}
+
+template <class R, int OP, bool FULL>
+hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* name) {
+  using T = typename Cx<R>::T;
+  a.log_cb = a.lo - SplitGeom<T>::LW;
+  a.region = 1LL << (a.lo + a.m);
+  a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
+  switch (a.nb) {
+    case 4: return launch_split_nb<R, OP, FULL, 4>(a, st, name);
+    case 5: return launch_split_nb<R, OP, FULL, 5>(a, st, name);
+    case 6: return launch_split_nb<R, OP, FULL, 6>(a, st, name);
+    case 7: return launch_split_nb<R, OP, FULL, 7>(a, st, name);
+    default: return fail(HHL_ERR_UNSUPPORTED, "split register pass: tile bits out of range");
+  }
 }
 
 template <class R, bool FULL>
@@ -760,7 +817,7 @@ hhl_status clock_block_split(const Plan& p, void* state, cudaStream_t st) {
   a.dst = S1;
   a.b0 = m_lo;
   a.nb = m_hi;
-  hhl_status s = launch_split<R, kSplitDif, FULL>(a, 1, st, "k_clock_pass_a");
+  hhl_status s = launch_split<R, kSplitDif, false>(a, 1, st, "k_clock_pass_a");
   if (s != HHL_OK) return s;
   // B: low-bit stages, rotation, low-bit QFT stages
   a.src = S1;
@@ -776,7 +833,7 @@ hhl_status clock_block_split(const Plan& p, void* state, cudaStream_t st) {
   a.dst = a.src;
   a.b0 = m_lo;
   a.nb = m_hi;
-  return launch_split<R, kSplitDit, FULL>(a, FULL ? 2 : 1, st, "k_clock_pass_c");
+  return launch_split<R, kSplitDit, false>(a, FULL ? 2 : 1, st, "k_clock_pass_c");
 }
 
 template <class R>

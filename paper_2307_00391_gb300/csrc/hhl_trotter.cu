@@ -16,7 +16,23 @@
 // so a small kernel first saves the 16 leading and 16 trailing amplitudes of every interior
 // into a side buffer and the pass reads its halos from there: each pass moves the rows
 // through HBM once (plus about 7% for the edges), in place.
+//
+// A 16-amplitude halo is exact for up to 17 layers when the first layer is an E layer: the
+// E pairs never cross the window edge, and each later layer moves the wrong values in from
+// the edge by one amplitude. Several clock bits share one pass: the controlled products of
+// QPE act on a clock row in bit order, and a row whose bits k1 < k2 < ... (within a group of
+// consecutive bits) are set gets U_k1, then U_k2, ..., applied to its system amplitudes, which
+// a pass over every row with some bit of the group set can do with the row's own layer list
+// (the trailing E(tau_k1 / 2) and leading E(tau_k2 / 2) merge into one E layer, since E
+// layers commute). Bits are grouped while the all-bits-set list stays within 17 layers; a
+// bit whose own list is longer gets passes over windows of its layers. For the 32-qubit
+// Poiseuille case (r_k = 1 for k < 8) 13 single-bit passes over half the rows each become 5
+// passes, 3 of them over half the rows.
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "hhl_common.cuh"
 
@@ -29,6 +45,14 @@ constexpr int kHalo = 16;                     // halo per side = max layers per 
 constexpr int kWin = 32 * kLaneAmps;          // 512 amplitudes per warp window
 constexpr int kInterior = kWin - 2 * kHalo;   // 480 written back per warp
 constexpr int kTrotThreads = 256;
+constexpr int kMaxPassLayers = kHalo + 1;     // exact with a kHalo halo when layer 0 is E
+
+struct LayerList {
+  int n;                   // layers (<= kMaxPassLayers)
+  int first_o;             // 1 if layer 0 is an O layer
+  double pc, ps;           // the pattern's summed E phase e^{i d (E time)} in this pass
+  double c[kMaxPassLayers], s[kMaxPassLayers];  // cos / sin of each layer's rotation angle
+};
 
 __device__ __forceinline__ int64_t row_with_bit_t(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
@@ -50,14 +74,10 @@ __device__ __forceinline__ T shfl_up1(T v) {
   return r;
 }
 
-// Rotations R(th) = [[cos th, i sin th], [i sin th, cos th]] of one pass: the half-step
-// E layers use th = (tau/2) o, the full E layers and the O layers th = tau o; the E-layer
-// phases e^{i s d} are scalars on the row and are applied once, summed, at the pass end.
-struct TrotBlocks {
-  double ch, sh, cf, sf;   // cos / sin of (tau/2) o and tau o
-  double pc, ps;           // cos / sin of the summed E phase of this pass
-};
-
+// Rotations R(th) = [[cos th, i sin th], [i sin th, cos th]]: E(s) = exp(i s E) is
+// e^{i s d} R(s o) on the E pairs and O(s) = exp(i s O) is R(s o) on the O pairs. A row
+// pattern's layers in one pass: their rotations and the summed E phase, applied once at
+// the end of the pass (it is a scalar on the row).
 // (a, b) <- R(th) (a, b) with c = cos th, s = sin th.
 template <class T, class R>
 __device__ __forceinline__ void rot_apply(T& a, T& b, R c, R s) {
@@ -67,37 +87,70 @@ __device__ __forceinline__ void rot_apply(T& a, T& b, R c, R s) {
   b = nb;
 }
 
+// Rows of a pass: single_k >= 0 enumerates the 2^(n_c - 1) rows with clock bit single_k set
+// (pattern 1); otherwise every row i, with pattern (i >> kb) & (2^gbits - 1) (rows whose
+// pattern is 0 are not touched).
+__device__ __forceinline__ void pass_row(int64_t i, int single_k, int kb, int gbits, int64_t* row, int* pattern) {
+  if (single_k >= 0) {
+    *row = row_with_bit_t(i, single_k);
+    *pattern = 1;
+  } else {
+    *row = i;
+    *pattern = (int)((i >> kb) & ((1 << gbits) - 1));
+  }
+}
+
 // side[(i * segs + s) * 32 + q]: q < 16 the first 16 interior amplitudes of segment s of
-// subset row i, q >= 16 its last 16 (zero beyond the row end).
+// pass row i, q >= 16 its last 16 (zero beyond the row end).
 template <class R>
 __global__ void k_trotter_edges(const typename Cx<R>::T* __restrict__ half, typename Cx<R>::T* __restrict__ side,
-                                int n_s, int k, int64_t segs, int64_t m_sub) {
+                                int n_s, int64_t segs, int64_t rows, int single_k, int kb, int gbits) {
   const int64_t N = 1LL << n_s;
-  const int64_t total = m_sub * segs * 32;
+  const int64_t total = rows * segs * 32;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t rs = e >> 5;
     const int q = (int)(e & 31);
     const int64_t i = rs / segs, s = rs - i * segs;
+    int64_t row;
+    int pattern;
+    pass_row(i, single_k, kb, gbits, &row, &pattern);
+    if (pattern == 0) continue;
     const int64_t g = s * kInterior + (q < 16 ? q : kInterior - 32 + q);
-    side[e] = g < N ? half[row_with_bit_t(i, k) * N + g] : mk<R>((R)0, (R)0);
+    side[e] = g < N ? half[row * N + g] : mk<R>((R)0, (R)0);
   }
 }
 
 template <class R>
 __global__ void __launch_bounds__(kTrotThreads) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
                                                               const typename Cx<R>::T* __restrict__ side, int n_s,
-                                                              int k, int64_t segs, int64_t m_sub, int l0, int l1,
-                                                              int n_layers_total, TrotBlocks blk, int adjoint) {
+                                                              int64_t segs, int64_t rows, int single_k, int kb,
+                                                              int gbits, const LayerList* __restrict__ lists) {
   using T = typename Cx<R>::T;
   constexpr int per = 16 / sizeof(T);  // amplitudes per 16-byte unit
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (kTrotThreads / 32) + (threadIdx.x >> 5);
-  if (gw >= m_sub * segs) return;  // warp-uniform: whole warps leave together
+  if (gw >= rows * segs) return;  // warp-uniform: whole warps leave together
   const int64_t N = 1LL << n_s;
   const int64_t i = gw / segs, s = gw - i * segs;
+  int64_t row_idx;
+  int pattern;
+  pass_row(i, single_k, kb, gbits, &row_idx, &pattern);
+  if (pattern == 0) return;  // warp-uniform: this row has no bit of the group set
+  const LayerList* L = lists + pattern;
+  const int n_layers = L->n, first_o = L->first_o;
+  // the warp's layer rotations, one layer per lane, broadcast from shared memory
+  __shared__ float2 rot_all[kTrotThreads / 32][32];
+  __shared__ double rotd_all[kTrotThreads / 32][32][2];
+  if (lane < n_layers) {
+    if constexpr (sizeof(R) == 4) rot_all[threadIdx.x >> 5][lane] = make_float2((float)L->c[lane], (float)L->s[lane]);
+    else {
+      rotd_all[threadIdx.x >> 5][lane][0] = L->c[lane];
+      rotd_all[threadIdx.x >> 5][lane][1] = L->s[lane];
+    }
+  }
   const int64_t g0 = s * kInterior;             // first interior amplitude
   const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
-  T* row = half + row_with_bit_t(i, k) * N;
+  T* row = half + row_idx * N;
 
   // Staging buffer of this warp: 32 x kLaneAmps amplitudes as 16-byte chunks, chunk c of
   // the window stored at position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both
@@ -141,17 +194,23 @@ __global__ void __launch_bounds__(kTrotThreads) k_trotter_pass(typename Cx<R>::T
       x[q] = (ns >= 0 && ns < segs) ? side[(i * segs + ns) * 32 + off + q] : mk<R>((R)0, (R)0);
   }
 
-  const R sg = adjoint ? (R)-1 : (R)1;  // the adjoint uses R(-th) and the conjugate phase
-  const R ch = (R)blk.ch, sh = sg * (R)blk.sh, cf = (R)blk.cf, sf = sg * (R)blk.sf;
+  __syncwarp();
   // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
   const bool in_ok = lane0 >= 0 && lane0 + kLaneAmps - 2 <= N - 1;
   const bool right_ok = lane < 31 && lane0 + kLaneAmps - 1 >= 1 && lane0 + kLaneAmps <= N - 1;
   const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
-  for (int l = l0; l < l1; ++l) {
-    if ((l & 1) == 0) {
+  for (int l = 0; l < n_layers; ++l) {
+    R c, sn;
+    if constexpr (sizeof(R) == 4) {
+      const float2 cs = rot_all[threadIdx.x >> 5][l];
+      c = cs.x;
+      sn = cs.y;
+    } else {
+      c = rotd_all[threadIdx.x >> 5][l][0];
+      sn = rotd_all[threadIdx.x >> 5][l][1];
+    }
+    if (((l + first_o) & 1) == 0) {
       // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
-      const bool halfstep = (l == 0 || l == n_layers_total - 1);
-      const R c = halfstep ? ch : cf, sn = halfstep ? sh : sf;
 #pragma unroll
       for (int q = 0; q < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
     } else {
@@ -159,26 +218,26 @@ __global__ void __launch_bounds__(kTrotThreads) k_trotter_pass(typename Cx<R>::T
       const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
       if (in_ok) {
 #pragma unroll
-        for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], cf, sf);
+        for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
       } else {
 #pragma unroll
         for (int q = 1; q + 1 < kLaneAmps; q += 2) {
           const int64_t j = lane0 + q;
-          if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], cf, sf);
+          if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
         }
       }
       if (right_ok) {  // (this lane's last a, next lane's first b): a <- c a + i s b
         const T a = x[kLaneAmps - 1];
-        x[kLaneAmps - 1] = mk<R>(cf * a.x - sf * right.y, cf * a.y + sf * right.x);
+        x[kLaneAmps - 1] = mk<R>(c * a.x - sn * right.y, c * a.y + sn * right.x);
       }
       if (left_ok) {  // (previous lane's last a, this lane's first b): b <- i s a + c b
         const T b = x[0];
-        x[0] = mk<R>(cf * b.x - sf * left.y, cf * b.y + sf * left.x);
+        x[0] = mk<R>(c * b.x - sn * left.y, c * b.y + sn * left.x);
       }
     }
   }
   {
-    const T ph = mk<R>((R)blk.pc, sg * (R)blk.ps);
+    const T ph = mk<R>((R)L->pc, (R)L->ps);
 #pragma unroll
     for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
   }
@@ -217,52 +276,142 @@ __global__ void k_interleave(const double* __restrict__ re, const double* __rest
 }
 
 template <class R>
-hhl_status trotter_impl(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
+hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  const int r = p.trot_r[k];
-  const int n_layers = 2 * r + 1;
-  const double* b = &p.trot_blocks[(size_t)k * 24];
-  const double tau = b[4], dh = b[5];
-  const int64_t m_sub = p.R / 2;
   const int64_t segs = trotter_segments(p.N);
-  const int64_t warps = m_sub * segs;
-  const int64_t grid = (warps + kTrotThreads / 32 - 1) / (kTrotThreads / 32);
-  if (grid > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "Trotter grid too large");
-  T* side = (T*)p.d_scratch;  // sized by the planner for m_sub * segs * 32 amplitudes
-  const int64_t edge_total = m_sub * segs * 32;
-  int eg = (int)((edge_total + 255) / 256);
-  if (eg > 152 * 16) eg = 152 * 16;
-  for (int l0 = 0; l0 < n_layers; l0 += kHalo) {
-    const int l1 = l0 + kHalo < n_layers ? l0 + kHalo : n_layers;
-    double steps = 0.0;  // E-layer time in this pass
-    for (int l = l0; l < l1; ++l)
-      if ((l & 1) == 0) steps += (l == 0 || l == n_layers - 1) ? 0.5 : 1.0;
-    TrotBlocks blk;
-    blk.ch = b[0];
-    blk.sh = b[1];
-    blk.cf = b[2];
-    blk.sf = b[3];
-    blk.pc = cos(steps * tau * dh);
-    blk.ps = sin(steps * tau * dh);
+  T* side = (T*)p.d_scratch;  // sized by the planner for R * segs * 32 amplitudes
+  const LayerList* lists = (const LayerList*)p.d_trot_lists;
+  for (const TrotPassDesc& d : p.trot_pass[adjoint ? 1 : 0]) {
+    const int64_t rows = d.single_k >= 0 ? p.R / 2 : p.R;
+    const int64_t warps = rows * segs;
+    const int64_t grid = (warps + kTrotThreads / 32 - 1) / (kTrotThreads / 32);
+    if (grid > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "Trotter grid too large");
+    const int64_t edge_total = rows * segs * 32;
+    int eg = (int)((edge_total + 255) / 256);
+    if (eg > 152 * 16) eg = 152 * 16;
     HHL_PROF_BEGIN(st);
-    k_trotter_edges<R><<<eg, 256, 0, st>>>((const T*)half, side, p.n_s, k, segs, m_sub);
+    k_trotter_edges<R><<<eg, 256, 0, st>>>((const T*)half, side, p.n_s, segs, rows, d.single_k, d.kb, d.gbits);
     HHL_LAUNCH_CHECK("k_trotter_edges");
     HHL_PROF_BEGIN(st);
-    k_trotter_pass<R><<<(unsigned)grid, kTrotThreads, 0, st>>>((T*)half, side, p.n_s, k, segs, m_sub, l0, l1,
-                                                               n_layers, blk, adjoint ? 1 : 0);
+    k_trotter_pass<R><<<(unsigned)grid, kTrotThreads, 0, st>>>((T*)half, side, p.n_s, segs, rows, d.single_k, d.kb,
+                                                               d.gbits, lists + d.list_off);
     HHL_LAUNCH_CHECK("k_trotter_pass");
   }
   return HHL_OK;
+}
+
+// The layer list of one pass for one row pattern. bits: the set clock bits of the pattern in
+// the order the circuit applies them; each contributes E(tau/2) O(tau) [E(tau) O(tau)]^(r-1)
+// E(tau/2) (sign -1 and the conjugate phase for the adjoint, whose palindromic Strang product
+// is the same list with negated angles), E layers of consecutive bits merged. A window
+// [l0, l1) of a single bit's list is taken when win_l1 > 0.
+void build_list(const Plan& p, const std::vector<int>& bits, bool adjoint, int win_l0, int win_l1, LayerList* out) {
+  const double sg = adjoint ? -1.0 : 1.0;
+  std::vector<std::pair<int, double>> layers;  // (is_o, time s): rotation angle s * o
+  double pending = 0.0;
+  for (size_t b = 0; b < bits.size(); ++b) {
+    const int k = bits[b];
+    const int r = p.trot_r[k];
+    const double tau = p.trot_blocks[(size_t)k * 24 + 4];
+    pending += 0.5 * tau;
+    layers.push_back({0, pending});
+    layers.push_back({1, tau});
+    for (int j = 1; j < r; ++j) {
+      layers.push_back({0, tau});
+      layers.push_back({1, tau});
+    }
+    pending = 0.5 * tau;
+  }
+  layers.push_back({0, pending});
+  const int l0 = win_l1 > 0 ? win_l0 : 0;
+  const int l1 = win_l1 > 0 ? win_l1 : (int)layers.size();
+  const double oh_k = p.trot_off_hat, dh = p.trot_diag_hat;
+  double e_time = 0.0;
+  out->n = l1 - l0;
+  out->first_o = layers[l0].first;
+  for (int l = l0; l < l1; ++l) {
+    const double th = sg * layers[l].second * oh_k;
+    out->c[l - l0] = cos(th);
+    out->s[l - l0] = sin(th);
+    if (layers[l].first == 0) e_time += layers[l].second;
+  }
+  out->pc = cos(e_time * dh);
+  out->ps = sg * sin(e_time * dh);
 }
 
 }  // namespace
 
 int64_t trotter_segments(int64_t N) { return (N + kInterior - 1) / kInterior; }
 
-hhl_status launch_trotter(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
-  if (p.d_scratch == nullptr) return fail(HHL_ERR_INVALID_ARG, "Trotter plan without scratch");
-  return p.prec == HHL_PREC_C64 ? trotter_impl<float>(p, half, k, adjoint, st)
-                                : trotter_impl<double>(p, half, k, adjoint, st);
+hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t st) {
+  if (p.d_scratch == nullptr || p.d_trot_lists == nullptr) return fail(HHL_ERR_INVALID_ARG, "Trotter plan without tables");
+  return p.prec == HHL_PREC_C64 ? trotter_impl<float>(p, half, adjoint, st)
+                                : trotter_impl<double>(p, half, adjoint, st);
+}
+
+size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table) {
+  std::vector<LayerList> lists;
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool adjoint = dir == 1;
+    p.trot_pass[dir].clear();
+    std::vector<int> order(p.n_c);
+    for (int j = 0; j < p.n_c; ++j) order[j] = adjoint ? p.n_c - 1 - j : j;
+    std::vector<int> group;
+    int group_layers = 1;
+    auto flush = [&]() {
+      if (group.empty()) return;
+      TrotPassDesc d;
+      d.kb = *std::min_element(group.begin(), group.end());
+      d.gbits = (int)group.size();
+      d.single_k = d.gbits == 1 ? group[0] : -1;
+      d.list_off = (int64_t)lists.size();
+      d.max_layers = group_layers;
+      const int npat = 1 << d.gbits;
+      lists.resize(lists.size() + npat);
+      LayerList* L = &lists[d.list_off];
+      L[0] = LayerList{};
+      for (int pat = 1; pat < npat; ++pat) {
+        std::vector<int> bits;
+        for (int k : group)
+          if ((pat >> (k - d.kb)) & 1) bits.push_back(k);
+        build_list(p, bits, adjoint, 0, 0, &L[pat]);
+      }
+      if (d.single_k >= 0) L[0] = L[1];  // unused: single-bit passes enumerate pattern-1 rows
+      p.trot_pass[dir].push_back(d);
+      group.clear();
+      group_layers = 1;
+    };
+    for (int k : order) {
+      const int lk = 2 * p.trot_r[k];
+      if (lk + 1 > kMaxPassLayers) {
+        flush();
+        // windows of this bit's 2r + 1 layers: 17 from an E layer, then 16 from O layers
+        for (int l0 = 0; l0 < lk + 1;) {
+          const int cap = (l0 & 1) ? kMaxPassLayers - 1 : kMaxPassLayers;
+          const int l1 = std::min(lk + 1, l0 + cap);
+          TrotPassDesc d;
+          d.kb = k;
+          d.gbits = 1;
+          d.single_k = k;
+          d.list_off = (int64_t)lists.size();
+          d.max_layers = l1 - l0;
+          lists.resize(lists.size() + 2);
+          build_list(p, std::vector<int>{k}, adjoint, l0, l1, &lists[d.list_off + 1]);
+          lists[d.list_off] = lists[d.list_off + 1];
+          p.trot_pass[dir].push_back(d);
+          l0 = l1;
+        }
+        continue;
+      }
+      if (group_layers + lk > kMaxPassLayers) flush();
+      group.push_back(k);
+      group_layers += lk;
+    }
+    flush();
+  }
+  table->resize(lists.size() * sizeof(LayerList));
+  memcpy(table->data(), lists.data(), table->size());
+  return lists.size();
 }
 
 hhl_status launch_interleave(const double* re, const double* im, int64_t n, double* out, cudaStream_t st) {

@@ -209,6 +209,34 @@ def test_trotter_parity(hhl, prec, dt, r_max):
     np.testing.assert_allclose(_np(st), ref["final_h"], atol=tol)
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_c,dt,r_max", [(9, 1.0e4, 0), (10, 400.0, 0)])
+def test_trotter_grouped_clock_bits_parity(hhl, prec, n_c, dt, r_max):
+    """Clock bits sharing one pass (up to 8 single-step bits, 17 layers for a row with all of
+    them set; larger steps counts in smaller groups and windows), against the oracle's
+    gate-by-gate controlled Strang products, the whole circuit in both uncompute modes."""
+    n_s = 5
+    diag, off, b, walls = problem("couette", n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    lub = pl["lam_ub"]
+    tro = dict(diag=diag / lub, off=off / lub, dt=dt, r_max=r_max)
+    ref = run_stages(b, n_s, pl, trotter=tro)
+    tol = TOL[prec] * (4 if prec == "c64" else 1)
+    for full in (False, True):
+        plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, expm="trotter", trotter_dt=dt, trotter_steps_max=r_max,
+                         full_uncompute=full)
+        st = plan.new_state()
+        plan.prepare_rhs_host(b, st)
+        plan.apply_stage("qpe_u", st)
+        np.testing.assert_allclose(_np(st), ref["qpe_u"], atol=tol)
+        for stage in ("clock_block", "uncompute_u", "final_h"):
+            plan.apply_stage(stage, st)
+        got = _np(st)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["final_h"], n_s, n_c, 1), atol=tol)
+        if full:
+            np.testing.assert_allclose(got, ref["final_h"], atol=tol)
+
+
 def test_trotter_large_row_spans_many_tiles(hhl):
     """A 2^13-point system row spans 4 shared-memory tiles with halos; checked against the
     oracle's dense Strang product on the controlled rows."""
