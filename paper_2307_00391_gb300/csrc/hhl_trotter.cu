@@ -104,169 +104,223 @@ __device__ __forceinline__ void pass_row(int64_t i, int single_k, int kb, int gb
 // pass row i, q >= 16 its last 16 (zero beyond the row end).
 template <class R>
 __global__ void k_trotter_edges(const typename Cx<R>::T* __restrict__ half, typename Cx<R>::T* __restrict__ side,
-                                int n_s, int64_t segs, int64_t rows, int single_k, int kb, int gbits) {
+                                int n_s, int segs, int rows, int single_k, int kb, int gbits) {
   const int64_t N = 1LL << n_s;
-  const int64_t total = rows * segs * 32;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t rs = e >> 5;
+  const unsigned total = (unsigned)rows * (unsigned)segs * 32u;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned rs = e >> 5;
     const int q = (int)(e & 31);
-    const int64_t i = rs / segs, s = rs - i * segs;
+    const unsigned i = rs / (unsigned)segs, s = rs - i * (unsigned)segs;
     int64_t row;
     int pattern;
     pass_row(i, single_k, kb, gbits, &row, &pattern);
     if (pattern == 0) continue;
-    const int64_t g = s * kInterior + (q < 16 ? q : kInterior - 32 + q);
+    const int64_t g = (int64_t)s * kInterior + (q < 16 ? q : kInterior - 32 + q);
     side[e] = g < N ? half[row * N + g] : mk<R>((R)0, (R)0);
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kTrotThreads) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
-                                                              const typename Cx<R>::T* __restrict__ side, int n_s,
-                                                              int64_t segs, int64_t rows, int single_k, int kb,
-                                                              int gbits, const LayerList* __restrict__ lists) {
-  using T = typename Cx<R>::T;
-  constexpr int per = 16 / sizeof(T);  // amplitudes per 16-byte unit
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * (kTrotThreads / 32) + (threadIdx.x >> 5);
-  if (gw >= rows * segs) return;  // warp-uniform: whole warps leave together
-  const int64_t N = 1LL << n_s;
-  const int64_t i = gw / segs, s = gw - i * segs;
-  int64_t row_idx;
-  int pattern;
-  pass_row(i, single_k, kb, gbits, &row_idx, &pattern);
-  if (pattern == 0) return;  // warp-uniform: this row has no bit of the group set
-  const LayerList* L = lists + pattern;
-  const int n_layers = L->n, first_o = L->first_o;
-  // the warp's layer rotations, one layer per lane, broadcast from shared memory
-  __shared__ float2 rot_all[kTrotThreads / 32][32];
-  __shared__ double rotd_all[kTrotThreads / 32][32][2];
-  if (lane < n_layers) {
-    if constexpr (sizeof(R) == 4) rot_all[threadIdx.x >> 5][lane] = make_float2((float)L->c[lane], (float)L->s[lane]);
-    else {
-      rotd_all[threadIdx.x >> 5][lane][0] = L->c[lane];
-      rotd_all[threadIdx.x >> 5][lane][1] = L->s[lane];
-    }
-  }
-  const int64_t g0 = s * kInterior;             // first interior amplitude
-  const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
-  T* row = half + row_idx * N;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-  // Staging buffer of this warp: 32 x kLaneAmps amplitudes as 16-byte chunks, chunk c of
-  // the window stored at position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both
-  // the coalesced pass (lane t <-> chunk q * 32 + t) and the blocked pass (lane t <-> its
-  // CPL consecutive chunks) spread over the banks.
+// One warp window: pass row i, segment s.
+struct Window {
+  int i, s;
+  int64_t row;
+  int pattern;
+  bool full;  // the 480-amplitude interior lies inside the row
+};
+
+__device__ __forceinline__ Window window_at(int i, int s, int64_t N, int single_k, int kb, int gbits) {
+  Window d;
+  d.i = i;
+  d.s = s;
+  pass_row(i, single_k, kb, gbits, &d.row, &d.pattern);
+  d.full = (int64_t)s * kInterior + kInterior <= N;
+  return d;
+}
+
+// Staging buffer of a warp: 32 x kLaneAmps amplitudes as 16-byte chunks, window chunk c
+// stored at position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both the coalesced
+// copy (lane t <-> chunk q * 32 + t) and the per-lane gather (lane t <-> its CPL consecutive
+// chunks) spread over the banks. Lane 0's chunks hold the left halo, lane 31's the right.
+template <class T>
+__device__ __forceinline__ void stage_issue(uint4* stage, const Window& d, const T* half, const T* side, int segs,
+                                            int64_t N, int lane) {
+  constexpr int per = 16 / sizeof(T);
   constexpr int CPL = kLaneAmps / per;
-  __shared__ uint4 stage_all[kTrotThreads / 32][32 * CPL];
-  uint4* stage = stage_all[threadIdx.x >> 5];
-  T x[kLaneAmps];
-  const bool full_interior = (g0 + kInterior <= N);  // warp-uniform
-  if (full_interior) {
-    // lanes 1..30 of the window = the 480 interior amplitudes: coalesced 16-byte loads
-    const uint4* src = reinterpret_cast<const uint4*>(row + g0);
-    constexpr int chunks = kInterior / per;  // 30 * CPL
+  if (d.pattern == 0 || !d.full) return;
+  const uint4* src = reinterpret_cast<const uint4*>(half + d.row * N + (int64_t)d.s * kInterior);
+  constexpr int chunks = kInterior / per;  // 30 * CPL
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-      const int c = q * 32 + lane;
-      if (c < chunks) {
-        const int wc = c + CPL;  // window chunk (lane 0 holds the left halo)
-        stage[wc ^ ((wc / CPL) & 7)] = src[c];
-      }
+  for (int q = 0; q < CPL; ++q) {
+    const int c = q * 32 + lane;
+    if (c < chunks) {
+      const int wc = c + CPL;
+      cp_async16(&stage[wc ^ ((wc / CPL) & 7)], src + c);
     }
-    __syncwarp();
-    if (lane > 0 && lane < 31) {
-      uint4* d = reinterpret_cast<uint4*>(x);
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const int wc = lane * CPL + q;
-        d[q] = stage[wc ^ (lane & 7)];
-      }
-    }
-  } else if (lane > 0 && lane < 31) {
-#pragma unroll
-    for (int q = 0; q < kLaneAmps; ++q) x[q] = lane0 + q < N ? row[lane0 + q] : mk<R>((R)0, (R)0);
   }
   if (lane == 0 || lane == 31) {
-    const int64_t ns = lane == 0 ? s - 1 : s + 1;
+    const int ns = lane == 0 ? d.s - 1 : d.s + 1;
     const int off = lane == 0 ? 16 : 0;  // the neighbour's last 16 / first 16
+    const int sw = lane & 7;
+    if (ns >= 0 && ns < segs) {
+      const uint4* hs = reinterpret_cast<const uint4*>(side + ((int64_t)d.i * segs + ns) * 32 + off);
 #pragma unroll
-    for (int q = 0; q < kLaneAmps; ++q)
-      x[q] = (ns >= 0 && ns < segs) ? side[(i * segs + ns) * 32 + off + q] : mk<R>((R)0, (R)0);
-  }
-
-  __syncwarp();
-  // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
-  const bool in_ok = lane0 >= 0 && lane0 + kLaneAmps - 2 <= N - 1;
-  const bool right_ok = lane < 31 && lane0 + kLaneAmps - 1 >= 1 && lane0 + kLaneAmps <= N - 1;
-  const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
-  for (int l = 0; l < n_layers; ++l) {
-    R c, sn;
-    if constexpr (sizeof(R) == 4) {
-      const float2 cs = rot_all[threadIdx.x >> 5][l];
-      c = cs.x;
-      sn = cs.y;
+      for (int q = 0; q < CPL; ++q) cp_async16(&stage[(lane * CPL + q) ^ sw], hs + q);
     } else {
-      c = rotd_all[threadIdx.x >> 5][l][0];
-      sn = rotd_all[threadIdx.x >> 5][l][1];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) stage[(lane * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (((l + first_o) & 1) == 0) {
-      // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
+  }
+}
+
+// Persistent warps: each warp walks the windows w = warp, warp + warps, ...; the copies of
+// its next window go to the second staging buffer (cp.async) while it computes the current.
+template <class R>
+__global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
+                                                              const typename Cx<R>::T* __restrict__ side, int n_s,
+                                                              int segs, int rows, int single_k, int kb, int gbits,
+                                                              const LayerList* __restrict__ lists) {
+  using T = typename Cx<R>::T;
+  constexpr int per = 16 / sizeof(T);  // amplitudes per 16-byte unit
+  constexpr int CPL = kLaneAmps / per;
+  extern __shared__ __align__(16) unsigned char trot_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint4* stage_w = reinterpret_cast<uint4*>(trot_smem) + (size_t)wid * 2 * 32 * CPL;  // two buffers
+  R* rot_w = reinterpret_cast<R*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)(kTrotThreads / 32) * 2 * 32 * CPL) +
+             (size_t)wid * 2 * 32;
+  const int64_t N = 1LL << n_s;
+  // windows w = warp, warp + nwarps, ... as (row i, segment s), stepped without division
+  const int nwarps = (int)gridDim.x * (kTrotThreads / 32);
+  const int w0 = (int)blockIdx.x * (kTrotThreads / 32) + wid;
+  const int step_i = nwarps / segs, step_s = nwarps - step_i * segs;
+  int i = w0 / segs, sg = w0 - (w0 / segs) * segs;
+  if (i >= rows) return;  // warp-uniform
+  Window cur = window_at(i, sg, N, single_k, kb, gbits);
+  stage_issue<T>(stage_w, cur, half, side, segs, N, lane);
+  cp_async_commit();
+  int buf = 0;
+  while (i < rows) {
+    sg += step_s;
+    i += step_i;
+    if (sg >= segs) {
+      sg -= segs;
+      ++i;
+    }
+    Window nxt;
+    if (i < rows) {
+      nxt = window_at(i, sg, N, single_k, kb, gbits);
+      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, nxt, half, side, segs, N, lane);
+    }
+    cp_async_commit();
+    cp_async_wait1();  // the current window's copies have landed
+    __syncwarp();
+    if (cur.pattern != 0) {
+      uint4* stage = stage_w + buf * 32 * CPL;
+      const LayerList* L = lists + cur.pattern;
+      const int n_layers = L->n, first_o = L->first_o;
+      if (lane < n_layers) {
+        rot_w[2 * lane] = (R)L->c[lane];
+        rot_w[2 * lane + 1] = (R)L->s[lane];
+      }
+      const int64_t g0 = (int64_t)cur.s * kInterior;               // first interior amplitude
+      const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
+      T* row = half + cur.row * N;
+      T x[kLaneAmps];
+      if (cur.full) {
+        uint4* d = reinterpret_cast<uint4*>(x);
 #pragma unroll
-      for (int q = 0; q < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
-    } else {
-      const T right = shfl_down1(x[0]);           // next lane's first amplitude
-      const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
-      if (in_ok) {
-#pragma unroll
-        for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+        for (int q = 0; q < CPL; ++q) d[q] = stage[(lane * CPL + q) ^ (lane & 7)];
       } else {
+        if (lane > 0 && lane < 31) {
 #pragma unroll
-        for (int q = 1; q + 1 < kLaneAmps; q += 2) {
-          const int64_t j = lane0 + q;
-          if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
+          for (int q = 0; q < kLaneAmps; ++q) x[q] = lane0 + q < N ? row[lane0 + q] : mk<R>((R)0, (R)0);
+        } else {
+          const int ns = lane == 0 ? cur.s - 1 : cur.s + 1;
+          const int off = lane == 0 ? 16 : 0;
+#pragma unroll
+          for (int q = 0; q < kLaneAmps; ++q)
+            x[q] = (ns >= 0 && ns < segs) ? side[((int64_t)cur.i * segs + ns) * 32 + off + q] : mk<R>((R)0, (R)0);
         }
       }
-      if (right_ok) {  // (this lane's last a, next lane's first b): a <- c a + i s b
-        const T a = x[kLaneAmps - 1];
-        x[kLaneAmps - 1] = mk<R>(c * a.x - sn * right.y, c * a.y + sn * right.x);
+      __syncwarp();
+      // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
+      const bool in_ok = lane0 >= 0 && lane0 + kLaneAmps - 2 <= N - 1;
+      const bool right_ok = lane < 31 && lane0 + kLaneAmps - 1 >= 1 && lane0 + kLaneAmps <= N - 1;
+      const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
+      for (int l = 0; l < n_layers; ++l) {
+        const R c = rot_w[2 * l], sn = rot_w[2 * l + 1];
+        if (((l + first_o) & 1) == 0) {
+          // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
+#pragma unroll
+          for (int q = 0; q < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+        } else {
+          const T right = shfl_down1(x[0]);           // next lane's first amplitude
+          const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
+          if (in_ok) {
+#pragma unroll
+            for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+          } else {
+#pragma unroll
+            for (int q = 1; q + 1 < kLaneAmps; q += 2) {
+              const int64_t j = lane0 + q;
+              if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
+            }
+          }
+          if (right_ok) {  // (this lane's last a, next lane's first b): a <- c a + i s b
+            const T a = x[kLaneAmps - 1];
+            x[kLaneAmps - 1] = mk<R>(c * a.x - sn * right.y, c * a.y + sn * right.x);
+          }
+          if (left_ok) {  // (previous lane's last a, this lane's first b): b <- i s a + c b
+            const T b = x[0];
+            x[0] = mk<R>(c * b.x - sn * left.y, c * b.y + sn * left.x);
+          }
+        }
       }
-      if (left_ok) {  // (previous lane's last a, this lane's first b): b <- i s a + c b
-        const T b = x[0];
-        x[0] = mk<R>(c * b.x - sn * left.y, c * b.y + sn * left.x);
+      {
+        const T ph = mk<R>((R)L->pc, (R)L->ps);
+#pragma unroll
+        for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
+      }
+      if (cur.full) {
+        if (lane > 0 && lane < 31) {
+          const uint4* sx = reinterpret_cast<const uint4*>(x);
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) stage[(lane * CPL + q) ^ (lane & 7)] = sx[q];
+        }
+        __syncwarp();
+        uint4* dst = reinterpret_cast<uint4*>(row + g0);
+        constexpr int chunks = kInterior / per;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const int c = q * 32 + lane;
+          if (c < chunks) {
+            const int wc = c + CPL;
+            dst[c] = stage[wc ^ ((wc / CPL) & 7)];
+          }
+        }
+      } else if (lane > 0 && lane < 31) {
+#pragma unroll
+        for (int q = 0; q < kLaneAmps; ++q)
+          if (lane0 + q < N) row[lane0 + q] = x[q];
       }
     }
+    __syncwarp();  // this buffer and the rotation table are free for the next issue
+    cur = nxt;
+    buf ^= 1;
   }
-  {
-    const T ph = mk<R>((R)L->pc, (R)L->ps);
-#pragma unroll
-    for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
-  }
-  if (full_interior) {
-    __syncwarp();
-    if (lane > 0 && lane < 31) {
-      const uint4* sx = reinterpret_cast<const uint4*>(x);
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const int wc = lane * CPL + q;
-        stage[wc ^ (lane & 7)] = sx[q];
-      }
-    }
-    __syncwarp();
-    uint4* dst = reinterpret_cast<uint4*>(row + g0);
-    constexpr int chunks = kInterior / per;
-#pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-      const int c = q * 32 + lane;
-      if (c < chunks) {
-        const int wc = c + CPL;
-        dst[c] = stage[wc ^ ((wc / CPL) & 7)];
-      }
-    }
-  } else if (lane > 0 && lane < 31) {
-#pragma unroll
-    for (int q = 0; q < kLaneAmps; ++q)
-      if (lane0 + q < N) row[lane0 + q] = x[q];
-  }
+}
+
+template <class R>
+size_t trotter_smem() {
+  constexpr int per = 16 / sizeof(typename Cx<R>::T);
+  constexpr int CPL = kLaneAmps / per;
+  return (size_t)(kTrotThreads / 32) * (2 * 32 * CPL * 16 + 2 * 32 * sizeof(R));
 }
 
 __global__ void k_interleave(const double* __restrict__ re, const double* __restrict__ im, int64_t n,
@@ -281,20 +335,30 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
   const int64_t segs = trotter_segments(p.N);
   T* side = (T*)p.d_scratch;  // sized by the planner for R * segs * 32 amplitudes
   const LayerList* lists = (const LayerList*)p.d_trot_lists;
+  const size_t smem = trotter_smem<R>();
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_trotter_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  HHL_CUDA_TRY(cudaGetDevice(&dev));
+  HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trotter_pass<R>, kTrotThreads, smem));
+  if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass does not fit an SM");
   for (const TrotPassDesc& d : p.trot_pass[adjoint ? 1 : 0]) {
     const int64_t rows = d.single_k >= 0 ? p.R / 2 : p.R;
     const int64_t warps = rows * segs;
     const int64_t grid = (warps + kTrotThreads / 32 - 1) / (kTrotThreads / 32);
-    if (grid > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "Trotter grid too large");
+    if (warps > 0x7fffffffLL - 4 * (int64_t)occ * sms * (kTrotThreads / 32))
+      return fail(HHL_ERR_UNSUPPORTED, "Trotter pass has too many windows");
     const int64_t edge_total = rows * segs * 32;
     int eg = (int)((edge_total + 255) / 256);
     if (eg > 152 * 16) eg = 152 * 16;
     HHL_PROF_BEGIN(st);
-    k_trotter_edges<R><<<eg, 256, 0, st>>>((const T*)half, side, p.n_s, segs, rows, d.single_k, d.kb, d.gbits);
+    k_trotter_edges<R><<<eg, 256, 0, st>>>((const T*)half, side, p.n_s, (int)segs, (int)rows, d.single_k, d.kb,
+                                           d.gbits);
     HHL_LAUNCH_CHECK("k_trotter_edges");
+    const unsigned pgrid = (unsigned)std::min<int64_t>(grid, (int64_t)occ * sms);
     HHL_PROF_BEGIN(st);
-    k_trotter_pass<R><<<(unsigned)grid, kTrotThreads, 0, st>>>((T*)half, side, p.n_s, segs, rows, d.single_k, d.kb,
-                                                               d.gbits, lists + d.list_off);
+    k_trotter_pass<R><<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)rows, d.single_k,
+                                                         d.kb, d.gbits, lists + d.list_off);
     HHL_LAUNCH_CHECK("k_trotter_pass");
   }
   return HHL_OK;
