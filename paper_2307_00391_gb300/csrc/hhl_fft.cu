@@ -546,7 +546,15 @@ struct SplitArgs {
   int lo, m, b0, nb;   // register at index bits [lo, lo + m); this pass: register bits [b0, b0 + nb)
   int log_cb;          // 2^log_cb column blocks (tiles) per row
   double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
+  float scale_f;       // the same in FP32 (GB300's FP64 pipe is narrow: no per-thread conversions)
+  int scaled;          // scale != 1
 };
+
+template <class R>
+__device__ __forceinline__ R split_scale(const SplitArgs& a) {
+  if constexpr (sizeof(R) == 4) return a.scale_f;
+  else return a.scale;
+}
 
 template <class T>
 struct SplitGeom {
@@ -722,10 +730,10 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
       tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)1, false);
     } else if (OP == kSplitHad) {
       tile_stages<T, NB, false, 1>(X, a.b0, lo_fixed, a.m, tw, false);
-      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)a.scale, a.scale != 1.0);
+      tile_store<T, NB>(dst, X, row_units, row0, a.b0, split_scale<R>(a), a.scaled != 0);
     } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
       tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
-      const R s = (R)a.scale;
+      const R s = split_scale<R>(a);
       const T* rot = static_cast<const T*>(a.rot);
       uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + base_amp);
       for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
@@ -792,6 +800,8 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   using T = typename Cx<R>::T;
   a.log_cb = a.lo - SplitGeom<T>::LW;
   a.region = 1LL << (a.lo + a.m);
+  a.scale_f = (float)a.scale;
+  a.scaled = a.scale != 1.0;
   a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
   switch (a.nb) {
     case 4: return launch_split_nb<R, OP, FULL, 4>(a, st, name);

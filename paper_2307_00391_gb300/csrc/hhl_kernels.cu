@@ -181,17 +181,19 @@ __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t 
   const V* u = reinterpret_cast<const V*>(S);
   const int64_t units = 2 * half / per, half_u = half / per, v_u = N / per;
   double a[3] = {0.0, 0.0, 0.0};
-  constexpr int U = 4;  // loads in flight per thread
+  constexpr int U = 4;      // loads in flight per thread
+  constexpr int FLUSH = 4;  // batches summed in the amplitude precision before each FP64 add
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // Up to U * FLUSH units (4 U FLUSH squares) are summed in the amplitude precision and then
+  // added to the FP64 totals: GB300's FP64 pipe is far narrower than its FP32 pipe, and one
+  // FP64 conversion and add per unit would bound the pass.
+  R s[3] = {(R)0, (R)0, (R)0};
+  int batches = 0;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < units; i0 += U * stride) {
     V z[U];
 #pragma unroll
     for (int k = 0; k < U; ++k)
       if (i0 + k * stride < units) z[k] = u[i0 + k * stride];
-    // The U units of one batch are summed in the amplitude precision (at most 4U squares)
-    // and added to the FP64 totals once: GB300's FP64 rate is far below its FP32 rate, and
-    // one FP64 conversion and add per unit would bound the pass.
-    R s[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int64_t i = i0 + k * stride;
@@ -209,10 +211,17 @@ __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t 
         if (i - half_u < v_u) s[2] += p;
       }
     }
-    a[0] += (double)s[0];
-    a[1] += (double)s[1];
-    a[2] += (double)s[2];
+    if (++batches == FLUSH) {
+      a[0] += (double)s[0];
+      a[1] += (double)s[1];
+      a[2] += (double)s[2];
+      s[0] = s[1] = s[2] = (R)0;
+      batches = 0;
+    }
   }
+  a[0] += (double)s[0];
+  a[1] += (double)s[1];
+  a[2] += (double)s[2];
   block_sum_atomic<3>(a, acc);
 }
 

@@ -52,7 +52,21 @@ struct LayerList {
   int first_o;             // 1 if layer 0 is an O layer
   double pc, ps;           // the pattern's summed E phase e^{i d (E time)} in this pass
   double c[kMaxPassLayers], s[kMaxPassLayers];  // cos / sin of each layer's rotation angle
+  // the same values rounded to FP32 on the host (GB300's FP64 conversions are slow)
+  float pcf, psf;
+  float cf[kMaxPassLayers], sf[kMaxPassLayers];
 };
+
+template <class R>
+__device__ __forceinline__ R layer_c(const LayerList* L, int l) {
+  if constexpr (sizeof(R) == 4) return L->cf[l];
+  else return L->c[l];
+}
+template <class R>
+__device__ __forceinline__ R layer_s(const LayerList* L, int l) {
+  if constexpr (sizeof(R) == 4) return L->sf[l];
+  else return L->s[l];
+}
 
 __device__ __forceinline__ int64_t row_with_bit_t(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
@@ -225,8 +239,8 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
       const LayerList* L = lists + cur.pattern;
       const int n_layers = L->n, first_o = L->first_o;
       if (lane < n_layers) {
-        rot_w[2 * lane] = (R)L->c[lane];
-        rot_w[2 * lane + 1] = (R)L->s[lane];
+        rot_w[2 * lane] = layer_c<R>(L, lane);
+        rot_w[2 * lane + 1] = layer_s<R>(L, lane);
       }
       const int64_t g0 = (int64_t)cur.s * kInterior;               // first interior amplitude
       const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
         }
       }
       {
-        const T ph = mk<R>((R)L->pc, (R)L->ps);
+        const T ph = sizeof(R) == 4 ? mk<R>((R)L->pcf, (R)L->psf) : mk<R>((R)L->pc, (R)L->ps);
 #pragma unroll
         for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
       }
@@ -401,6 +415,12 @@ void build_list(const Plan& p, const std::vector<int>& bits, bool adjoint, int w
   }
   out->pc = cos(e_time * dh);
   out->ps = sg * sin(e_time * dh);
+  out->pcf = (float)out->pc;
+  out->psf = (float)out->ps;
+  for (int l = 0; l < out->n; ++l) {
+    out->cf[l] = (float)out->c[l];
+    out->sf[l] = (float)out->s[l];
+  }
 }
 
 }  // namespace
