@@ -647,11 +647,20 @@ __device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, c
   }
 }
 
+__device__ __forceinline__ void split_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void split_cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void split_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
 // Tile rows <-> shared memory in 16-byte units. Thread t moves the units t + k * 256: its
 // column unit h = t & 15 is fixed and its row advances by 16 per k, so the global address
-// advances by a constant stride.
+// advances by a constant stride. Loads are asynchronous copies (cp.async), so a tile can be
+// fetched while the previous one is transformed.
 template <class T, int NB>
-__device__ __forceinline__ void tile_load(T* X, const T* base, long long row_units, long long row0, int b0) {
+__device__ __forceinline__ void tile_issue(T* X, const T* base, long long row_units, long long row0, int b0) {
   constexpr int upr = kSplitSegBytes / 16;
   constexpr int total = (1 << NB) * upr;
   constexpr int per_thread = total / kSplitThreads;
@@ -660,15 +669,8 @@ __device__ __forceinline__ void tile_load(T* X, const T* base, long long row_uni
   const uint4* src = reinterpret_cast<const uint4*>(base) + (row0 + ((long long)j0 << b0)) * row_units + h;
   const long long step = ((long long)(kSplitThreads / upr) << b0) * row_units;
   uint4* dst = reinterpret_cast<uint4*>(X) + threadIdx.x;
-  constexpr int U = per_thread < kSplitUnroll ? per_thread : kSplitUnroll;
 #pragma unroll
-  for (int k0 = 0; k0 < per_thread; k0 += U) {
-    uint4 v[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) v[k] = src[(k0 + k) * step];
-#pragma unroll
-    for (int k = 0; k < U; ++k) dst[(k0 + k) * kSplitThreads] = v[k];
-  }
+  for (int k = 0; k < per_thread; ++k) split_cp_async16(dst + k * kSplitThreads, src + k * step);
 }
 
 template <class T, int NB, class S>
@@ -693,52 +695,81 @@ __device__ __forceinline__ void tile_store(T* base, const T* X, long long row_un
   }
 }
 
+// Position of tile t: column block ib, fixed register bits f, outer block o.
+struct TilePos {
+  long long row0, base_amp;
+  int lo_fixed, hi_fixed;
+};
+
+template <int NB, int LW>
+__device__ __forceinline__ TilePos tile_pos(const SplitArgs& a, long long t) {
+  const int other = a.m - NB;
+  const long long ib = t & (((long long)1 << a.log_cb) - 1);
+  const long long rest = t >> a.log_cb;
+  const int f = (int)(rest & ((1LL << other) - 1));
+  const long long o = rest >> other;
+  TilePos q;
+  q.lo_fixed = f & ((1 << a.b0) - 1);
+  q.hi_fixed = f >> a.b0;
+  q.row0 = q.lo_fixed + ((long long)q.hi_fixed << (a.b0 + NB));
+  q.base_amp = o * a.region + (ib << LW);
+  return q;
+}
+
 template <class R, int OP, bool FULL, int NB>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
   constexpr int upr = kSplitSegBytes / 16;
   constexpr int per = 16 / sizeof(T);
+  constexpr size_t tile_amps = (size_t)1 << (NB + LW);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t0 = reinterpret_cast<T*>(smem_raw);
   T* t1 = t0 + 64;
-  T* X = t0 + twiddle_entries(a.m);
-  T* Y = X + ((size_t)1 << (NB + LW));
+  T* Xb = t0 + twiddle_entries(a.m);  // two tile buffers (double buffering), then Y
+  T* Y = Xb + 2 * tile_amps;
   if (OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
   const Twiddle<T> tw{t0, t1};
-  const int other = a.m - NB;
+  const int rows = 1 << NB;
   const long long row_units = ((long long)1 << a.lo) / per;  // 16-byte units per row
-  for (long long t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-    const long long ib = t & (((long long)1 << a.log_cb) - 1);
-    const long long rest = t >> a.log_cb;
-    const int f = (int)(rest & ((1LL << other) - 1));
-    const long long o = rest >> other;
-    const int lo_fixed = f & ((1 << a.b0) - 1);
-    const int hi_fixed = f >> a.b0;
-    const long long row0 = lo_fixed + ((long long)hi_fixed << (a.b0 + NB));
-    const long long base_amp = o * a.region + (ib << LW);
-    const T* src = static_cast<const T*>(a.src) + base_amp;
-    T* dst = static_cast<T*>(a.dst) + base_amp;
-    __syncthreads();  // the previous tile's shared-memory reads are done
-    tile_load<T, NB>(X, src, row_units, row0, a.b0);
-    __syncthreads();
+  long long t = blockIdx.x;
+  if (t >= a.tiles) return;  // block-uniform
+  {
+    const TilePos q = tile_pos<NB, LW>(a, t);
+    tile_issue<T, NB>(Xb, static_cast<const T*>(a.src) + q.base_amp, row_units, q.row0, a.b0);
+  }
+  split_cp_async_commit();
+  int buf = 0;
+  for (; t < a.tiles; t += gridDim.x) {
+    const long long tn = t + gridDim.x;
+    if (tn < a.tiles) {
+      const TilePos qn = tile_pos<NB, LW>(a, tn);
+      tile_issue<T, NB>(Xb + (buf ^ 1) * tile_amps, static_cast<const T*>(a.src) + qn.base_amp, row_units, qn.row0,
+                        a.b0);
+    }
+    split_cp_async_commit();
+    split_cp_async_wait1();
+    __syncthreads();  // the current tile has landed for every thread
+    const TilePos q = tile_pos<NB, LW>(a, t);
+    T* X = Xb + buf * tile_amps;
+    T* dst = static_cast<T*>(a.dst) + q.base_amp;
     if (OP == kSplitDif) {
-      tile_stages<T, NB, false, 0>(X, a.b0, lo_fixed, a.m, tw, false);
-      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)1, false);
+      tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
+      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
     } else if (OP == kSplitDit) {
-      tile_stages<T, NB, true, 0>(X, a.b0, lo_fixed, a.m, tw, true);
-      tile_store<T, NB>(dst, X, row_units, row0, a.b0, (R)1, false);
+      tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, a.m, tw, true);
+      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
     } else if (OP == kSplitHad) {
-      tile_stages<T, NB, false, 1>(X, a.b0, lo_fixed, a.m, tw, false);
-      tile_store<T, NB>(dst, X, row_units, row0, a.b0, split_scale<R>(a), a.scaled != 0);
+      tile_stages<T, NB, false, 1>(X, a.b0, q.lo_fixed, a.m, tw, false);
+      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
     } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
       tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
       const R s = split_scale<R>(a);
       const T* rot = static_cast<const T*>(a.rot);
-      uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + base_amp);
+      uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + q.base_amp);
       for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
         const int j = u / upr, h = u - j * upr;
-        const int y = bitrev_m(j + (hi_fixed << NB), a.m);
+        const int y = bitrev_m(j + (q.hi_fixed << NB), a.m);
         const T r = rot[y];
         uint4 xv = reinterpret_cast<uint4*>(X)[u];
         uint4 keep, yv;
@@ -746,11 +777,11 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
         T* kt = reinterpret_cast<T*>(&keep);
         T* yt = reinterpret_cast<T*>(&yv);
 #pragma unroll
-        for (int q = 0; q < per; ++q) {
-          const T x = cscale(xt[q], s);
-          if (FULL) yt[q] = cscale(x, r.x * s);
-          else kt[q] = cscale(x, r.x);
-          xt[q] = cscale(x, r.y * s);
+        for (int e = 0; e < per; ++e) {
+          const T x = cscale(xt[e], s);
+          if (FULL) yt[e] = cscale(x, r.x * s);
+          else kt[e] = cscale(x, r.x);
+          xt[e] = cscale(x, r.y * s);
         }
         reinterpret_cast<uint4*>(X)[u] = xv;
         if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
@@ -759,10 +790,13 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
       __syncthreads();
       tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
       if (FULL) tile_stages<T, NB, true, 0>(Y, 0, 0, a.m, tw, true);
-      tile_store<T, NB>(dst, X, row_units, row0, 0, (R)1, false);
-      if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, row0, 0, (R)1, false);
+      tile_store<T, NB>(dst, X, row_units, q.row0, 0, (R)1, false);
+      if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, q.row0, 0, (R)1, false);
     }
+    __syncthreads();  // this buffer is read out before it is refilled
+    buf ^= 1;
   }
+  (void)rows;
 }
 
 // The split path serves registers of 8..14 bits whose rows hold at least one 256-byte segment,
@@ -780,7 +814,7 @@ template <class R, int OP, bool FULL, int NB>
 hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
   const size_t tile = ((size_t)1 << (NB + SplitGeom<T>::LW)) * sizeof(T);
-  const size_t smem = (size_t)twiddle_entries(a.m) * sizeof(T) + ((OP == kSplitMid && FULL) ? 2 : 1) * tile;
+  const size_t smem = (size_t)twiddle_entries(a.m) * sizeof(T) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
   auto kern = k_split_pass<R, OP, FULL, NB>;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;

@@ -174,21 +174,28 @@ __global__ void k_rows_scatter(typename Cx<R>::T* __restrict__ S, const typename
 
 // FP64 sums of |S0|^2, |S1|^2 and |v|^2 (v = first row of S1), read in 16-byte units; the
 // squares of one unit are added in the amplitude precision, the running sums are FP64.
+// s - c <- s - c + p (compensated summation; c holds the negated lost low-order part)
+template <class R>
+__device__ __forceinline__ void kahan_add(R& s, R& c, R p) {
+  const R y = p - c;
+  const R t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 template <class R>
 __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N, double* acc) {
   constexpr int per = 16 / sizeof(typename Cx<R>::T);  // amplitudes per 16-byte unit
   using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
   const V* u = reinterpret_cast<const V*>(S);
   const int64_t units = 2 * half / per, half_u = half / per, v_u = N / per;
-  double a[3] = {0.0, 0.0, 0.0};
-  constexpr int U = 4;      // loads in flight per thread
-  constexpr int FLUSH = 4;  // batches summed in the amplitude precision before each FP64 add
+  constexpr int U = 4;  // loads in flight per thread
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // Up to U * FLUSH units (4 U FLUSH squares) are summed in the amplitude precision and then
-  // added to the FP64 totals: GB300's FP64 pipe is far narrower than its FP32 pipe, and one
-  // FP64 conversion and add per unit would bound the pass.
-  R s[3] = {(R)0, (R)0, (R)0};
-  int batches = 0;
+  // Each thread sums its squares in the amplitude precision with compensated (Kahan)
+  // summation, so the partial carries about one rounding error whatever its length, and
+  // converts it to FP64 once; the block and grid totals are FP64. (GB300's FP64 pipe is far
+  // narrower than its FP32 pipe: an FP64 conversion and add per amplitude would bound the pass.)
+  R s[3] = {(R)0, (R)0, (R)0}, c[3] = {(R)0, (R)0, (R)0};
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < units; i0 += U * stride) {
     V z[U];
 #pragma unroll
@@ -205,23 +212,14 @@ __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t 
         p = z[k].x * z[k].x + z[k].y * z[k].y;
       }
       if (i < half_u) {
-        s[0] += p;
+        kahan_add(s[0], c[0], p);
       } else {
-        s[1] += p;
-        if (i - half_u < v_u) s[2] += p;
+        kahan_add(s[1], c[1], p);
+        if (i - half_u < v_u) kahan_add(s[2], c[2], p);
       }
     }
-    if (++batches == FLUSH) {
-      a[0] += (double)s[0];
-      a[1] += (double)s[1];
-      a[2] += (double)s[2];
-      s[0] = s[1] = s[2] = (R)0;
-      batches = 0;
-    }
   }
-  a[0] += (double)s[0];
-  a[1] += (double)s[1];
-  a[2] += (double)s[2];
+  double a[3] = {(double)s[0] - (double)c[0], (double)s[1] - (double)c[1], (double)s[2] - (double)c[2]};
   block_sum_atomic<3>(a, acc);
 }
 
