@@ -89,7 +89,7 @@ typedef enum hhl_precision {
 } hhl_precision;
 
 typedef enum hhl_gemm_impl {
-  HHL_GEMM_AUTO = 0,    /* tensor cores (tcgen05, split TF32) for complex64 where built */
+  HHL_GEMM_AUTO = 0,    /* tensor cores (tcgen05, split FP16) for complex64 where built */
   HHL_GEMM_SIMT = 1,    /* CUDA-core FMA tiles (FP32 or FP64) */
   HHL_GEMM_TCGEN05 = 2  /* force the tcgen05 path (complex64 only) */
 } hhl_gemm_impl;

@@ -754,6 +754,7 @@ hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* 
   int tc_err = 0;
   if (int* ef = hhl::tc_error_flag(p)) HHL_CUDA_TRY(cudaMemcpyAsync(&tc_err, ef, sizeof(int), cudaMemcpyDeviceToHost, st));
   HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  if (tc_err == 4) return fail(HHL_ERR_NUMERIC, "an amplitude of magnitude >= 2 reached the FP16 tensor-core operands");
   if (tc_err != 0) return fail(HHL_ERR_TIMEOUT, "a bounded wait in the tcgen05 GEMM ran out (stage " + std::to_string(tc_err) + ")");
   out->p_success = sc[0];
   out->p_anc1 = sc[1];

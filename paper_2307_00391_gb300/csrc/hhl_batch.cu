@@ -3,7 +3,7 @@
 //
 // Each instance is the same circuit as the single-plan path (same kernels). What changes is
 // how the controlled products get their operands: a batch of a few hundred instances cannot
-// hold every U_k (at N = 4096 the split-TF32 operands of one instance alone are ~13 GB), so
+// hold every U_k (at N = 4096 the split-FP16 operands of one instance alone are ~6.4 GB), so
 // every U_k is generated just in time from the eigen-decomposition of the Toeplitz
 // tridiagonal A. With v_j(i) = sqrt(2/(N+1)) sin(i j pi/(N+1)), the product formula
 // sin a sin b = (cos(a-b) - cos(a+b))/2 turns U_k = V diag(e^{i lambdahat_j t_k}) V^T into
@@ -11,7 +11,7 @@
 //     g_k(d) = 1/(N+1) sum_{j=1..N} cos(d j pi/(N+1)) e^{i lambdahat_j t_k},
 // so one FP64 kernel computes the 2N+2 values of g_k for every k of an instance (O(N^2)
 // each), and one expansion kernel writes the GEMM operand of a controlled product (the
-// split-TF32 real embedding for the tensor-core GEMM, or the complex64 matrix for the
+// split-FP16 real embedding for the tensor-core GEMM, or the complex64 matrix for the
 // CUDA-core GEMM) into a per-stream workspace right before it is used.
 //
 // Instances are spread over worker streams by decreasing GEMM work (longest processing
@@ -27,6 +27,8 @@
 #include <algorithm>
 #include <numeric>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "hhl_common.cuh"
 
@@ -63,10 +65,14 @@ __global__ void __launch_bounds__(256) k_ugen_g(int N, const double2* __restrict
   }
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// v (scaled by 2^15) -> FP16 hi = nearest(v), lo = nearest(v - hi), as the tcgen05 GEMM expects.
+__device__ __forceinline__ void f16_split(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
 // U_k[n][m] = g(|n-m|) - g(n+m+2) (0-based n, m) from the double-float table, in FP32: the
@@ -76,11 +82,12 @@ __device__ __forceinline__ float2 u_elem(const float4* __restrict__ g, int n, in
   return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
 }
 
-// Split-TF32 real embedding of U_k (adjoint: U_k^dagger = conj(U_k), A real symmetric):
-// hi / lo (2N x 2N), rows = output real column, columns = input real index. One thread per
-// (n, m) writes the 2 x 2 block [[Re, -Im], [Im, Re]] at rows 2n, 2n+1 and columns 2m, 2m+1.
-__global__ void k_ugen_embed_tc(int n_s, const float4* __restrict__ g, int adjoint, float* __restrict__ hi,
-                                float* __restrict__ lo) {
+// Split-FP16 real embedding of U_k (adjoint: U_k^dagger = conj(U_k), A real symmetric),
+// scaled by 2^15: hi / lo (2N x 2N), rows = output real column, columns = input real index.
+// One thread per (n, m) writes the 2 x 2 block [[Re, -Im], [Im, Re]] at rows 2n, 2n+1 and
+// columns 2m, 2m+1.
+__global__ void k_ugen_embed_tc(int n_s, const float4* __restrict__ g, int adjoint, __half* __restrict__ hi,
+                                __half* __restrict__ lo) {
   const int N = 1 << n_s;
   const int64_t N2 = 2LL * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
@@ -88,13 +95,15 @@ __global__ void k_ugen_embed_tc(int n_s, const float4* __restrict__ g, int adjoi
     const int n = (int)(e >> n_s), m = (int)(e & (N - 1));
     float2 u = u_elem(g, n, m);
     if (adjoint) u.y = -u.y;
-    const float hr = tf32_rna(u.x), hi_ = tf32_rna(u.y);
-    const float lr = tf32_rna(u.x - hr), li = tf32_rna(u.y - hi_);
+    __half hr, hi_, lr, li;
+    f16_split(u.x * 32768.0f, hr, lr);
+    f16_split(u.y * 32768.0f, hi_, li);
+    const __half nhi = __hneg(hi_), nli = __hneg(li);
     const int64_t r0 = (2LL * n) * N2 + 2LL * m, r1 = r0 + N2;
-    *reinterpret_cast<float2*>(hi + r0) = make_float2(hr, -hi_);
-    *reinterpret_cast<float2*>(hi + r1) = make_float2(hi_, hr);
-    *reinterpret_cast<float2*>(lo + r0) = make_float2(lr, -li);
-    *reinterpret_cast<float2*>(lo + r1) = make_float2(li, lr);
+    *reinterpret_cast<uint32_t*>(hi + r0) = pack_h2(hr, nhi);
+    *reinterpret_cast<uint32_t*>(hi + r1) = pack_h2(hi_, hr);
+    *reinterpret_cast<uint32_t*>(lo + r0) = pack_h2(lr, nli);
+    *reinterpret_cast<uint32_t*>(lo + r1) = pack_h2(li, lr);
   }
 }
 
@@ -114,9 +123,9 @@ struct Work {
   cudaStream_t s = nullptr;
   cudaEvent_t done = nullptr;
   int64_t capN = 0, cap_msub = 0;
-  void* ubuf = nullptr;    // operand: tc hi|lo (2 x 4N^2 floats) or simt (N^2 complex64)
-  float* a_hi = nullptr;   // tc split rows (M_sub x 2N)
-  float* a_lo = nullptr;
+  void* ubuf = nullptr;    // operand: tc hi|lo (2 x 4N^2 FP16) or simt (N^2 complex64)
+  __half* a_hi = nullptr;  // tc split rows (M_sub x 2N FP16)
+  __half* a_lo = nullptr;
   void* scratch = nullptr; // simt GEMM output rows (M_sub x N complex64)
 };
 
@@ -212,8 +221,8 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
       HHL_LAUNCH_CHECK("k_ugen_embed_simt");
       return launch_ctrl_u_simt(p, adjoint ? (void*)s1 : (void*)s0, k, w.ubuf, st);
     }
-    float* hi = (float*)w.ubuf;
-    float* lo = hi + N2 * N2;
+    __half* hi = (__half*)w.ubuf;
+    __half* lo = hi + N2 * N2;
     int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
     HHL_PROF_BEGIN(st);
     k_ugen_embed_tc<<<g, 256, 0, st>>>(p.n_s, gk, adjoint ? 1 : 0, hi, lo);
@@ -363,9 +372,11 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
   for (auto& w : B->work) {
     if (!ok) break;
     const int64_t N2 = 2 * w.capN;
-    ok = alloc(&w.ubuf, (size_t)2 * N2 * N2 * sizeof(float)) && alloc((void**)&w.a_hi, (size_t)w.cap_msub * N2 * 4) &&
-         alloc((void**)&w.a_lo, (size_t)w.cap_msub * N2 * 4) && alloc(&w.scratch, (size_t)w.cap_msub * w.capN * 8);
-    B->work_bytes += (size_t)2 * N2 * N2 * 4 + 2 * (size_t)w.cap_msub * N2 * 4 + (size_t)w.cap_msub * w.capN * 8;
+    // ubuf holds the FP16 hi|lo embedding (2 x 4 N^2 x 2 bytes) or the complex64 SIMT operand
+    // (N^2 x 8 bytes), whichever the instances of this stream need (16 N^2 bytes cover both)
+    ok = alloc(&w.ubuf, (size_t)2 * N2 * N2 * sizeof(__half)) && alloc((void**)&w.a_hi, (size_t)w.cap_msub * N2 * 2) &&
+         alloc((void**)&w.a_lo, (size_t)w.cap_msub * N2 * 2) && alloc(&w.scratch, (size_t)w.cap_msub * w.capN * 8);
+    B->work_bytes += (size_t)2 * N2 * N2 * 2 + 2 * (size_t)w.cap_msub * N2 * 2 + (size_t)w.cap_msub * w.capN * 8;
     if (ok) ok = cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) == cudaSuccess;
   }
@@ -405,8 +416,8 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
       const int64_t N2 = 2 * p.N;
       hhl_status s = tc_make_map(&m4[0], w.a_hi, N2, p.R / 2, 128);
       if (s == HHL_OK) s = tc_make_map(&m4[1], w.a_lo, N2, p.R / 2, 128);
-      if (s == HHL_OK) s = tc_make_map(&m4[2], (float*)w.ubuf, N2, N2, B->gemm[i]);
-      if (s == HHL_OK) s = tc_make_map(&m4[3], (float*)w.ubuf + N2 * N2, N2, N2, B->gemm[i]);
+      if (s == HHL_OK) s = tc_make_map(&m4[2], (__half*)w.ubuf, N2, N2, B->gemm[i]);
+      if (s == HHL_OK) s = tc_make_map(&m4[3], (__half*)w.ubuf + N2 * N2, N2, N2, B->gemm[i]);
       if (s != HHL_OK) {
         free_batch(B);
         return s;
@@ -527,6 +538,7 @@ hhl_status hhl_batch_run_host(hhl_batch_t b, const double* b_host, double* out_h
   HHL_CUDA_TRY(cudaStreamSynchronize(st));
   int err = 0;
   HHL_CUDA_TRY(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err == 4) return fail(HHL_ERR_NUMERIC, "an amplitude of magnitude >= 2 reached the FP16 tensor-core operands");
   if (err) return fail(HHL_ERR_TIMEOUT, "a bounded wait in the tcgen05 GEMM ran out");
   return HHL_OK;
 }

@@ -138,17 +138,18 @@ bool tc_supported(const Plan& p);
 hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t st);
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
 void tc_free(Plan& p);
-int* tc_error_flag(const Plan& p);  // device flag set when a bounded wait in the GEMM ran out
+int* tc_error_flag(const Plan& p);  // device flag: 1-3 a bounded GEMM wait ran out, 4 operand out of range
 }  // namespace hhl
 #include <cuda.h>
 namespace hhl {
-// The split-TF32 tcgen05 GEMM with explicit operands (row gather + GEMM of one controlled
-// product): bn = 128 or 256 output real columns per CTA; the maps describe a_hi / a_lo
-// (M_sub x 2N) and the embedded operand hi / lo (2N x 2N) with boxes (32 x 128) and (32 x bn).
-hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi, float* a_lo,
+// The split-FP16 tcgen05 GEMM with explicit operands (row gather + GEMM of one controlled
+// product): bn = 128 or 256 output real columns per CTA; the maps describe the FP16 a_hi /
+// a_lo (M_sub x 2N) and the embedded operand hi / lo (2N x 2N, both scaled by 2^15) with
+// boxes (64 x 128) and (64 x bn).
+hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo,
                           const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
                           const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
-hhl_status tc_make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows);
+hhl_status tc_make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows);
 hhl_status tc_init_kernels();
 
 }  // namespace hhl

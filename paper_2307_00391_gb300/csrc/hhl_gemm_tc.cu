@@ -7,23 +7,29 @@
 // E[2n+1][2m] = Im U[n][m], E[2n+1][2m+1] = Re U[n][m]. Its flops equal the complex GEMM's
 // 8 M N N.
 //
-// FP32 accuracy from TF32 tensor cores (split TF32): every operand is split as
-// v ~ hi + lo with hi = v rounded to nearest TF32 and lo = (v - hi) rounded to nearest TF32
-// (round-to-nearest keeps the splitting error unbiased, so the norm does not drift over
-// the 2 n_c controlled products), and the product is
-// X_hi E_hi + X_hi E_lo + X_lo E_hi, accumulated in FP32 in tensor memory (three
-// kind::tf32 MMAs per K step). The plan stores E_hi and E_lo (forward and adjoint) for
-// every k; a gather kernel copies the rows with bit k set into compact X_hi / X_lo arrays,
-// so the GEMM may write its result straight back into those state rows.
+// FP32 accuracy from FP16 tensor cores (split FP16): both operands are scaled by 2^15
+// (|amplitude| <= 1 in a normalised state and |U entry| <= 1, so the scaled values stay
+// below the FP16 maximum 65504) and split as v ~ hi + lo, hi = v rounded to the nearest FP16,
+// lo = (v - hi) rounded to the nearest FP16 (round to nearest keeps the splitting error
+// unbiased, so the norm does not drift over the 2 n_c controlled products). The product is
+// X_hi E_hi + X_hi E_lo + X_lo E_hi, accumulated in FP32 in tensor memory (three kind::f16
+// MMAs per K step, A and B both FP16), and the epilogue multiplies by 2^-30. Each part carries
+// 11 significant bits, so the represented operands hold about 22 bits, as split TF32 does, at
+// twice the TF32 tensor rate and with half the operand bytes. The row gather flags any
+// amplitude of magnitude >= 2 (outside the scaled FP16 range) as a numeric error.
+// The plan stores E_hi and E_lo (forward and adjoint) for every k; the gather kernel copies
+// the rows with bit k set into compact X_hi / X_lo arrays, so the GEMM may write its result
+// straight back into those state rows.
 //
-// Kernel: one CTA of 128 threads per 128 x 256 output tile. Warp 0 (one lane) issues TMA
+// Kernel: one CTA of 128 threads per 128 x BN output tile. Warp 0 (one lane) issues TMA
 // loads (128-byte swizzle) into a 2-stage shared-memory ring, warp 1 (one lane) issues the
-// MMAs (M = 128, N = 256, K = 8) into a 256-column TMEM accumulator, and all four warps
+// MMAs (M = 128, N = BN, K = 16) into a BN-column TMEM accumulator, and all four warps
 // drain TMEM with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. output rows) and
 // store the rows. Every mbarrier wait is bounded; on expiry the CTA records an error flag
 // (read back as HHL_ERR_TIMEOUT), skips the remaining work, frees its TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <stdlib.h>
 
 #include "hhl_common.cuh"
@@ -34,11 +40,13 @@ namespace {
 
 constexpr int kBM = 128;           // output rows per CTA (MMA M)
 constexpr int kBN = 256;           // output real columns per CTA (MMA N), plan path
-constexpr int kBK = 32;            // fp32 K elements per stage (128 bytes: one swizzle row)
+constexpr int kBK = 64;            // fp16 K elements per stage (128 bytes: one swizzle row)
 constexpr int kStages = 2;
-constexpr int kTileA = kBM * kBK * 4;   // 16 KiB
+constexpr int kTileA = kBM * kBK * 2;   // 16 KiB
+constexpr float kOpScale = 32768.0f;    // 2^15 on each operand
+constexpr float kUnscale = 1.0f / (32768.0f * 32768.0f);  // 2^-30 on the product
 template <int BN> struct TcShape {
-  static constexpr int kTileB = BN * kBK * 4;                     // 32 KiB at BN = 256
+  static constexpr int kTileB = BN * kBK * 2;                     // 32 KiB at BN = 256
   static constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;     // A_hi, A_lo, B_hi, B_lo
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
   static constexpr int kTmemCols = BN;                            // fp32 accumulator columns
@@ -46,10 +54,10 @@ template <int BN> struct TcShape {
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcState {
-  float* a_hi = nullptr;  // M_sub x 2N
-  float* a_lo = nullptr;
-  float* b = nullptr;     // n_c x {fwd_hi, fwd_lo, adj_hi, adj_lo} x (2N x 2N)
-  int* err = nullptr;     // device error flag
+  __half* a_hi = nullptr;  // M_sub x 2N
+  __half* a_lo = nullptr;
+  __half* b = nullptr;     // n_c x {fwd_hi, fwd_lo, adj_hi, adj_lo} x (2N x 2N)
+  int* err = nullptr;      // device error flag
   int bn = kBN;           // output tile width (128 or 256)
   std::vector<CUtensorMap> maps;  // [0] A_hi, [1] A_lo, then per k: fwd_hi, fwd_lo, adj_hi, adj_lo
 };
@@ -107,16 +115,16 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor: kind::f16, D = F32, A = B = F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
@@ -141,11 +149,10 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Round to the nearest TF32 value (10 explicit mantissa bits), ties away from zero.
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// v (already scaled by 2^15) -> (hi, lo): hi = nearest FP16, lo = nearest FP16 of v - hi.
+__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
 }
 
 __device__ __forceinline__ int64_t row_with_bit_tc(int64_t i, int k) {
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = idesc_tf32(kBM, BN);
+    constexpr uint32_t idesc = idesc_f16(kBM, BN);
     bool ok = true;
     for (int it = 0; it < k_iters; ++it) {
       const int s = it % kStages;
@@ -221,12 +228,12 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t st = base + s * kStageBytes;
       const uint32_t a_hi = st, a_lo = st + kTileA, b_hi = st + 2 * kTileA, b_lo = st + 2 * kTileA + kTileB;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzled row
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint32_t off = kk * 32;  // 16 fp16 = 32 bytes along K inside the swizzled row
         const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
-        mma_tf32(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
-        mma_tf32(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+        mma_f16(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
+        mma_f16(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+        mma_f16(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
       }
       mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
     }
@@ -250,7 +257,9 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld_32cols(lane_addr + c, v);
       float4* d4 = reinterpret_cast<float4*>(dst + c);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      for (int q = 0; q < 8; ++q)
+        d4[q] = make_float4(v[4 * q] * kUnscale, v[4 * q + 1] * kUnscale, v[4 * q + 2] * kUnscale,
+                            v[4 * q + 3] * kUnscale);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -260,13 +269,15 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-// Rows with clock bit k set -> compact TF32 hi / lo arrays (M_sub x 2N floats).
-__global__ void k_tc_split_rows(const float4* __restrict__ half, float4* __restrict__ a_hi, float4* __restrict__ a_lo,
-                                int n_s, int k, int64_t m_sub) {
+// Rows with clock bit k set -> compact FP16 hi / lo arrays (M_sub x 2N), scaled by 2^15.
+// An amplitude component of magnitude >= 2 cannot be represented: error flag 4.
+__global__ void k_tc_split_rows(const float4* __restrict__ half, uint2* __restrict__ a_hi, uint2* __restrict__ a_lo,
+                                int n_s, int k, int64_t m_sub, int* err) {
   const int row4_bits = n_s - 1;  // float4 per row = 2N/4 = 2^(n_s-1)
   const int64_t total = m_sub << row4_bits;
   constexpr int U = 4;  // loads in flight per thread
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
   for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total; e0 += U * stride) {
     float4 v[U];
 #pragma unroll
@@ -281,19 +292,27 @@ __global__ void k_tc_split_rows(const float4* __restrict__ half, float4* __restr
     for (int q = 0; q < U; ++q) {
       const int64_t e = e0 + q * stride;
       if (e < total) {
-        const float4 h = make_float4(to_tf32(v[q].x), to_tf32(v[q].y), to_tf32(v[q].z), to_tf32(v[q].w));
-        a_hi[e] = h;
-        a_lo[e] = make_float4(to_tf32(v[q].x - h.x), to_tf32(v[q].y - h.y), to_tf32(v[q].z - h.z),
-                              to_tf32(v[q].w - h.w));
+        const float x[4] = {v[q].x * kOpScale, v[q].y * kOpScale, v[q].z * kOpScale, v[q].w * kOpScale};
+        __half h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          split_f16(x[j], h[j], l[j]);
+          bad |= !(fabsf(x[j]) < 2.0f * kOpScale);
+        }
+        a_hi[e] = make_uint2((uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16),
+                             (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16));
+        a_lo[e] = make_uint2((uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16),
+                             (uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16));
       }
     }
   }
+  if (bad) atomicExch(err, 4);
 }
 
-// Real embeddings of U_k (forward) and U_k^dagger (adjoint), split into TF32 hi / lo.
-// out layout: [fwd_hi | fwd_lo | adj_hi | adj_lo], each (2N x 2N) row-major with rows =
-// output real column, columns = input real index (K-major B operand).
-__global__ void k_tc_prep_b(const double2* __restrict__ U, int64_t N, float* __restrict__ out) {
+// Real embeddings of U_k (forward) and U_k^dagger (adjoint), scaled by 2^15 and split into
+// FP16 hi / lo. out layout: [fwd_hi | fwd_lo | adj_hi | adj_lo], each (2N x 2N) row-major with
+// rows = output real column, columns = input real index (K-major B operand).
+__global__ void k_tc_prep_b(const double2* __restrict__ U, int64_t N, __half* __restrict__ out) {
   const int64_t N2 = 2 * N, sz = N2 * N2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sz; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t nr = e / N2, kr = e - nr * N2;
@@ -302,13 +321,13 @@ __global__ void k_tc_prep_b(const double2* __restrict__ U, int64_t N, float* __r
     const double2 uf = U[n * N + m];
     const double2 ua = U[m * N + n];
     const double ar = ua.x, ai = -ua.y;  // (U^dagger)[n][m] = conj(U[m][n])
-    const double vf = s == 0 ? (t == 0 ? uf.x : -uf.y) : (t == 0 ? uf.y : uf.x);
-    const double va = s == 0 ? (t == 0 ? ar : -ai) : (t == 0 ? ai : ar);
-    const float hf = to_tf32((float)vf), ha = to_tf32((float)va);
+    const double vf = (s == 0 ? (t == 0 ? uf.x : -uf.y) : (t == 0 ? uf.y : uf.x)) * (double)kOpScale;
+    const double va = (s == 0 ? (t == 0 ? ar : -ai) : (t == 0 ? ai : ar)) * (double)kOpScale;
+    const __half hf = __float2half_rn((float)vf), ha = __float2half_rn((float)va);
     out[e] = hf;
-    out[sz + e] = to_tf32((float)(vf - (double)hf));
+    out[sz + e] = __float2half_rn((float)(vf - (double)__half2float(hf)));
     out[2 * sz + e] = ha;
-    out[3 * sz + e] = to_tf32((float)(va - (double)ha));
+    out[3 * sz + e] = __float2half_rn((float)(va - (double)__half2float(ha)));
   }
 }
 
@@ -324,14 +343,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-hhl_status make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+hhl_status make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
   auto fn = encode_fn();
   if (fn == nullptr) return fail(HHL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * sizeof(float)};
+  cuuint64_t strides[1] = {cols * sizeof(__half)};
   cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(HHL_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -357,15 +376,15 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
   if (t == nullptr) {
     t = new TcState();
     p.d_tc = t;
-    const size_t abytes = (size_t)(p.R / 2) * N2 * sizeof(float);
+    const size_t abytes = (size_t)(p.R / 2) * N2 * sizeof(__half);
     if (cudaMalloc(&t->a_hi, abytes) != cudaSuccess || cudaMalloc(&t->a_lo, abytes) != cudaSuccess ||
-        cudaMalloc(&t->b, (size_t)p.n_c * 4 * mat * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&t->b, (size_t)p.n_c * 4 * mat * sizeof(__half)) != cudaSuccess ||
         cudaMalloc(&t->err, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       return fail(HHL_ERR_OOM, "tcgen05 operand allocation failed");
     }
     p.workspace_bytes += 2 * abytes;
-    p.table_bytes += (size_t)p.n_c * 4 * mat * sizeof(float);
+    p.table_bytes += (size_t)p.n_c * 4 * mat * sizeof(__half);
     HHL_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), st));
     // tile width: 256 unless HHL_TC_BN=128 (tuning) or the operand is narrower
     if (const char* env = getenv("HHL_TC_BN")) t->bn = atoi(env) == 128 ? 128 : 256;
@@ -395,7 +414,7 @@ hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cuda
   return launch_tc_gemm(p.n_s, p.R / 2, k, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn, t->err, st);
 }
 
-hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi, float* a_lo, const CUtensorMap& map_ahi,
+hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo, const CUtensorMap& map_ahi,
                           const CUtensorMap& map_alo, const CUtensorMap& map_bhi, const CUtensorMap& map_blo, int bn,
                           int* err, cudaStream_t st) {
   const int64_t N2 = 2LL << n_s;
@@ -403,7 +422,7 @@ hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, float* a_hi
   int g = (int)((total4 + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
   HHL_PROF_BEGIN(st);
-  k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (float4*)a_hi, (float4*)a_lo, n_s, k, m_sub);
+  k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (uint2*)a_hi, (uint2*)a_lo, n_s, k, m_sub, err);
   HHL_LAUNCH_CHECK("k_tc_split_rows");
   if (bn == 256) {
     dim3 grid((unsigned)(N2 / 256), (unsigned)(m_sub / kBM));
@@ -428,7 +447,7 @@ hhl_status tc_init_kernels() {
   return HHL_OK;
 }
 
-hhl_status tc_make_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+hhl_status tc_make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
   return make_map(map, base, cols, rows, box_rows);
 }
 
