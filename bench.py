@@ -57,8 +57,8 @@ WORKLOADS = {
 # SHA-256 prefix of the kernel's source file at capture time: reported only while the source is
 # unchanged (otherwise null, the counters no longer describe the kernel).
 KERNEL_TRAFFIC = {
-    ("poiseuille_2p18", "k_trotter_pass"): (23611299072.0, "hhl_trotter.cu", "6e892b5cac35b7f9"),
-    ("couette_1024", "k_ctrl_gemm_tc"): (67300515.6, "hhl_gemm_tc.cu", "32bdfd605cd0eba1"),  # split-TF32 capture
+    ("poiseuille_2p18", "k_trotter_pass"): (23611334784.0, "hhl_trotter.cu", "6e892b5cac35b7f9"),
+    ("couette_1024", "k_ctrl_gemm_tc"): (33605361.8, "hhl_gemm_tc.cu", "b3fc4e648ee914d8"),
 }
 
 
