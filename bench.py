@@ -57,13 +57,13 @@ WORKLOADS = {
 # SHA-256 prefix of the kernel's source file at capture time: reported only while the source is
 # unchanged (otherwise null, the counters no longer describe the kernel).
 KERNEL_TRAFFIC = {
-    ("poiseuille_2p18", "k_trotter_pass"): (23611334784.0, "hhl_trotter.cu", "6e892b5cac35b7f9"),
-    ("couette_1024", "k_ctrl_gemm_tc"): (33605361.8, "hhl_gemm_tc.cu", "b3fc4e648ee914d8"),
+    ("poiseuille_2p18", "c64", "k_trotter_pass"): (23611334784.0, "hhl_trotter.cu", "6e892b5cac35b7f9"),
+    ("couette_1024", "c64", "k_ctrl_gemm_tc"): (33605361.8, "hhl_gemm_tc.cu", "b3fc4e648ee914d8"),
 }
 
 
-def _traffic(workload: str, kernel: str):
-    ent = KERNEL_TRAFFIC.get((workload, kernel))
+def _traffic(workload: str, precision: str, kernel: str):
+    ent = KERNEL_TRAFFIC.get((workload, precision, kernel))
     if ent is None:
         return None
     import hashlib
@@ -545,13 +545,13 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                 peak = _fp32_simt_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
                 bound, pk_note = "alu", "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x max SM clock"
             roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": _traffic(args.workload, dom), "peak_source": pk_note,
+                        "frac": achieved / peak, "traffic": _traffic(args.workload, args.precision, dom), "peak_source": pk_note,
                         "algorithmic_per_launch": per, "avg_launch_ms": avg_s * 1e3}
         else:
             achieved = per / avg_s / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
             roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": _traffic(args.workload, dom),
+                        "frac": achieved / peak, "traffic": _traffic(args.workload, args.precision, dom),
                         "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
                         "algorithmic_per_launch": per, "avg_launch_ms": avg_s * 1e3}
     if wl["unit"] == "GB/s":

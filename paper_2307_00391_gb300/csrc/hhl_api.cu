@@ -166,6 +166,7 @@ struct Eigen {
   std::vector<double> lam, vr, vi;
   double wgt = 1.0;
   bool have_vectors = false;
+  bool toeplitz = false;  // analytic sine basis: U_k from the g_k formula, no vectors needed
 };
 
 bool is_toeplitz(const double* d, const double* o, int64_t n) {
@@ -234,6 +235,7 @@ hhl_status eigen_of(const hhl_problem* pr, bool need_vectors, Plan& p, Eigen& eg
     // Toeplitz tridiagonal: lambda_j = d + 2 o cos(j pi/(N+1)), v_j(i) = sqrt(2/(N+1)) sin(i j pi/(N+1)).
     const double d = pr->diag[0], o = N > 1 ? pr->off[0] : 0.0;
     eg.J = n;
+    eg.toeplitz = true;
     eg.lam.resize(n);
     for (int j = 1; j <= n; ++j) eg.lam[j - 1] = d + 2.0 * o * cos(j * kPi / (N + 1));
     if (need_vectors) {
@@ -328,7 +330,8 @@ hhl_status plan_host(const hhl_problem* prob, const hhl_params* params, Plan& p,
   const bool dense = p.expm_mode == HHL_EXPM_DENSE;
   if (!dense && !(prob->kind == HHL_MATRIX_TRIDIAG && is_toeplitz(prob->diag, prob->off, N)))
     return fail(HHL_ERR_UNSUPPORTED, "Trotter mode needs a Toeplitz tridiagonal A");
-  hhl_status s = eigen_of(prob, dense && need_vectors, p, eg);
+  const bool toeplitz_a = prob->kind == HHL_MATRIX_TRIDIAG && (N == 1 || is_toeplitz(prob->diag, prob->off, N));
+  hhl_status s = eigen_of(prob, dense && need_vectors && !toeplitz_a, p, eg);
   if (s != HHL_OK) { return s; }
   double lmin = 1e300, lmax = -1e300, amin = 1e300, amax = 0.0;
   for (double l : eg.lam) {
@@ -533,9 +536,11 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       HHL_ALLOC(p.d_bfwd, (size_t)p.n_c * mat * ab, &p.table_bytes);
       HHL_ALLOC(p.d_badj, (size_t)p.n_c * mat * ab, &p.table_bytes);
     }
-    // eigenvectors to the device once; per k the phases and one FP64 exponential
-    double *d_vr = nullptr, *d_vi = nullptr, *d_c = nullptr, *d_s = nullptr;
-    double2* d_u = nullptr;
+    // Toeplitz A (the channel-flow operators): U_k[n][m] = g_k(n-m) - g_k(n+m+2) from the
+    // analytic sine basis, O(N^2) per k. Otherwise the eigenvectors go to the device once and
+    // every U_k is one FP64 eigen-product (O(N^3)).
+    double *d_vr = nullptr, *d_vi = nullptr, *d_c = nullptr, *d_s = nullptr, *d_ctab = nullptr;
+    double2 *d_u = nullptr, *d_g = nullptr;
     const int J = eg.J;
     uint64_t tmp_bytes = 0;
     auto free_tmp = [&]() {
@@ -544,14 +549,27 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       if (d_c) cudaFree(d_c);
       if (d_s) cudaFree(d_s);
       if (d_u) cudaFree(d_u);
+      if (d_ctab) cudaFree(d_ctab);
+      if (d_g) cudaFree(d_g);
     };
-    hhl_status ts = dev_alloc((void**)&d_vr, (size_t)N * J * sizeof(double), &tmp_bytes);
+    hhl_status ts = HHL_OK;
+    if (!eg.toeplitz) ts = dev_alloc((void**)&d_vr, (size_t)N * J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK && !eg.vi.empty()) ts = dev_alloc((void**)&d_vi, (size_t)N * J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK) ts = dev_alloc((void**)&d_c, (size_t)J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK) ts = dev_alloc((void**)&d_s, (size_t)J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK) ts = dev_alloc((void**)&d_u, mat * sizeof(double2), &tmp_bytes);
+    if (ts == HHL_OK && eg.toeplitz) ts = dev_alloc((void**)&d_ctab, (size_t)(2 * N + 2) * sizeof(double), &tmp_bytes);
+    if (ts == HHL_OK && eg.toeplitz) ts = dev_alloc((void**)&d_g, (size_t)(2 * N + 2) * sizeof(double2), &tmp_bytes);
     if (ts != HHL_OK) { free_tmp(); cudaStreamDestroy(st); hhl_plan_destroy(h); return ts; }
-    cudaError_t ce = cudaMemcpyAsync(d_vr, eg.vr.data(), (size_t)N * J * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaError_t ce = cudaSuccess;
+    std::vector<double> ctab;
+    if (eg.toeplitz) {
+      ctab.resize(2 * N + 2);
+      for (int64_t q = 0; q < 2 * N + 2; ++q) ctab[q] = cos((double)q * kPi / (double)(N + 1));
+      ce = cudaMemcpyAsync(d_ctab, ctab.data(), ctab.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    } else {
+      ce = cudaMemcpyAsync(d_vr, eg.vr.data(), (size_t)N * J * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
     if (ce == cudaSuccess && d_vi)
       ce = cudaMemcpyAsync(d_vi, eg.vi.data(), (size_t)N * J * sizeof(double), cudaMemcpyHostToDevice, st);
     std::vector<double> ch(J), sh(J);
@@ -565,7 +583,8 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       ce = cudaMemcpyAsync(d_c, ch.data(), J * sizeof(double), cudaMemcpyHostToDevice, st);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_s, sh.data(), J * sizeof(double), cudaMemcpyHostToDevice, st);
       if (ce != cudaSuccess) break;
-      hhl_status ks = launch_expm_eigen((int)N, J, d_vr, d_vi, d_c, d_s, eg.wgt, d_u, st);
+      hhl_status ks = eg.toeplitz ? launch_toeplitz_expm((int)N, d_c, d_s, d_ctab, d_g, d_u, st)
+                                  : launch_expm_eigen((int)N, J, d_vr, d_vi, d_c, d_s, eg.wgt, d_u, st);
       if (ks == HHL_OK) ks = p.gemm_impl == HHL_GEMM_SIMT ? launch_store_operands(p, d_u, k, st)
                                                           : tc_prepare_operands(p, d_u, k, st);
       if (ks != HHL_OK) { cudaStreamSynchronize(st); free_tmp(); cudaStreamDestroy(st); hhl_plan_destroy(h); return ks; }

@@ -127,6 +127,10 @@ hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_v
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);
 // All controlled products of QPE (adjoint: of the uncompute) on one half, in grouped passes.
 hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t st);
+// U = exp(i Ahat t) (N x N complex128) for a Toeplitz tridiagonal A from the analytic sine
+// basis: d_c / d_s = cos / sin(lambdahat_j t), d_ctab[q] = cos(q pi/(N+1)), q < 2N+2.
+hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, const double* d_ctab, double2* d_g,
+                                double2* d_u, cudaStream_t st);
 // Plan time: group the clock bits into passes, fill p.trot_pass and the layer-list table
 // (bytes, to be uploaded to p.d_trot_lists); returns the number of lists.
 size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table);

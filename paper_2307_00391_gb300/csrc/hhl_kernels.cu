@@ -425,6 +425,53 @@ hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_v
   return HHL_OK;
 }
 
+// Toeplitz tridiagonal A = tridiag(o, d, o): eigenpairs lambda_j = d + 2 o cos(j pi/(N+1)),
+// v_j(i) = sqrt(2/(N+1)) sin(i j pi/(N+1)) (i, j = 1..N), so with sin a sin b =
+// (cos(a-b) - cos(a+b))/2,
+//   U[n][m] = sum_j v_j(n) v_j(m) e^{i lambdahat_j t} = g(n-m) - g(n+m)   (1-based n, m),
+//   g(q) = 1/(N+1) sum_j cos(q j pi/(N+1)) e^{i lambdahat_j t}.
+// g for q in [0, 2N+2) (cos(q j pi/(N+1)) read from a table by (q j) mod (2N+2)), FP64.
+__global__ void __launch_bounds__(256) k_toeplitz_g(int N, const double* __restrict__ cph,
+                                                    const double* __restrict__ sph,
+                                                    const double* __restrict__ ctab, double2* __restrict__ g) {
+  const int M = 2 * N + 2;
+  const double inv = 1.0 / (double)(N + 1);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < M; q += gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    int r = 0;  // (q j) mod M
+    for (int j = 1; j <= N; ++j) {
+      r += q;
+      if (r >= M) r -= M;
+      const double c = ctab[r];
+      re = fma(c, cph[j - 1], re);
+      im = fma(c, sph[j - 1], im);
+    }
+    g[q] = make_double2(re * inv, im * inv);
+  }
+}
+
+// U[n][m] = g(|n - m|) - g(n + m + 2), 0-based n, m.
+__global__ void k_toeplitz_u(int N, const double2* __restrict__ g, double2* __restrict__ U) {
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / N), m = (int)(e - (int64_t)n * N);
+    const double2 a = g[n > m ? n - m : m - n], b = g[n + m + 2];
+    U[e] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, const double* d_ctab, double2* d_g,
+                                double2* d_u, cudaStream_t st) {
+  const int M = 2 * N + 2;
+  HHL_PROF_BEGIN(st);
+  k_toeplitz_g<<<(M + 255) / 256, 256, 0, st>>>(N, d_c, d_s, d_ctab, d_g);
+  HHL_LAUNCH_CHECK("k_toeplitz_g");
+  HHL_PROF_BEGIN(st);
+  k_toeplitz_u<<<grid_for((int64_t)N * N, kThreads, 152 * 16), kThreads, 0, st>>>(N, d_g, d_u);
+  HHL_LAUNCH_CHECK("k_toeplitz_u");
+  return HHL_OK;
+}
+
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st) {
   const size_t mat = (size_t)p.N * p.N;
   const int g = grid_for((int64_t)mat, kThreads, 152 * 16);
