@@ -1,6 +1,7 @@
 """Benchmark of the HHL state-vector hot path on GB300.
 
-python bench.py [--gpus N --steps K --warmup W] [--workload couette_1024|poiseuille_16|poiseuille_2p18]
+python bench.py [--gpus N --steps K --warmup W]
+                [--workload poiseuille_2p18|couette_1024|batch_256|poiseuille_16|poiseuille_2p16|qft_iqft_20x16|qft_iqft_30|qft_iqft_32]
                 [--impl ours|reference] [--precision c64|c128] [--gemm auto|simt|tcgen05]
 
 A step is one whole HHL solve of the workload: a1 prepare_rhs, a2..a5 apply_circuit (QPE
@@ -46,6 +47,13 @@ WORKLOADS = {
                             trotter_dt=1024.0, trotter_steps_max=8,
                             desc="Poiseuille flow, N=2^16, n_c=11, 28 qubits, Strang-Trotter exp(i A t) "
                                  "(a 2 GiB case of the 32-qubit kernels, for profiling)"),
+    # the paper's Fig. 1c gate benchmark: QFT then inverse QFT on whole registers of random states
+    "qft_iqft_20x16": dict(kind="qft", n=20, states=16, unit="GB/s", n_s=0, n_c=0, expm="none",
+                           desc="QFT then inverse QFT on all 20 qubits of 16 random states (Fig. 1c circuit)"),
+    "qft_iqft_30": dict(kind="qft", n=30, states=1, unit="GB/s", n_s=0, n_c=0, expm="none",
+                        desc="QFT then inverse QFT on all 30 qubits of one random state (Fig. 1c circuit)"),
+    "qft_iqft_32": dict(kind="qft", n=32, states=1, unit="GB/s", n_s=0, n_c=0, expm="none",
+                        desc="QFT then inverse QFT on all 32 qubits of one random state (Fig. 1c circuit)"),
     "poiseuille_2p18": dict(flow="poiseuille", n_s=18, n_c=13, expm="trotter", unit="GB/s",
                             trotter_dt=1024.0, trotter_steps_max=8,
                             desc="Poiseuille flow, N=2^18, n_c=13, 32 qubits, Strang-Trotter exp(i A t)"),
@@ -301,6 +309,32 @@ def _oracle_trotter_sample(wl: dict, budget_s: float) -> dict:
                       f"({est:.0f} s per solve); algorithmic bytes per solve / estimated time"}
 
 
+def _oracle_qft_sample(wl: dict, budget_s: float) -> dict:
+    """The oracle's gate-by-gate QFT then inverse QFT on 20-qubit random states (whole
+    circuits, repeated while the budget lasts), extrapolated to the workload by gate count x
+    state size (n (n+1) / 2 gates of 2^n amplitudes per transform)."""
+    from oracle import hhl_oracle as o
+    from synth_inputs import random_state
+    n0 = min(wl["n"], 20)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        psi = random_state(n0, seed_offset=900 + len(times))
+        tt = time.perf_counter()
+        o.qft_then_iqft(psi, n0)
+        times.append(time.perf_counter() - tt)
+        if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 8:
+            break
+    t0 = sum(times) / len(times)
+    n = wl["n"]
+    est = t0 * (n * (n + 1) * 2.0 ** n) / (n0 * (n0 + 1) * 2.0 ** n0) * wl["states"]
+    value = 4.0 * wl["states"] * (2 ** n) * 8 / est / 1e9
+    return {"value": value, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(times)} oracle QFT-IQFT circuits on {n0}-qubit random states "
+                      f"({sum(times):.1f} s)" + ("" if n == n0 and wl["states"] == 1 else
+                                                 f", extrapolated to {wl['states']} x {n} qubits by gates x amplitudes")}
+
+
 def cpu_baseline_sample(workload: str, budget_s: float = 30.0) -> dict:
     """The oracle as it stands, timed on the host cores on whole solves of the workload
     (the plan's matrix exponentials excluded, as on the GPU side); stops after the first
@@ -308,6 +342,8 @@ def cpu_baseline_sample(workload: str, budget_s: float = 30.0) -> dict:
     wl = WORKLOADS[workload]
     if wl.get("kind") == "batch":
         return _oracle_batch_sample(budget_s)
+    if wl.get("kind") == "qft":
+        return _oracle_qft_sample(wl, budget_s)
     if wl["expm"] != "dense":
         return _oracle_trotter_sample(wl, budget_s)
     o, pl, ev, b = _oracle_setup(wl)
@@ -351,6 +387,18 @@ def run_reference(args, rank: int, world: int) -> None:
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": wl["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    if wl.get("kind") == "qft":
+        samples = [_oracle_qft_sample(wl, 20.0) for _ in range(max(1, min(args.steps, 3)))]
+        value = sum(x["value"] for x in samples) / len(samples)
+        step_bytes = 4.0 * wl["states"] * (2 ** wl["n"]) * 8
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": len(samples),
+            "warmup": 0, "ms_per_step": 1e3 * step_bytes / (value * 1e9), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]}, "impl": "reference",
+            "cpu_baseline": dict(samples[-1], value=value),
+            "e2e": {"value": value, "unit": wl["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
     if wl["expm"] != "dense":
         # each step: one bounded oracle sample of the solve (see _oracle_trotter_sample)
@@ -589,6 +637,112 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     print(json.dumps(out))
 
 
+def run_qft(args, rank: int, world: int, local_rank: int) -> None:
+    """The Fig. 1c gate benchmark: QFT then inverse QFT on whole registers of random states
+    (seeded, on the device). value = algorithmic bytes / time, where each of the two
+    transforms must read and write every amplitude once."""
+    import torch
+
+    import paper_2307_00391_gb300 as pkg
+    from paper_2307_00391_gb300 import build as _b
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pkg.load()
+    wl = WORKLOADS[args.workload]
+    n, states = wl["n"], wl["states"]
+    dt = torch.complex64 if args.precision == "c64" else torch.complex128
+    amp_bytes = 8 if args.precision == "c64" else 16
+    st = torch.empty(states << n, dtype=dt, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(230700391 + rank)
+    torch.view_as_real(st).normal_(generator=gen)
+    view = st.view(states, 1 << n)
+    view /= torch.linalg.vector_norm(view, dim=1, keepdim=True)
+    x0 = view[:, :4].clone()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def step():
+        pkg.qft_whole(st, n, states, 0, stream=stream)
+        pkg.qft_whole(st, n, states, 1, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pkg.profile_reset()
+    pkg.profile_enable(True)
+    launches0 = pkg.kernel_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = pkg.kernel_launch_count() - launches0
+    pkg.profile_enable(False)
+    prof = pkg.profile_read()
+    total_s = sum(a.elapsed_time(c) for a, c in evs) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    step_bytes = 4.0 * states * (1 << n) * amp_bytes
+    # QFT-IQFT is the identity: the state after all steps is the input up to rounding
+    drift = float((view[:, :4] - x0).abs().max().item())
+    # end to end: the states from pinned host memory, both transforms, the states back
+    host = torch.empty(states << n, dtype=dt, pin_memory=True)
+    host.copy_(st)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            st.copy_(host, non_blocking=True)
+            step()
+            host.copy_(st, non_blocking=True)
+        stream.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    passes = sum(c for c, _ in prof.values())
+    per_launch = step_bytes * args.steps / passes if passes else 0.0
+    breakdown = {k: {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps}
+                 for k, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    peaks = _peaks()
+    roofline = None
+    if dom is not None:
+        c, ms = prof[dom]
+        achieved = per_launch / (ms / c / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
+                    "algorithmic_per_launch": per_launch, "avg_launch_ms": ms / c,
+                    "note": "the two transforms' minimum bytes spread evenly over their passes"}
+    cpu = _cpu_baseline_subprocess(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * step_bytes * args.steps / total_s / 1e9, "unit": wl["unit"],
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (f32)" if args.precision == "c64" else "c128 (f64)", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
+                       "l2": "inputs larger than L2" if states * (1 << n) * amp_bytes > (256 << 20) else "L2-resident",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "breakdown": breakdown, "clocks": clk.summary(),
+            "e2e": {"value": world * step_bytes * len(e2e_t) / sum(e2e_t) / 1e9, "unit": wl["unit"],
+                    "h2d_bytes_per_step": states * (1 << n) * amp_bytes,
+                    "d2h_bytes_per_step": states * (1 << n) * amp_bytes},
+            "gpu_launches": launches, "cpu_baseline": cpu,
+            "result": {"max_drift_after_all_steps": drift}}))
+
+
 def run_batch(args, rank: int, world: int, local_rank: int) -> None:
     """The batched engine: one step = one replay of the graph over all instances."""
     import numpy as np
@@ -755,6 +909,8 @@ def main():
     try:
         if WORKLOADS[args.workload].get("kind") == "batch":
             run_batch(args, rank, world, local_rank)
+        elif WORKLOADS[args.workload].get("kind") == "qft":
+            run_qft(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -310,6 +310,21 @@ hhl_status hhl_mlp_train_step(hhl_mlp_t mlp, const float* x_dev, const float* t_
 hhl_status hhl_apply_qft(void* state_dev, int32_t n_qubits, int32_t lo, int32_t m,
                          int32_t inverse, int32_t precision, void* stream);
 
+/* Whole-register QFT of the Fig. 1c experiment (the QFT-then-inverse-QFT circuit run on
+ * random states as the paper's gate benchmark): on each of n_states consecutive n-qubit
+ * states (state_dev holds n_states * 2^n amplitudes, n_states a power of two), in place,
+ *   direction 0: QFT|x> = 2^(-n/2) sum_y e^{+2 pi i x y / 2^n}|y>, with the result left in
+ *                bit-reversed order (amplitude of y at index bitrev_n(y)), i.e. the circuit
+ *                without its final swap layer;
+ *   direction 1: the inverse QFT reading its input in that bit-reversed order and writing
+ *                natural order.
+ * Direction 0 followed by direction 1 is the QFT-IQFT circuit (the identity up to rounding).
+ * Requires 1 <= n <= 32, n + log2(n_states) <= 34; precision HHL_PREC_C64 or HHL_PREC_C128.
+ * Asynchronous on stream; the first call for a given n builds a 48 KiB (c64) twiddle table
+ * on the device, kept until exit. */
+hhl_status hhl_qft_whole(void* state_dev, int32_t n_qubits, int32_t n_states, int32_t direction, int32_t precision,
+                         void* stream);
+
 /* Number of kernels this library has launched since load (all entry points). */
 uint64_t hhl_kernel_launch_count(void);
 

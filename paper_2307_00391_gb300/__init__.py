@@ -216,6 +216,15 @@ def apply_qft(state, n_qubits: int, lo: int, m: int, inverse: bool, stream=None)
                                ctypes.c_void_p(_stream_handle(stream))), "hhl_apply_qft")
 
 
+def qft_whole(state, n_qubits: int, n_states: int, direction: int, stream=None) -> None:
+    """Whole-register QFT (direction 0, result in bit-reversed order) or inverse QFT
+    (direction 1, input in bit-reversed order) of n_states consecutive n-qubit states."""
+    import torch
+    prec = _ffi.PREC_C64 if state.dtype == torch.complex64 else _ffi.PREC_C128
+    check(load().hhl_qft_whole(ctypes.c_void_p(state.data_ptr()), n_qubits, n_states, direction, prec,
+                               ctypes.c_void_p(_stream_handle(stream))), "hhl_qft_whole")
+
+
 class HHLBatch:
     """An hhl_batch_t: many uneven instances (Toeplitz tridiagonal A, complex64) run as one
     CUDA graph. ``problems``: dicts with n_sys_qubits, n_clock, diag, off and optionally nu,

@@ -813,4 +813,17 @@ hhl_status hhl_apply_qft(void* state_dev, int32_t n_qubits, int32_t lo, int32_t 
   return hhl::launch_qft_register(state_dev, n_qubits, lo, m, inverse != 0, precision, (cudaStream_t)stream);
 }
 
+hhl_status hhl_qft_whole(void* state_dev, int32_t n_qubits, int32_t n_states, int32_t direction, int32_t precision,
+                         void* stream) {
+  if (state_dev == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL state");
+  if (n_qubits < 1 || n_qubits > 32 || n_states < 1 || (n_states & (n_states - 1)) != 0)
+    return fail(HHL_ERR_INVALID_ARG, "register out of range (1 <= n <= 32, n_states a power of two)");
+  int lo = 0;
+  while ((1 << lo) < n_states) ++lo;
+  if (n_qubits + lo > 34) return fail(HHL_ERR_INVALID_ARG, "n + log2(n_states) > 34");
+  if (direction != 0 && direction != 1) return fail(HHL_ERR_INVALID_ARG, "direction must be 0 or 1");
+  if (precision != HHL_PREC_C64 && precision != HHL_PREC_C128) return fail(HHL_ERR_INVALID_ARG, "bad precision");
+  return hhl::launch_qft_whole(state_dev, n_qubits, n_states, direction, precision, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -122,6 +122,9 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st);
 hhl_status launch_dissipation(const Plan& p, const void* state, double* eps, double* u_dev, cudaStream_t st);
 hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st);
+// Whole-register QFT (direction 0, output in bit-reversed order) or inverse QFT (direction 1,
+// input in bit-reversed order) of `outer` consecutive n-qubit states.
+hhl_status launch_qft_whole(void* state, int n, int outer, int direction, int prec, cudaStream_t st);
 hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_vi, const double* d_cos,
                              const double* d_sin, double wgt, double2* d_u, cudaStream_t st);
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);

@@ -25,6 +25,10 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <type_traits>
+#include <vector>
 
 #include "hhl_common.cuh"
 
@@ -49,6 +53,21 @@ struct Twiddle {
   const T* t1;  // exp(-2 pi i 64 j / L)
   __device__ __forceinline__ T operator()(int q, bool conj) const {
     T f = cmul(t1[q >> 6], t0[q & 63]);
+    if (conj) f.y = -f.y;
+    return f;
+  }
+};
+
+// Three-level table for transforms of up to 33 bits (global memory, read through L1):
+// exp(-2 pi i q / L) = T2[q >> 22] T1[(q >> 11) & 2047] T0[q & 2047].
+template <class T>
+struct Twiddle3 {
+  const T* t0;
+  const T* t1;
+  const T* t2;
+  __device__ __forceinline__ T operator()(int q, bool conj) const {
+    T f = cmul(cmul(__ldg(reinterpret_cast<const T*>(t2) + (q >> 22)), __ldg(t1 + ((q >> 11) & 2047))),
+               __ldg(t0 + (q & 2047)));
     if (conj) f.y = -f.y;
     return f;
   }
@@ -231,7 +250,26 @@ __device__ void cross_stages(cg::cluster_group& cl, T* X, T* X2, int Lp, int W, 
 template <class T>
 __device__ void load_block(T* X, int Lp, const T* src, int64_t row_stride, int Lc, int W) {
   constexpr int per = 16 / sizeof(T);
-  if (W % per == 0) {
+  if (W == 1 && row_stride == 1) {
+    // one contiguous column (a register at the lowest index bits): 16-byte units of rows
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    const int units = Lc / per;
+    for (int b = threadIdx.x; b < units; b += blockDim.x * kUnroll) {
+      uint4 v[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k)
+        if (b + k * blockDim.x < units) v[k] = s4[b + k * blockDim.x];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int u = b + k * blockDim.x;
+        if (u < units) {
+          const T* t = reinterpret_cast<const T*>(&v[k]);
+#pragma unroll
+          for (int q = 0; q < per; ++q) X[pad16(u * per + q)] = t[q];
+        }
+      }
+    }
+  } else if (W % per == 0) {
     const int upr = W / per;
     const int total = Lc * upr;
     for (int b = threadIdx.x; b < total; b += blockDim.x * kUnroll) {
@@ -279,7 +317,16 @@ template <class T, class S>
 __device__ void store_block(T* dst, int64_t row_stride, const T* X, int Lp, int Lc, int W, S scale, bool rev,
                             int rank, int m) {
   constexpr int per = 16 / sizeof(T);
-  if (W % per == 0) {
+  if (W == 1 && row_stride == 1 && !rev) {
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int u = threadIdx.x; u < Lc / per; u += blockDim.x) {
+      uint4 v;
+      T* t = reinterpret_cast<T*>(&v);
+#pragma unroll
+      for (int q = 0; q < per; ++q) t[q] = cscale(X[pad16(u * per + q)], scale);
+      d4[u] = v;
+    }
+  } else if (W % per == 0) {
     const int upr = W / per;
     for (int u = threadIdx.x; u < Lc * upr; u += blockDim.x) {
       const int p = u / upr, h = u - p * upr;
@@ -361,11 +408,14 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_clock_block(typename Cx<R>::
   if (FULL) store_block(S0 + row0 * N + j0, N, Y, Lp, Lc, W, inv, false, rank, m);
 }
 
-// Register transform on bits [lo, lo+m): mode 0 = QFT, 1 = inverse QFT, 2 = Hadamards.
-// DIF (natural in); QFT / inverse QFT results are stored from bit-reversed positions.
+// Register transform on bits [lo, lo+m): mode 0 = QFT, 1 = inverse QFT, 2 = Hadamards (DIF,
+// natural in; QFT / inverse QFT results are stored from bit-reversed positions), 3 = the QFT's
+// DIF stages left in bit-reversed order, 4 = the inverse QFT's DIT stages from bit-reversed
+// order (the low register of a whole-register transform: its stages do not depend on the
+// bits above). Every output is multiplied by scale.
 template <class R, int CB>
 __global__ void __launch_bounds__(kFftThreads, 2) k_register_transform(typename Cx<R>::T* __restrict__ S, int lo, int m,
-                                                                    int W, int mode) {
+                                                                    int W, int mode, R scale) {
   using T = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
@@ -383,19 +433,27 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_register_transform(typename 
   const int64_t o = col / groups, g = col - o * groups;
   T* base = S + o * ((int64_t)1 << (lo + m)) + g * W;
   load_block(X, Lp, base + (int64_t)rank * Lc * inner, inner, Lc, W);
-  const bool conj = mode == 0;  // QFT: exp(+2 pi i x y / L)
-  if (CB > 0) {
-    cl.sync();
-    if (mode == 2) cross_stages<T, CB, false, 1>(cl, X, (T*)nullptr, Lp, W, tw, m, false);
-    else cross_stages<T, CB, false, 0>(cl, X, (T*)nullptr, Lp, W, tw, m, conj);
-  } else {
+  const bool conj = mode == 0 || mode == 3;  // QFT: exp(+2 pi i x y / L)
+  if (mode == 4) {  // DIT: low (local) stages first, then the cluster's top stages
     __syncthreads();
+    local_stages<T, true, 0>(X, Lp, W, tw, m, m_loc, false);
+    if (CB > 0) {
+      cl.sync();
+      cross_stages<T, CB, true, 0>(cl, X, (T*)nullptr, Lp, W, tw, m, false);
+    }
+  } else {
+    if (CB > 0) {
+      cl.sync();
+      if (mode == 2) cross_stages<T, CB, false, 1>(cl, X, (T*)nullptr, Lp, W, tw, m, false);
+      else cross_stages<T, CB, false, 0>(cl, X, (T*)nullptr, Lp, W, tw, m, conj);
+    } else {
+      __syncthreads();
+    }
+    if (mode == 2) local_stages<T, false, 1>(X, Lp, W, tw, m, m_loc, false);
+    else local_stages<T, false, 0>(X, Lp, W, tw, m, m_loc, conj);
   }
-  if (mode == 2) local_stages<T, false, 1>(X, Lp, W, tw, m, m_loc, false);
-  else local_stages<T, false, 0>(X, Lp, W, tw, m, m_loc, conj);
-  const R inv = (R)(1.0 / sqrt((double)(1 << m)));
-  if (mode == 2) store_block(base + (int64_t)rank * Lc * inner, inner, X, Lp, Lc, W, inv, false, rank, m);
-  else store_block(base, inner, X, Lp, Lc, W, inv, true, rank, m);
+  if (mode >= 2) store_block(base + (int64_t)rank * Lc * inner, inner, X, Lp, Lc, W, scale, false, rank, m);
+  else store_block(base, inner, X, Lp, Lc, W, scale, true, rank, m);
 }
 
 template <class R>
@@ -486,7 +544,8 @@ hhl_status clock_block_impl(const Plan& p, void* state, cudaStream_t st) {
 }
 
 template <class R>
-hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, cudaStream_t st) {
+hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, cudaStream_t st,
+                                   double scale = 0.0) {
   using T = typename Cx<R>::T;
   int W = 0, cb = 0;
   size_t smem = 0;
@@ -496,7 +555,8 @@ hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, 
   if ((cols << cb) > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
   const int grid = (int)(cols << cb);
   T* S = (T*)state;
-  void* args[] = {&S, &lo, &m, &W, &mode};
+  R sc = (R)(scale != 0.0 ? scale : 1.0 / sqrt((double)(1LL << m)));
+  void* args[] = {&S, &lo, &m, &W, &mode, &sc};
   switch (cb) {
     case 0: return launch_cluster(k_register_transform<R, 0>, grid, cb, smem, st, "k_register_transform", args);
     case 1: return launch_cluster(k_register_transform<R, 1>, grid, cb, smem, st, "k_register_transform", args);
@@ -534,7 +594,6 @@ constexpr int kSplitThreads = 256;
 constexpr int kSplitSegBytes = 256;  // bytes per row segment of a tile
 constexpr int kSplitMinBits = 4;     // tile rows >= 16
 constexpr int kSplitMaxBits = 7;     // tile rows <= 128
-constexpr int kSplitUnroll = 8;      // 16-byte tile loads in flight per thread (at most)
 
 struct SplitArgs {
   void* src;           // tiles are read here ...
@@ -548,6 +607,7 @@ struct SplitArgs {
   double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
   float scale_f;       // the same in FP32 (GB300's FP64 pipe is narrow: no per-thread conversions)
   int scaled;          // scale != 1
+  const void* tw3[3];  // whole-register transform: the three-level twiddle tables of 2^m
 };
 
 template <class R>
@@ -565,8 +625,8 @@ struct SplitGeom {
 // The RB radix-2 stages of one group (same arithmetic as butterflies() above), with the
 // twiddles of each stage formed once per distinct value: stage t needs 2^t factors
 // base_t * exp(-2 pi i xr / 2^(t+1)), xr < 2^t.
-template <class T, int RB, bool DIT, int MODE>
-__device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int lo_bits, int m, const Twiddle<T>& tw,
+template <class T, int RB, bool DIT, int MODE, class TW>
+__device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int lo_bits, int m, const TW& tw,
                                                   bool conj) {
   constexpr int G = 1 << RB;
   using R = decltype(T().x);
@@ -612,8 +672,11 @@ __device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int l
 
 // One radix-2^RB pass over tile bits [TB, TB + RB) of the row-major tile X[row * W + w]
 // (2^NB rows). Tile row j is register index lo_fixed + (j << b0) + (fixed bits above).
-template <class T, int NB, int TB, int RB, bool DIT, int MODE>
-__device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
+// With a whole-register transform (inner_base >= 0) the tile's columns are register bits
+// too: the index below the pass's bits is inner_base + w + ((lo_fixed + (lo << b0)) << shift).
+template <class T, int NB, int TB, int RB, bool DIT, int MODE, class TW>
+__device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj, int inner_base,
+                                          int shift) {
   constexpr int LW = SplitGeom<T>::LW, W = 1 << LW, G = 1 << RB;
   constexpr int total = W << (NB - RB);
 #pragma unroll 1
@@ -626,7 +689,11 @@ __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, con
     T v[G];
 #pragma unroll
     for (int x = 0; x < G; ++x) v[x] = q[x << (TB + LW)];
-    group_butterflies<T, RB, DIT, MODE>(v, lo_fixed + (lo << b0), b0 + TB, m, tw, conj);
+    if (inner_base >= 0)
+      group_butterflies<T, RB, DIT, MODE>(v, inner_base + w + ((lo_fixed + (lo << b0)) << shift), shift + b0 + TB, m,
+                                          tw, conj);
+    else
+      group_butterflies<T, RB, DIT, MODE>(v, lo_fixed + (lo << b0), b0 + TB, m, tw, conj);
 #pragma unroll
     for (int x = 0; x < G; ++x) q[x << (TB + LW)] = v[x];
   }
@@ -634,16 +701,17 @@ __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, con
 
 // All NB stages of a tile in passes of at most MR bits (DIF: high bits first), a barrier
 // after each pass.
-template <class T, int NB, bool DIT, int MODE, int Q = 0, int DONE = 0>
-__device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, const Twiddle<T>& tw, bool conj) {
+template <class T, int NB, bool DIT, int MODE, int Q = 0, int DONE = 0, class TW>
+__device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj,
+                                            int inner_base = -1, int shift = 0) {
   constexpr int MR = SplitGeom<T>::MR;
   constexpr int NPASS = (NB + MR - 1) / MR;
   if constexpr (Q < NPASS) {
     constexpr int RB = (NB - DONE) / (NPASS - Q);
     constexpr int TB = DIT ? DONE : NB - DONE - RB;
-    tile_pass<T, NB, TB, RB, DIT, MODE>(X, b0, lo_fixed, m, tw, conj);
+    tile_pass<T, NB, TB, RB, DIT, MODE>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
     __syncthreads();
-    tile_stages<T, NB, DIT, MODE, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj);
+    tile_stages<T, NB, DIT, MODE, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
   }
 }
 
@@ -699,6 +767,7 @@ __device__ __forceinline__ void tile_store(T* base, const T* X, long long row_un
 struct TilePos {
   long long row0, base_amp;
   int lo_fixed, hi_fixed;
+  int inner_base;  // first inner index of the tile's columns
 };
 
 template <int NB, int LW>
@@ -713,10 +782,14 @@ __device__ __forceinline__ TilePos tile_pos(const SplitArgs& a, long long t) {
   q.hi_fixed = f >> a.b0;
   q.row0 = q.lo_fixed + ((long long)q.hi_fixed << (a.b0 + NB));
   q.base_amp = o * a.region + (ib << LW);
+  q.inner_base = (int)(ib << LW);
   return q;
 }
 
-template <class R, int OP, bool FULL, int NB>
+// WHOLE: the register is the whole index range [0, lo + m) of each outer block, the tile
+// rows are its bits [lo + b0, lo + b0 + NB) and the twiddles are those of the 2^(lo + m) point
+// transform (three-level global tables); only the DIF and DIT passes are used this way.
+template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
@@ -726,10 +799,20 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t0 = reinterpret_cast<T*>(smem_raw);
   T* t1 = t0 + 64;
-  T* Xb = t0 + twiddle_entries(a.m);  // two tile buffers (double buffering), then Y
+  T* Xb = t0 + (WHOLE ? 0 : twiddle_entries(a.m));  // two tile buffers (double buffering), then Y
   T* Y = Xb + 2 * tile_amps;
-  if (OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
-  const Twiddle<T> tw{t0, t1};
+  if (!WHOLE && OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
+  using TW = typename std::conditional<WHOLE, Twiddle3<T>, Twiddle<T>>::type;
+  TW tw;
+  if constexpr (WHOLE) {
+    tw.t0 = static_cast<const T*>(a.tw3[0]);
+    tw.t1 = static_cast<const T*>(a.tw3[1]);
+    tw.t2 = static_cast<const T*>(a.tw3[2]);
+  } else {
+    tw.t0 = t0;
+    tw.t1 = t1;
+  }
+  const int mt = WHOLE ? a.lo + a.m : a.m;  // bits of the transform the twiddles belong to
   const int rows = 1 << NB;
   const long long row_units = ((long long)1 << a.lo) / per;  // 16-byte units per row
   long long t = blockIdx.x;
@@ -753,7 +836,12 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
     const TilePos q = tile_pos<NB, LW>(a, t);
     T* X = Xb + buf * tile_amps;
     T* dst = static_cast<T*>(a.dst) + q.base_amp;
-    if (OP == kSplitDif) {
+    if (WHOLE) {
+      // whole-register QFT (DIF, + sign) or inverse QFT (DIT, - sign)
+      if (OP == kSplitDif) tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, mt, tw, true, q.inner_base, a.lo);
+      else tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, mt, tw, false, q.inner_base, a.lo);
+      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+    } else if (OP == kSplitDif) {
       tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
       tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
     } else if (OP == kSplitDit) {
@@ -810,12 +898,12 @@ bool split_applies(int lo, int m, long long region_amps) {
   return (size_t)region_amps * sz > ((size_t)256 << 20);
 }
 
-template <class R, int OP, bool FULL, int NB>
+template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
 hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
   const size_t tile = ((size_t)1 << (NB + SplitGeom<T>::LW)) * sizeof(T);
-  const size_t smem = (size_t)twiddle_entries(a.m) * sizeof(T) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
-  auto kern = k_split_pass<R, OP, FULL, NB>;
+  const size_t smem = (WHOLE ? 0 : (size_t)twiddle_entries(a.m) * sizeof(T)) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
+  auto kern = k_split_pass<R, OP, FULL, NB, WHOLE>;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
@@ -829,7 +917,7 @@ hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name
   return HHL_OK;
 }
 
-template <class R, int OP, bool FULL>
+template <class R, int OP, bool FULL, bool WHOLE = false>
 hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
   a.log_cb = a.lo - SplitGeom<T>::LW;
@@ -838,12 +926,94 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   a.scaled = a.scale != 1.0;
   a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
   switch (a.nb) {
-    case 4: return launch_split_nb<R, OP, FULL, 4>(a, st, name);
-    case 5: return launch_split_nb<R, OP, FULL, 5>(a, st, name);
-    case 6: return launch_split_nb<R, OP, FULL, 6>(a, st, name);
-    case 7: return launch_split_nb<R, OP, FULL, 7>(a, st, name);
+    case 4: return launch_split_nb<R, OP, FULL, 4, WHOLE>(a, st, name);
+    case 5: return launch_split_nb<R, OP, FULL, 5, WHOLE>(a, st, name);
+    case 6: return launch_split_nb<R, OP, FULL, 6, WHOLE>(a, st, name);
+    case 7: return launch_split_nb<R, OP, FULL, 7, WHOLE>(a, st, name);
     default: return fail(HHL_ERR_UNSUPPORTED, "split register pass: tile bits out of range");
   }
+}
+
+// Three-level twiddle tables of the 2^n-point transform, built on the host in FP64 once per
+// (device, n, precision) and kept for the process.
+template <class R>
+hhl_status whole_tables(int n, const void* out[3]) {
+  using T = typename Cx<R>::T;
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, void*> cache;
+  int dev = 0;
+  HHL_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  void*& ptr = cache[{dev * 64 + n, (int)sizeof(R)}];
+  if (ptr == nullptr) {
+    std::vector<T> h(3 * 2048);
+    const double L = ldexp(1.0, n);
+    for (int lvl = 0; lvl < 3; ++lvl)
+      for (int j = 0; j < 2048; ++j) {
+        const double q = fmod(ldexp((double)j, 11 * lvl), L);  // exact: j 2^(11 lvl) < 2^53
+        const double a = -2.0 * q / L;                         // angle / pi in [-2, 0]
+        h[lvl * 2048 + j] = mk<R>((R)cospi(a), (R)sinpi(a));
+      }
+    void* d = nullptr;
+    HHL_CUDA_TRY(cudaMalloc(&d, h.size() * sizeof(T)));
+    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "twiddle tables");
+    }
+    ptr = d;
+  }
+  for (int lvl = 0; lvl < 3; ++lvl) out[lvl] = static_cast<const T*>(ptr) + lvl * 2048;
+  return HHL_OK;
+}
+
+// QFT (direction 0: DIF, natural order in, bit-reversed order out) or inverse QFT (direction
+// 1: DIT, bit-reversed in, natural out) on the whole n-qubit register of each of `outer`
+// consecutive states. The low g bits (g <= 12) form one pass over contiguous 2^g-amplitude
+// chunks (their stages need no higher bits); the other n - g bits are split passes of 4..7
+// bits over 256-byte row segments, with the twiddles of the 2^n-point transform.
+template <class R>
+hhl_status whole_register_impl(void* state, int n, int outer, int direction, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  const int g = n <= 12 ? n : std::min(12, n - 4);
+  const int hbits = n - g;
+  const int ngroups = (hbits + kSplitMaxBits - 1) / kSplitMaxBits;
+  int logo = 0;
+  while ((1 << logo) < outer) ++logo;
+  if ((1 << logo) != outer) return fail(HHL_ERR_INVALID_ARG, "state count must be a power of two");
+  const double scale = 1.0 / sqrt(ldexp(1.0, n));
+  std::vector<std::pair<int, int>> groups;  // (first bit relative to g, bits), low to high
+  for (int q = 0, done = 0; q < ngroups; ++q) {
+    const int nb = (hbits - done) / (ngroups - q);
+    groups.push_back({done, nb});
+    done += nb;
+  }
+  SplitArgs a = {};
+  a.src = state;
+  a.dst = state;
+  a.lo = g;
+  a.m = hbits;
+  a.scale = 1.0;
+  if (hbits > 0) {
+    hhl_status s = whole_tables<R>(n, a.tw3);
+    if (s != HHL_OK) return s;
+  }
+  if (direction == 0) {
+    for (int q = ngroups - 1; q >= 0; --q) {
+      a.b0 = groups[q].first;
+      a.nb = groups[q].second;
+      hhl_status s = launch_split<R, kSplitDif, false, true>(a, outer, st, "k_whole_pass");
+      if (s != HHL_OK) return s;
+    }
+    return register_transform_impl<R>(state, n + logo, 0, g, 3, st, scale);
+  }
+  hhl_status s = register_transform_impl<R>(state, n + logo, 0, g, 4, st, scale);
+  for (int q = 0; q < ngroups && s == HHL_OK; ++q) {
+    a.b0 = groups[q].first;
+    a.nb = groups[q].second;
+    s = launch_split<R, kSplitDit, false, true>(a, outer, st, "k_whole_pass");
+  }
+  return s;
 }
 
 template <class R, bool FULL>
@@ -924,6 +1094,11 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
                                                          : register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
   return split_applies<double>(p.n_s, p.n_c, half_amps) ? hadamard_split<double>(base, p.n_s, p.n_c, outer, st)
                                                         : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
+}
+
+hhl_status launch_qft_whole(void* state, int n, int outer, int direction, int prec, cudaStream_t st) {
+  return prec == HHL_PREC_C64 ? whole_register_impl<float>(state, n, outer, direction, st)
+                              : whole_register_impl<double>(state, n, outer, direction, st);
 }
 
 hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st) {

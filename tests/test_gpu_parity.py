@@ -186,6 +186,40 @@ def test_qft_register_blocks(hhl, prec, n, lo, m):
         np.testing.assert_allclose(_np(st), ref, atol=TOL[prec])
 
 
+def _bitrev(n):
+    idx = np.arange(1 << n)
+    out = np.zeros_like(idx)
+    for b in range(n):
+        out |= ((idx >> b) & 1) << (n - 1 - b)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,states", [(9, 2), (13, 1), (16, 2), (18, 1), (21, 1)])
+def test_qft_whole_register_parity(hhl, prec, n, states):
+    """The Fig. 1c circuit's QFT on the whole register (low bits in one pass, the rest in
+    split passes with the 2^n-point twiddles) against the oracle's gate-by-gate QFT (read in
+    bit-reversed order), then the inverse QFT back to the input."""
+    import torch
+    from synth_inputs import random_state
+    psis = [random_state(n, seed_offset=500 + n * 10 + j) for j in range(states)]
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    st = torch.tensor(np.concatenate(psis), dtype=dt, device="cuda")
+    hhl.qft_whole(st, n, states, 0)
+    got = _np(st).reshape(states, 1 << n)
+    rev = _bitrev(n)
+    rel = 1e-4 if prec == "c64" else 1e-9  # of the largest amplitude (the state is normalised)
+    for j, psi in enumerate(psis):
+        ref = o.qft_register(psi, n, 0, n, False)
+        np.testing.assert_allclose(got[j][rev], ref, atol=TOL[prec])
+        assert np.abs(got[j][rev] - ref).max() <= rel * np.abs(ref).max()
+    hhl.qft_whole(st, n, states, 1)
+    back = _np(st).reshape(states, 1 << n)
+    for j, psi in enumerate(psis):
+        np.testing.assert_allclose(back[j], psi, atol=TOL[prec])
+        assert np.abs(back[j] - psi).max() <= rel * np.abs(psi).max()
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("dt,r_max", [(3.0, 0), (0.5, 40), (50.0, 7)])
 def test_trotter_parity(hhl, prec, dt, r_max):
