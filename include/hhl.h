@@ -215,6 +215,15 @@ hhl_status hhl_measure_async(hhl_plan_t plan, const void* state_dev, double* out
 hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* out,
                        double* x_host, void* stream);
 
+/* a6 - shots: the system register measured `shots` times after postselection (ancilla 1,
+ * clock 0; Sec. II.A reads the solution by repeated measurement): outcome j with probability
+ * |v_j|^2 / sum |v|^2, by inverse-transform sampling of the caller's uniforms:
+ * shot s lands in the bin j with cdf_{j-1} <= u_s * cdf_{N-1} < cdf_j (cdf = running FP64 sum
+ * of |v|^2). uniforms_dev: DEVICE, shots doubles in [0, 1) (the random numbers are inputs, so
+ * the outcome is reproducible); counts_dev: DEVICE, N uint64 (overwritten). Asynchronous. */
+hhl_status hhl_sample(hhl_plan_t plan, const void* state_dev, const double* uniforms_dev, int64_t shots,
+                      uint64_t* counts_dev, void* stream);
+
 /* a7 - in-situ viscous dissipation rate (Sec. VII, App. D: eps = nu <(du/dy)^2>, the
  * same finite-difference post-processing as the classical solution). The velocity is
  * u_i = |b| Re(v_i) / (C lambda_ub) at the N interior nodes, u_0 = wall_lo,

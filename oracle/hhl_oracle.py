@@ -433,6 +433,17 @@ def postselect(psi: np.ndarray, n_s: int, n_c: int) -> dict:
     return dict(v=v, p_success=p_succ, p_anc1=p_anc1, norm=norm, xhat=xhat)
 
 
+def sample_counts(v: np.ndarray, uniforms: np.ndarray) -> np.ndarray:
+    """Shots of the system register after postselection (Sec. II.A: the solution is read by
+    repeated measurement): outcome j has probability |v_j|^2 / sum |v|^2; shot s with the
+    uniform u_s in [0, 1) lands in the bin j with cdf_{j-1} <= u_s * total < cdf_j, where cdf
+    is the running sum of |v|^2 (inverse-transform sampling). Returns the N counts."""
+    p = np.abs(np.asarray(v, dtype=np.complex128)) ** 2
+    cdf = np.cumsum(p)
+    idx = np.searchsorted(cdf, np.asarray(uniforms, dtype=np.float64) * cdf[-1], side="right")
+    return np.bincount(np.minimum(idx, len(p) - 1), minlength=len(p)).astype(np.int64)
+
+
 def velocity(v: np.ndarray, b_norm: float, c_const: float, lam_ub: float) -> np.ndarray:
     """Denormalised velocity at the interior nodes: u = |b| Re(v) / (C lambda_ub)."""
     return b_norm * np.real(v) / (c_const * lam_ub)

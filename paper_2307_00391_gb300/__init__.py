@@ -202,6 +202,14 @@ class HHLPlan:
                                         ctypes.c_void_p(_stream_handle(stream))), "hhl_dissipation")
         return (eps.value, u) if want_u else eps.value
 
+    def sample(self, state, uniforms_dev, counts_dev, stream=None) -> None:
+        """Shots of the postselected system register: counts_dev (torch int64, N) from the
+        uniforms in uniforms_dev (torch float64, one per shot)."""
+        check(self._lib.hhl_sample(self._h, ctypes.c_void_p(state.data_ptr()),
+                                   ctypes.c_void_p(uniforms_dev.data_ptr()), int(uniforms_dev.numel()),
+                                   ctypes.c_void_p(counts_dev.data_ptr()),
+                                   ctypes.c_void_p(_stream_handle(stream))), "hhl_sample")
+
     def dissipation_async(self, state, eps_dev, stream=None) -> None:
         check(self._lib.hhl_dissipation_async(self._h, ctypes.c_void_p(state.data_ptr()),
                                               ctypes.c_void_p(eps_dev.data_ptr()),

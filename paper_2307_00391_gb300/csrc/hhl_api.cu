@@ -384,6 +384,7 @@ struct hhl_plan_s {
   Plan p;
   void* d_meas = nullptr;  // 4 + 2N doubles
   double* d_u = nullptr;   // N doubles + 1 (eps)
+  double* d_cdf = nullptr; // N doubles: running sum of the outcome probabilities (shots)
   double* d_bsplit = nullptr;  // 2N doubles: host re / im staging
 };
 
@@ -499,6 +500,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
   HHL_ALLOC(h->d_bsplit, (size_t)N * 2 * sizeof(double), &p.workspace_bytes);
   HHL_ALLOC(h->d_meas, (size_t)(4 + 2 * N) * sizeof(double), &p.workspace_bytes);
   HHL_ALLOC(h->d_u, (size_t)(N + 1) * sizeof(double), &p.workspace_bytes);
+  HHL_ALLOC(h->d_cdf, (size_t)N * sizeof(double), &p.workspace_bytes);
   HHL_ALLOC(p.d_rot, (size_t)p.R * rsz, &p.table_bytes);
   {
     std::vector<double> rot(2 * p.R);
@@ -650,7 +652,7 @@ void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
   void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
-                  p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_bsplit};
+                  p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_cdf, plan->d_bsplit};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   hhl::tc_free(p);
@@ -782,6 +784,13 @@ hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* 
   if (!(sc[3] > 0.0)) return fail(HHL_ERR_SINGULAR, "|b| = 0");
   if (!(sc[0] > 0.0)) return fail(HHL_ERR_SINGULAR, "postselection probability is 0");
   return HHL_OK;
+}
+
+hhl_status hhl_sample(hhl_plan_t plan, const void* state_dev, const double* uniforms_dev, int64_t shots,
+                      uint64_t* counts_dev, void* stream) {
+  if (plan == nullptr || state_dev == nullptr || counts_dev == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL argument");
+  if (shots < 0 || (shots > 0 && uniforms_dev == nullptr)) return fail(HHL_ERR_INVALID_ARG, "bad shots / uniforms");
+  return hhl::launch_sample(plan->p, state_dev, uniforms_dev, shots, counts_dev, plan->d_cdf, (cudaStream_t)stream);
 }
 
 hhl_status hhl_dissipation_async(hhl_plan_t plan, const void* state_dev, double* eps_dev, void* stream) {

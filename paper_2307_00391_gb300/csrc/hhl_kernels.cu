@@ -243,6 +243,48 @@ __global__ void k_measure_finish(const typename Cx<R>::T* __restrict__ S, int64_
   }
 }
 
+// Shots (inverse-transform sampling of the postselected outcome distribution): running sum
+// cdf_j = sum_{i <= j} |v_i|^2 in FP64 by one block (contiguous chunks per thread, then a scan
+// of the chunk totals), then per shot the bin j with cdf_{j-1} <= u total < cdf_j.
+template <class R>
+__global__ void __launch_bounds__(1024) k_sample_cdf(const typename Cx<R>::T* __restrict__ v, int64_t N,
+                                                     double* __restrict__ cdf) {
+  __shared__ double part[1024];
+  const int t = threadIdx.x;
+  const int64_t chunk = (N + blockDim.x - 1) / blockDim.x;
+  const int64_t a = t * chunk, b = a + chunk < N ? a + chunk : N;
+  double sum = 0.0;
+  for (int64_t j = a; j < b; ++j) sum += (double)v[j].x * (double)v[j].x + (double)v[j].y * (double)v[j].y;
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive Hillis-Steele scan
+    const double add = t >= off ? part[t - off] : 0.0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  double run = t > 0 ? part[t - 1] : 0.0;
+  for (int64_t j = a; j < b; ++j) {
+    run += (double)v[j].x * (double)v[j].x + (double)v[j].y * (double)v[j].y;
+    cdf[j] = run;
+  }
+}
+
+__global__ void k_sample_bins(const double* __restrict__ cdf, int64_t N, const double* __restrict__ u, int64_t shots,
+                              unsigned long long* __restrict__ counts) {
+  const double total = cdf[N - 1];
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < shots; s += (int64_t)gridDim.x * blockDim.x) {
+    const double x = u[s] * total;
+    int64_t lo = 0, hi = N - 1;  // smallest j with x < cdf[j] (the last bin if none)
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (x < cdf[mid]) hi = mid;
+      else lo = mid + 1;
+    }
+    atomicAdd(counts + lo, 1ULL);
+  }
+}
+
 // Dissipation: sum over the N+1 cells of (u_{i+1} - u_i)^2 with walls at both ends.
 template <class R>
 __global__ void k_diss_sum(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N,
@@ -392,6 +434,23 @@ hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStr
     k_measure_finish<double><<<gf, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, out);
   }
   HHL_LAUNCH_CHECK("k_measure_finish");
+  return HHL_OK;
+}
+
+hhl_status launch_sample(const Plan& p, const void* state, const double* uniforms, int64_t shots, uint64_t* counts,
+                         double* cdf, cudaStream_t st) {
+  const int64_t half = p.R * p.N;
+  HHL_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)p.N * sizeof(uint64_t), st));
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64) k_sample_cdf<float><<<1, 1024, 0, st>>>((const float2*)state + half, p.N, cdf);
+  else k_sample_cdf<double><<<1, 1024, 0, st>>>((const double2*)state + half, p.N, cdf);
+  HHL_LAUNCH_CHECK("k_sample_cdf");
+  if (shots > 0) {
+    HHL_PROF_BEGIN(st);
+    k_sample_bins<<<grid_for(shots, kThreads, 152 * 4), kThreads, 0, st>>>(cdf, p.N, uniforms, shots,
+                                                                          (unsigned long long*)counts);
+    HHL_LAUNCH_CHECK("k_sample_bins");
+  }
   return HHL_OK;
 }
 

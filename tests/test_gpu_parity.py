@@ -84,6 +84,43 @@ def test_stagewise_parity(hhl, prec, full, flow, n_s, n_c, rule):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_shots_match_the_oracle_sampler(hhl, prec):
+    """Shots of the postselected register from the same uniforms: the oracle's inverse-
+    transform sampler on the oracle's final state against the GPU sampler on the GPU state;
+    shots whose uniform falls within the two states' probability difference of a bin edge are
+    the only ones allowed to differ."""
+    import torch
+    from synth_inputs import uniform_draws
+    n_s, n_c = 6, 7
+    diag, off, b, walls = problem("poiseuille", n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    v_ref = o.postselect(o.hhl_circuit(b, n_s, pl), n_s, n_c)["v"]
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    u = uniform_draws(8000, seed_offset=7)
+    counts = torch.empty(1 << n_s, dtype=torch.int64, device="cuda")
+    plan.sample(st, torch.tensor(u, device="cuda"), counts)
+    got = counts.cpu().numpy()
+    ref = o.sample_counts(v_ref, u)
+    assert got.sum() == 8000
+    p = np.abs(v_ref) ** 2
+    cdf = np.cumsum(p) / p.sum()
+    margin = 1e-12 if prec == "c128" else 1e-4
+    near = np.min(np.abs(u[:, None] - cdf[None, :]), axis=1) < margin
+    assert np.abs(got - ref).sum() <= 2 * int(near.sum()), (int(near.sum()), np.abs(got - ref).sum())
+    # the GPU sampler on a state it did not compute: exact
+    psi = np.zeros(2 << (n_s + n_c), dtype=np.complex128)
+    vv = np.sqrt(np.arange(1, (1 << n_s) + 1, dtype=np.float64)) * np.exp(1j * np.arange(1 << n_s))
+    psi[(1 << (n_s + n_c)):(1 << (n_s + n_c)) + (1 << n_s)] = vv
+    st2 = torch.tensor(psi, dtype=st.dtype, device="cuda")
+    plan.sample(st2, torch.tensor(u, device="cuda"), counts)
+    vv_in = (vv.astype(np.complex64) if prec == "c64" else vv).astype(np.complex128)  # the stored amplitudes
+    np.testing.assert_array_equal(counts.cpu().numpy(), o.sample_counts(vv_in, u))
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("flow", ["poiseuille", "couette"])
 def test_measure_and_dissipation_parity(hhl, prec, flow):
     n_s, n_c = 6, 7

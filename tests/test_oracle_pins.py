@@ -452,3 +452,19 @@ def test_mlp_oracle_special_cases():
     assert loss == pytest.approx((0.25 + 2.25) / 2)
     np.testing.assert_allclose(g[-2:], [0.5, -1.5])   # d/db3 of mean (b3)^2 over 2 outputs
     np.testing.assert_allclose(g[:-2], 0.0)
+
+
+def test_sampler_counts_on_a_uniform_grid_match_the_probabilities():
+    """Inverse-transform sampling with the S grid uniforms (s + 1/2)/S puts floor or ceil of
+    p_j S shots in bin j (the cdf steps are p_j): a deterministic pin of the sampler."""
+    p = np.array([0.1, 0.25, 0.0, 0.3, 0.35])
+    v = np.sqrt(p) * np.exp(1j * np.array([0.3, -1.0, 0.0, 2.0, 0.5]))
+    S = 1000
+    u = (np.arange(S) + 0.5) / S
+    counts = o.sample_counts(v, u)
+    assert counts.sum() == S
+    assert np.all(np.abs(counts - p * S) <= 1.0)
+    assert counts[2] == 0
+    # a single bin takes every shot; the last bin takes u -> 1
+    assert o.sample_counts(np.array([0, 0, 1.0]), u).tolist() == [0, 0, S]
+    assert o.sample_counts(np.array([1.0, 1.0]), np.array([0.0, 0.4999, 0.5, 0.999999])).tolist() == [2, 2]
