@@ -185,6 +185,15 @@ hhl_status hhl_prepare_rhs(hhl_plan_t plan, const double* b_dev, void* state_dev
 hhl_status hhl_prepare_rhs_host(hhl_plan_t plan, const double* b_re, const double* b_im,
                                 void* state_dev, void* stream);
 
+/* a1, gate-level form (App. C, QSP-1): the system register is prepared from |0> by the
+ * binary tree of uniformly controlled RY rotations (level l rotates qubit n_s-1-l by the
+ * paper's R_y(theta), theta = arccos sqrt(p(zero child) / p(node)), conditioned on the l more
+ * significant qubits), and the Hadamard layer on the clock puts that state into every clock
+ * row: the anc = 0 half holds |b|-amplitude encoding / 2^(n_c/2), the anc = 1 half is zero.
+ * The tree encodes magnitudes: for b_i >= 0 (every flow right-hand side) the result equals
+ * hhl_prepare_rhs. b_dev: DEVICE, N real doubles. Uses plan-owned scratch; asynchronous. */
+hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* state_dev, void* stream);
+
 /* a2..a5 - the circuit after state preparation, in place (Sec. IV/VI, standard HHL):
  * clock-bit-controlled U_k for k = 0..n_c-1, inverse QFT on the clock, clock-controlled
  * RY on the ancilla, QFT on the clock, controlled U_k^dagger for k = n_c-1..0, Hadamard on

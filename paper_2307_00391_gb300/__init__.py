@@ -202,6 +202,12 @@ class HHLPlan:
                                         ctypes.c_void_p(_stream_handle(stream))), "hhl_dissipation")
         return (eps.value, u) if want_u else eps.value
 
+    def prepare_rhs_qsp1(self, b_dev, state, stream=None) -> None:
+        """Gate-level RHS preparation (QSP-1 tree + clock Hadamards); b_dev: torch float64 (N)."""
+        check(self._lib.hhl_prepare_rhs_qsp1(self._h, ctypes.c_void_p(b_dev.data_ptr()),
+                                             ctypes.c_void_p(state.data_ptr()),
+                                             ctypes.c_void_p(_stream_handle(stream))), "hhl_prepare_rhs_qsp1")
+
     def sample(self, state, uniforms_dev, counts_dev, stream=None) -> None:
         """Shots of the postselected system register: counts_dev (torch int64, N) from the
         uniforms in uniforms_dev (torch float64, one per shot)."""

@@ -243,6 +243,52 @@ __global__ void k_measure_finish(const typename Cx<R>::T* __restrict__ S, int64_
   }
 }
 
+// QSP-1 (App. C): the system register prepared from |0> by a binary tree of uniformly
+// controlled RY rotations. tree[(1 << l) + i] holds the probability mass of node i of level l
+// (level n_s: the leaves |b_i|^2); level l rotates qubit n_s-1-l, conditioned on the l more
+// significant qubits holding node i, by R_y(theta) in the paper's convention (our RY(2 theta)),
+// theta = arccos sqrt(p(zero child) / p(node)).
+__global__ void k_qsp_leaves(const double* __restrict__ b, int64_t N, double* __restrict__ tree) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    tree[N + i] = b[i] * b[i];
+}
+
+__global__ void k_qsp_sum(int l, double* __restrict__ tree) {
+  const int64_t n = 1LL << l;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    tree[n + i] = tree[2 * n + 2 * i] + tree[2 * n + 2 * i + 1];
+}
+
+__global__ void k_qsp_level(int l, int n_s, const double* __restrict__ tree, double2* __restrict__ psi) {
+  const int t = n_s - 1 - l;
+  const int64_t pairs = 1LL << (n_s - 1);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < pairs; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = ((q >> t) << (t + 1)) | (q & ((1LL << t) - 1));
+    const int64_t i1 = i0 | (1LL << t);
+    const int64_t node = i0 >> (t + 1);
+    const double parent = tree[(1LL << l) + node];
+    const double child0 = tree[(2LL << l) + 2 * node];
+    const double th = parent > 0.0 ? acos(sqrt(fmin(1.0, child0 / parent))) : 0.0;
+    const double c = cos(th), s = sin(th);
+    const double2 a0 = psi[i0], a1 = psi[i1];
+    psi[i0] = make_double2(c * a0.x - s * a1.x, c * a0.y - s * a1.y);
+    psi[i1] = make_double2(s * a0.x + c * a1.x, s * a0.y + c * a1.y);
+  }
+}
+
+// psi = |0>, then (after the tree) bs = psi / 2^(n_c/2) in the amplitude precision.
+__global__ void k_qsp_init(double2* __restrict__ psi, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    psi[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+}
+
+template <class R>
+__global__ void k_qsp_scale(const double2* __restrict__ psi, int64_t N, int n_c, typename Cx<R>::T* __restrict__ bs) {
+  const double sc = 1.0 / sqrt((double)(1LL << n_c));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    bs[i] = mk<R>((R)(psi[i].x * sc), (R)(psi[i].y * sc));
+}
+
 // Shots (inverse-transform sampling of the postselected outcome distribution): running sum
 // cdf_j = sum_{i <= j} |v_i|^2 in FP64 by one block (contiguous chunks per thread, then a scan
 // of the chunk totals), then per shot the bin j with cdf_{j-1} <= u total < cdf_j.
@@ -434,6 +480,39 @@ hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStr
     k_measure_finish<double><<<gf, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, out);
   }
   HHL_LAUNCH_CHECK("k_measure_finish");
+  return HHL_OK;
+}
+
+hhl_status launch_prep_qsp1(const Plan& p, const double* b, double* tree, double2* psi, void* state,
+                            cudaStream_t st) {
+  const int g = grid_for(p.N, kThreads, 152 * 4);
+  HHL_PROF_BEGIN(st);
+  k_qsp_leaves<<<g, kThreads, 0, st>>>(b, p.N, tree);
+  HHL_LAUNCH_CHECK("k_qsp_leaves");
+  for (int l = p.n_s - 1; l >= 0; --l) {
+    HHL_PROF_BEGIN(st);
+    k_qsp_sum<<<grid_for(1LL << l, kThreads, 152 * 4), kThreads, 0, st>>>(l, tree);
+    HHL_LAUNCH_CHECK("k_qsp_sum");
+  }
+  HHL_PROF_BEGIN(st);
+  k_qsp_init<<<g, kThreads, 0, st>>>(psi, p.N);
+  HHL_LAUNCH_CHECK("k_qsp_init");
+  for (int l = 0; l < p.n_s; ++l) {
+    HHL_PROF_BEGIN(st);
+    k_qsp_level<<<grid_for(p.N / 2, kThreads, 152 * 4), kThreads, 0, st>>>(l, p.n_s, tree, psi);
+    HHL_LAUNCH_CHECK("k_qsp_level");
+  }
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64) k_qsp_scale<float><<<g, kThreads, 0, st>>>(psi, p.N, p.n_c, (float2*)p.d_bs);
+  else k_qsp_scale<double><<<g, kThreads, 0, st>>>(psi, p.N, p.n_c, (double2*)p.d_bs);
+  HHL_LAUNCH_CHECK("k_qsp_scale");
+  // H on every clock qubit of |0>: every clock row holds the prepared system state
+  const int64_t row_units = p.N * (int64_t)p.amp_bytes() / 16;
+  const int64_t half_units = p.R * row_units;
+  HHL_PROF_BEGIN(st);
+  k_prep_fill<<<grid_for(2 * half_units, kThreads, 152 * 16), kThreads, 0, st>>>((const uint4*)p.d_bs, (uint4*)state,
+                                                                                row_units, half_units);
+  HHL_LAUNCH_CHECK("k_prep_fill");
   return HHL_OK;
 }
 

@@ -84,6 +84,36 @@ def test_stagewise_parity(hhl, prec, full, flow, n_s, n_c, rule):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_s,n_c,kind", [(2, 3, "worked"), (4, 6, "poiseuille"), (6, 5, "random"),
+                                          (10, 4, "couette")])
+def test_qsp1_gate_level_preparation(hhl, prec, n_s, n_c, kind):
+    """The QSP-1 tree on the GPU against the oracle's gate sequence (App. C), and against the
+    direct amplitude encoding of hhl_prepare_rhs for non-negative b."""
+    import json
+    import os
+    import torch
+    from synth_inputs import random_rhs
+    N = 1 << n_s
+    if kind == "worked":
+        fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "qsp1_worked_example.json")))
+        b = np.sqrt(np.array(fx["leaf_probabilities"], dtype=np.float64))
+    elif kind == "random":
+        b = random_rhs(N, seed_offset=31)
+    else:
+        b = problem(kind, n_s)[2]
+    diag, off = o.laplacian_tridiag(N)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec)
+    st = plan.new_state()
+    plan.prepare_rhs_qsp1(torch.tensor(b, dtype=torch.float64, device="cuda"), st)
+    got = _np(st)
+    sys_ref = o.qsp1_prepare(b / np.linalg.norm(b))
+    ref = np.zeros(2 << (n_s + n_c), dtype=np.complex128)
+    ref[: 1 << (n_s + n_c)] = np.tile(sys_ref, 1 << n_c) / math.sqrt(1 << n_c)
+    np.testing.assert_allclose(got, ref, atol=TOL[prec])
+    np.testing.assert_allclose(got, o.prepare_state(b, n_s, n_c), atol=TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_shots_match_the_oracle_sampler(hhl, prec):
     """Shots of the postselected register from the same uniforms: the oracle's inverse-
     transform sampler on the oracle's final state against the GPU sampler on the GPU state;
