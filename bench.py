@@ -83,6 +83,21 @@ def _traffic(workload: str, precision: str, kernel: str):
     return ent[0] if digest == ent[2] else None
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (timings: the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world: int, slowest_s: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return world * units_per_rank / slowest_s
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -531,10 +546,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     prof = pkg.profile_read()
     step_ms = [a.elapsed_time(c) for a, c in evs]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, world)
 
     # ---- end to end through the public API with host buffers
     b_pin = torch.tensor(b, dtype=torch.float64).pin_memory()
@@ -549,12 +561,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         e = plan.dissipation(st, stream=stream)
         e2e_times.append(time.perf_counter() - t0)
     e2e_times = e2e_times[1:]
-    if world > 1:
-        t = torch.tensor([sum(e2e_times)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    else:
-        e2e_total = sum(e2e_times)
+    e2e_total = max_over_ranks(sum(e2e_times), world)
 
     if rank != 0:
         return
@@ -603,11 +610,11 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                         "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
                         "algorithmic_per_launch": per, "avg_launch_ms": avg_s * 1e3}
     if wl["unit"] == "GB/s":
-        value = world * hbm_bytes_step * args.steps / total_s / 1e9
-        e2e_value = world * hbm_bytes_step * len(e2e_times) / e2e_total / 1e9
+        value = replica_rate(hbm_bytes_step * args.steps, world, total_s) / 1e9
+        e2e_value = replica_rate(hbm_bytes_step * len(e2e_times), world, e2e_total) / 1e9
     else:
-        value = world * args.steps / total_s
-        e2e_value = world * len(e2e_times) / e2e_total
+        value = replica_rate(args.steps, world, total_s)
+        e2e_value = replica_rate(len(e2e_times), world, e2e_total)
     cpu = _cpu_baseline_subprocess(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
     out = {
         "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": args.steps,
@@ -690,10 +697,7 @@ def run_qft(args, rank: int, world: int, local_rank: int) -> None:
     pkg.profile_enable(False)
     prof = pkg.profile_read()
     total_s = sum(a.elapsed_time(c) for a, c in evs) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, world)
     step_bytes = 4.0 * states * (1 << n) * amp_bytes
     # QFT-IQFT is the identity: the state after all steps is the input up to rounding
     drift = float((view[:, :4] - x0).abs().max().item())
@@ -728,7 +732,7 @@ def run_qft(args, rank: int, world: int, local_rank: int) -> None:
     cpu = _cpu_baseline_subprocess(args.workload) if (world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": world * step_bytes * args.steps / total_s / 1e9, "unit": wl["unit"],
+            "metric": METRIC, "value": replica_rate(step_bytes * args.steps, world, total_s) / 1e9, "unit": wl["unit"],
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 (f32)" if args.precision == "c64" else "c128 (f64)", "data": "synthetic",
@@ -736,7 +740,8 @@ def run_qft(args, rank: int, world: int, local_rank: int) -> None:
                        "l2": "inputs larger than L2" if states * (1 << n) * amp_bytes > (256 << 20) else "L2-resident",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "breakdown": breakdown, "clocks": clk.summary(),
-            "e2e": {"value": world * step_bytes * len(e2e_t) / sum(e2e_t) / 1e9, "unit": wl["unit"],
+            "e2e": {"value": replica_rate(step_bytes * len(e2e_t), world, max_over_ranks(sum(e2e_t), world)) / 1e9,
+                    "unit": wl["unit"],
                     "h2d_bytes_per_step": states * (1 << n) * amp_bytes,
                     "d2h_bytes_per_step": states * (1 << n) * amp_bytes},
             "gpu_launches": launches, "cpu_baseline": cpu,
@@ -792,10 +797,7 @@ def run_batch(args, rank: int, world: int, local_rank: int) -> None:
                 evs[i][1].record(stream)
         torch.cuda.synchronize()
     total_s = sum(a.elapsed_time(c) for a, c in evs) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, world)
     res = batch.unpack(out.cpu().numpy())
     # per-kernel times from the same work launched eagerly right after the timed region
     pkg.profile_reset()
@@ -857,7 +859,7 @@ def run_batch(args, rank: int, world: int, local_rank: int) -> None:
                     "peak_source": "FP16 dense = measured bf16 burst (same nominal rate); 3 MMAs per algorithmic product",
                     "algorithmic_per_launch": tc_flops / n, "avg_launch_ms": ms / n,
                     "timing": "eager replay of the batch right after the timed region (per-kernel events)"}
-    value = world * wl["count"] * args.steps / total_s
+    value = replica_rate(wl["count"] * args.steps, world, total_s)
     ok = [f for f in fids if f >= 1 - 1e-6]
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": args.steps,
@@ -877,7 +879,8 @@ def run_batch(args, rank: int, world: int, local_rank: int) -> None:
         "plan": {"plan_seconds": t_plan, "gemm_flops_per_run": binf["gemm_flops"],
                  "state_bytes": binf["state_bytes"], "workspace_bytes": binf["workspace_bytes"]},
         "clocks": clk.summary(),
-        "e2e": {"value": world * wl["count"] * len(e2e) / sum(e2e), "unit": wl["unit"],
+        "e2e": {"value": replica_rate(wl["count"] * len(e2e), world, max_over_ranks(sum(e2e), world)),
+                "unit": wl["unit"],
                 "h2d_bytes_per_step": binf["b_doubles"] * 8, "d2h_bytes_per_step": (binf["out_doubles"] + wl["count"]) * 8},
         "gpu_launches": launches_per_run * args.steps,
         "cpu_baseline": None if (world > 1 or args.no_cpu_baseline) else _cpu_baseline_subprocess(args.workload),
