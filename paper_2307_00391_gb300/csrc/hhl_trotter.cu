@@ -47,14 +47,25 @@ constexpr int kInterior = kWin - 2 * kHalo;   // 480 written back per warp
 constexpr int kTrotThreads = 256;
 constexpr int kMaxPassLayers = kHalo + 1;     // exact with a kHalo halo when layer 0 is E
 
+// A layer list also carries each rotation in factored form, used by windows away from the
+// row ends: with |cos th| >= |sin th| (form 0)
+//   (a, b) <- (a + i w b, b + i w a) = R(th) (a, b) / cos th,        w = tan th,
+// else (form 1)
+//   (a, b) <- (b + i w a, a + i w b) = R(th) (a, b) / (i sin th),    w = -cot th,
+// two FMAs per output component instead of four, |w| <= 1; the product of the factors is
+// folded into the end-of-pass scalar (pc2, ps2). (At the row ends an amplitude without an O
+// partner would need the inverse factor, so those windows keep the plain rotations.)
 struct LayerList {
   int n;                   // layers (<= kMaxPassLayers)
   int first_o;             // 1 if layer 0 is an O layer
   double pc, ps;           // the pattern's summed E phase e^{i d (E time)} in this pass
   double c[kMaxPassLayers], s[kMaxPassLayers];  // cos / sin of each layer's rotation angle
+  double w[kMaxPassLayers];                     // factored form
+  int form[kMaxPassLayers];
+  double pc2, ps2;                              // the phase times the product of the factors
   // the same values rounded to FP32 on the host (GB300's FP64 conversions are slow)
-  float pcf, psf;
-  float cf[kMaxPassLayers], sf[kMaxPassLayers];
+  float pcf, psf, pc2f, ps2f;
+  float cf[kMaxPassLayers], sf[kMaxPassLayers], wf[kMaxPassLayers];
 };
 
 template <class R>
@@ -67,7 +78,6 @@ __device__ __forceinline__ R layer_s(const LayerList* L, int l) {
   if constexpr (sizeof(R) == 4) return L->sf[l];
   else return L->s[l];
 }
-
 __device__ __forceinline__ int64_t row_with_bit_t(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
 }
@@ -86,6 +96,40 @@ __device__ __forceinline__ T shfl_up1(T v) {
   r.x = __shfl_up_sync(0xffffffffu, v.x, 1);
   r.y = __shfl_up_sync(0xffffffffu, v.y, 1);
   return r;
+}
+
+template <class R>
+__device__ __forceinline__ R layer_w(const LayerList* L, int l) {
+  if constexpr (sizeof(R) == 4) return L->wf[l];
+  else return L->w[l];
+}
+
+// (a, b) <- (a + i w b, b + i w a), or with SWAP (b + i w a, a + i w b).
+template <bool SWAP, class T, class R>
+__device__ __forceinline__ void rot_factored(T& a, T& b, R w) {
+  const T na = mk<R>(a.x - w * b.y, a.y + w * b.x);
+  const T nb = mk<R>(b.x - w * a.y, b.y + w * a.x);
+  a = SWAP ? nb : na;
+  b = SWAP ? na : nb;
+}
+
+// All layers of a list on a window away from the row ends, in factored form (the result is
+// off by the product of the factors, applied with the end-of-pass scalar).
+template <bool SWAP, class T, class R>
+__device__ __forceinline__ void layer_factored(T (&x)[kLaneAmps], bool e_layer, R w) {
+  if (e_layer) {
+#pragma unroll
+    for (int q = 0; q < kLaneAmps; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
+  } else {
+    const T right = shfl_down1(x[0]);           // next lane's first amplitude
+    const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
+#pragma unroll
+    for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
+    const T a = x[kLaneAmps - 1], b = x[0];
+    // (this lane's last a, next lane's first) and (previous lane's last, this lane's first b)
+    x[kLaneAmps - 1] = SWAP ? mk<R>(right.x - w * a.y, right.y + w * a.x) : mk<R>(a.x - w * right.y, a.y + w * right.x);
+    x[0] = SWAP ? mk<R>(left.x - w * b.y, left.y + w * b.x) : mk<R>(b.x - w * left.y, b.y + w * left.x);
+  }
 }
 
 // Rotations R(th) = [[cos th, i sin th], [i sin th, cos th]]: E(s) = exp(i s E) is
@@ -207,7 +251,7 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint4* stage_w = reinterpret_cast<uint4*>(trot_smem) + (size_t)wid * 2 * 32 * CPL;  // two buffers
   R* rot_w = reinterpret_cast<R*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)(kTrotThreads / 32) * 2 * 32 * CPL) +
-             (size_t)wid * 2 * 32;
+             (size_t)wid * 4 * 32;
   const int64_t N = 1LL << n_s;
   // windows w = warp, warp + nwarps, ... as (row i, segment s), stepped without division
   const int nwarps = (int)gridDim.x * (kTrotThreads / 32);
@@ -239,8 +283,10 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
       const LayerList* L = lists + cur.pattern;
       const int n_layers = L->n, first_o = L->first_o;
       if (lane < n_layers) {
-        rot_w[2 * lane] = layer_c<R>(L, lane);
-        rot_w[2 * lane + 1] = layer_s<R>(L, lane);
+        rot_w[4 * lane] = layer_c<R>(L, lane);
+        rot_w[4 * lane + 1] = layer_s<R>(L, lane);
+        rot_w[4 * lane + 2] = layer_w<R>(L, lane);
+        rot_w[4 * lane + 3] = (R)L->form[lane];
       }
       const int64_t g0 = (int64_t)cur.s * kInterior;               // first interior amplitude
       const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
@@ -263,12 +309,23 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
         }
       }
       __syncwarp();
+      // warp-uniform: every O pair of the interior lanes lies inside the row (no row end in
+      // the window but possibly the halos', whose values do not reach the interior)
+      const bool away = cur.full && g0 >= 2 && g0 + kInterior + 1 <= N;
+      if (away) {
+        for (int l = 0; l < n_layers; ++l) {
+          const R wl = rot_w[4 * l + 2];
+          const bool e_layer = ((l + first_o) & 1) == 0;
+          if (rot_w[4 * l + 3] != (R)0) layer_factored<true>(x, e_layer, wl);
+          else layer_factored<false>(x, e_layer, wl);
+        }
+      }
       // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
       const bool in_ok = lane0 >= 0 && lane0 + kLaneAmps - 2 <= N - 1;
       const bool right_ok = lane < 31 && lane0 + kLaneAmps - 1 >= 1 && lane0 + kLaneAmps <= N - 1;
       const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
-      for (int l = 0; l < n_layers; ++l) {
-        const R c = rot_w[2 * l], sn = rot_w[2 * l + 1];
+      for (int l = 0; l < (away ? 0 : n_layers); ++l) {
+        const R c = rot_w[4 * l], sn = rot_w[4 * l + 1];
         if (((l + first_o) & 1) == 0) {
           // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
 #pragma unroll
@@ -297,7 +354,9 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
         }
       }
       {
-        const T ph = sizeof(R) == 4 ? mk<R>((R)L->pcf, (R)L->psf) : mk<R>((R)L->pc, (R)L->ps);
+        T ph;
+        if constexpr (sizeof(R) == 4) ph = away ? mk<R>(L->pc2f, L->ps2f) : mk<R>(L->pcf, L->psf);
+        else ph = away ? mk<R>(L->pc2, L->ps2) : mk<R>(L->pc, L->ps);
 #pragma unroll
         for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
       }
@@ -334,7 +393,7 @@ template <class R>
 size_t trotter_smem() {
   constexpr int per = 16 / sizeof(typename Cx<R>::T);
   constexpr int CPL = kLaneAmps / per;
-  return (size_t)(kTrotThreads / 32) * (2 * 32 * CPL * 16 + 2 * 32 * sizeof(R));
+  return (size_t)(kTrotThreads / 32) * (2 * 32 * CPL * 16 + 4 * 32 * sizeof(R));
 }
 
 __global__ void k_interleave(const double* __restrict__ re, const double* __restrict__ im, int64_t n,
@@ -407,19 +466,41 @@ void build_list(const Plan& p, const std::vector<int>& bits, bool adjoint, int w
   double e_time = 0.0;
   out->n = l1 - l0;
   out->first_o = layers[l0].first;
+  double fr = 1.0, fi = 0.0;  // product of the factored forms' factors
   for (int l = l0; l < l1; ++l) {
     const double th = sg * layers[l].second * oh_k;
-    out->c[l - l0] = cos(th);
-    out->s[l - l0] = sin(th);
+    const double c = cos(th), sn = sin(th);
+    out->c[l - l0] = c;
+    out->s[l - l0] = sn;
+    double gr, gi;
+    if (fabs(c) >= fabs(sn)) {
+      out->w[l - l0] = sn / c;
+      out->form[l - l0] = 0;
+      gr = c;
+      gi = 0.0;
+    } else {
+      out->w[l - l0] = -c / sn;
+      out->form[l - l0] = 1;
+      gr = 0.0;
+      gi = sn;
+    }
+    const double nr = fr * gr - fi * gi, ni = fr * gi + fi * gr;
+    fr = nr;
+    fi = ni;
     if (layers[l].first == 0) e_time += layers[l].second;
   }
   out->pc = cos(e_time * dh);
   out->ps = sg * sin(e_time * dh);
+  out->pc2 = out->pc * fr - out->ps * fi;
+  out->ps2 = out->pc * fi + out->ps * fr;
+  out->pc2f = (float)out->pc2;
+  out->ps2f = (float)out->ps2;
   out->pcf = (float)out->pc;
   out->psf = (float)out->ps;
   for (int l = 0; l < out->n; ++l) {
     out->cf[l] = (float)out->c[l];
     out->sf[l] = (float)out->s[l];
+    out->wf[l] = (float)out->w[l];
   }
 }
 
