@@ -114,3 +114,38 @@ def test_batch_rejects_unsupported_instances(hhl):
     with pytest.raises(hhl.HHLError) as e:
         hhl.HHLBatch([dict(n_sys_qubits=3, n_clock=4, diag=diag, off=off)])
     assert e.value.status == 8
+
+
+@pytest.mark.slow
+def test_full_batch_of_256_in_the_bench_configuration(hhl):
+    """The 256 uneven instances exactly as the bench runs them (autotuned GEMM choices, 8
+    worker streams, one graph): sampled instances with n_s <= 7 against the FP64 oracle one by
+    one, every instance against the invariants (unit norm, 0 < p_success <= p_anc1 <= 1)."""
+    import torch
+    from paper_2307_00391_gb300 import autotune
+    from synth_inputs import batch_instances, walls
+    inst = batch_instances(256)
+    probs = []
+    for it in inst:
+        diag, off = hhl.laplacian(1 << it["n_s"])
+        probs.append(dict(n_sys_qubits=it["n_s"], n_clock=it["n_c"], diag=diag, off=off, nu=0.1,
+                          walls=walls(it["flow"]), t0_rule="power_law", t0_scale=it["t0_mult"]))
+    choices = autotune.choices_for([(it["n_s"], it["n_c"]) for it in inst])
+    batch = hhl.HHLBatch(probs, gemm_choice=choices, streams=8)
+    out, eps = batch.run_host(batch.pack_rhs([it["b"] for it in inst]))
+    res = batch.unpack(out)
+    for i, r in enumerate(res):
+        assert r["norm"] == pytest.approx(1.0, abs=2e-4), i
+        assert 0.0 < r["p_success"] <= r["p_anc1"] + 1e-9 <= 1.0 + 1e-6, i
+        assert np.isfinite(eps[i])
+    small = [i for i, it in enumerate(inst) if it["n_s"] <= 7][:6]
+    assert len(small) >= 3
+    for i in small:
+        it, pr = inst[i], probs[i]
+        a = o.dense_from_tridiag(pr["diag"], pr["off"])
+        t0 = o.t0_total("power_law", it["n_c"], kappa=o.condition_number(a)) * it["t0_mult"]
+        pl = o.plan(a, it["n_c"], t0_rule="user", t0=t0)
+        post = o.postselect(o.hhl_circuit(it["b"], it["n_s"], pl), it["n_s"], it["n_c"])
+        assert res[i]["p_success"] == pytest.approx(post["p_success"], rel=1e-3), i
+        assert abs(np.vdot(post["xhat"], res[i]["xhat"])) > 1 - 1e-6, i
+    batch.close()

@@ -578,3 +578,32 @@ def test_split_register_passes_parity(hhl, monkeypatch, prec, full, flow, n_s, n
         hhl.profile_enable(False)
     assert all(prof[f"k_clock_pass_{x}"][0] == 1 for x in "abc") and "k_clock_block" not in prof
     assert prof["k_hadamard_pass"][0] == 2 and "k_register_transform" not in prof
+
+
+@pytest.mark.slow
+def test_qft_whole_register_32_qubits_on_a_fourier_mode(hhl):
+    """The Fig. 1c transform at full size (32 qubits, complex64, the bench's launches): the
+    QFT of the Fourier mode psi_x = e^{-2 pi i x k0 / 2^32} / 2^16 is |k0> exactly (closed
+    form), read at bit-reversed position; the inverse QFT restores the mode (sampled)."""
+    import torch
+    n, k0 = 32, 123456789
+    L = 1 << n
+    st = torch.empty(L, dtype=torch.complex64, device="cuda")
+    chunk = 1 << 28
+    for c0 in range(0, L, chunk):   # the mode in chunks (FP64 phase, exact mod 2^32)
+        x = torch.arange(c0, c0 + chunk, dtype=torch.int64, device="cuda")
+        ph = ((x * k0) % L).to(torch.float64) * (-2.0 * math.pi / L)
+        st[c0:c0 + chunk] = (torch.polar(torch.ones_like(ph), ph) / 65536.0).to(torch.complex64)
+        del x, ph
+    probe = torch.tensor([0, 1, 77, L // 3, L - 1], device="cuda")
+    before = _np(st[probe])
+    hhl.qft_whole(st, n, 1, 0)
+    rev = int(format(k0, "032b")[::-1], 2)
+    assert abs(_np(st[rev:rev + 1])[0] - 1.0) < 2e-3
+    others = torch.randint(0, L, (4096,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    others = others[others != rev]
+    assert np.abs(_np(st[others])).max() < 2e-3
+    hhl.qft_whole(st, n, 1, 1)
+    np.testing.assert_allclose(_np(st[probe]), before, atol=2e-7)
+    del st
+    torch.cuda.empty_cache()
