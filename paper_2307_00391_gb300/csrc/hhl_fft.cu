@@ -100,6 +100,21 @@ __constant__ double kRoot16[16][2] = {
     {-0.92387953251128674, 0.38268343236508978}, {-0.70710678118654752, 0.70710678118654752},
     {-0.38268343236508978, 0.92387953251128674}, {0.0, 1.0}, {0.38268343236508978, 0.92387953251128674},
     {0.70710678118654752, 0.70710678118654752}, {0.92387953251128674, 0.38268343236508978}};
+__constant__ float kRoot16f[16][2] = {
+    {1.0f, 0.0f}, {0.92387953251128674f, -0.38268343236508978f}, {0.70710678118654752f, -0.70710678118654752f},
+    {0.38268343236508978f, -0.92387953251128674f}, {0.0f, -1.0f}, {-0.38268343236508978f, -0.92387953251128674f},
+    {-0.70710678118654752f, -0.70710678118654752f}, {-0.92387953251128674f, -0.38268343236508978f}, {-1.0f, 0.0f},
+    {-0.92387953251128674f, 0.38268343236508978f}, {-0.70710678118654752f, 0.70710678118654752f},
+    {-0.38268343236508978f, 0.92387953251128674f}, {0.0f, 1.0f}, {0.38268343236508978f, 0.92387953251128674f},
+    {0.70710678118654752f, 0.70710678118654752f}, {0.92387953251128674f, 0.38268343236508978f}};
+
+// The root for the amplitude precision (FP32 kernels read FP32 constants: converting an FP64
+// constant costs a pass through GB300's narrow FP64 pipe).
+template <class R>
+__device__ __forceinline__ R root16(int k, int part) {
+  if constexpr (sizeof(R) == 4) return kRoot16f[k][part];
+  else return (R)kRoot16[k][part];
+}
 
 // The RB radix-2 stages of one group: v[x] = element lo + x * 2^lo_bits (+ a multiple of
 // 2^(lo_bits + RB)); local bit t is global stage s = t + 1 + lo_bits of an m-stage transform.
@@ -129,8 +144,8 @@ __device__ __forceinline__ void butterflies(T (&v)[1 << RB], int lo, int lo_bits
         if (xr != 0) {
           const int k16 = xr << (3 - t);
           T w;
-          w.x = (R)kRoot16[k16][0];
-          w.y = conj ? -(R)kRoot16[k16][1] : (R)kRoot16[k16][1];
+          w.x = root16<R>(k16, 0);
+          w.y = conj ? -root16<R>(k16, 1) : root16<R>(k16, 1);
           f = cmul(base, w);
         }
         if (DIT) {
@@ -642,8 +657,8 @@ __device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int l
       for (int xr = 1; xr < (1 << t); ++xr) {
         const int k16 = xr << (3 - t);
         T w;
-        w.x = (R)kRoot16[k16][0];
-        w.y = conj ? -(R)kRoot16[k16][1] : (R)kRoot16[k16][1];
+        w.x = root16<R>(k16, 0);
+        w.y = conj ? -root16<R>(k16, 1) : root16<R>(k16, 1);
         f[xr] = cmul(base, w);
       }
     }
@@ -674,13 +689,13 @@ __device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int l
 // (2^NB rows). Tile row j is register index lo_fixed + (j << b0) + (fixed bits above).
 // With a whole-register transform (inner_base >= 0) the tile's columns are register bits
 // too: the index below the pass's bits is inner_base + w + ((lo_fixed + (lo << b0)) << shift).
-template <class T, int NB, int TB, int RB, bool DIT, int MODE, class TW>
+template <class T, int NB, int TB, int RB, bool DIT, int MODE, int LW, class TW>
 __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj, int inner_base,
                                           int shift) {
-  constexpr int LW = SplitGeom<T>::LW, W = 1 << LW, G = 1 << RB;
+  constexpr int W = 1 << LW, G = 1 << RB;
   constexpr int total = W << (NB - RB);
 #pragma unroll 1
-  for (int g = threadIdx.x; g < total; g += kSplitThreads) {
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
     const int w = g & (W - 1);
     const int gg = g >> LW;
     const int lo = gg & ((1 << TB) - 1);
@@ -701,7 +716,7 @@ __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, con
 
 // All NB stages of a tile in passes of at most MR bits (DIF: high bits first), a barrier
 // after each pass.
-template <class T, int NB, bool DIT, int MODE, int Q = 0, int DONE = 0, class TW>
+template <class T, int NB, bool DIT, int MODE, int LW = SplitGeom<T>::LW, int Q = 0, int DONE = 0, class TW>
 __device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj,
                                             int inner_base = -1, int shift = 0) {
   constexpr int MR = SplitGeom<T>::MR;
@@ -709,9 +724,9 @@ __device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, c
   if constexpr (Q < NPASS) {
     constexpr int RB = (NB - DONE) / (NPASS - Q);
     constexpr int TB = DIT ? DONE : NB - DONE - RB;
-    tile_pass<T, NB, TB, RB, DIT, MODE>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
+    tile_pass<T, NB, TB, RB, DIT, MODE, LW>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
     __syncthreads();
-    tile_stages<T, NB, DIT, MODE, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
+    tile_stages<T, NB, DIT, MODE, LW, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
   }
 }
 
@@ -934,6 +949,298 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   }
 }
 
+// ------------------------------------------------------------- one-pass clustered clock block
+// The clock block of a large state in one HBM pass: a cluster of 8 CTAs holds one 128-byte
+// column block of all 2^m clock rows (m <= 13: 1 MiB for complex64), CTA r the rows
+// p = 8 j + r. The inverse-QFT DIF stages on the top m - 3 bits are local to each CTA; the
+// three stages on bits 2..0 pair rows of different CTAs. For those, CTA r takes the positions
+// j in [r J/8, (r+1) J/8) of every CTA (J = 2^(m-3)), gathers the 8 values of a position
+// through distributed shared memory, runs the last three DIF stages, the rotation at the
+// bit-reversed frequency (storing the cos part to the anc = 0 half) and the first three DIT
+// stages of the QFT, and writes the 8 results back to their owners: one exchange, no
+// butterfly computed twice. Then each CTA runs the remaining DIT stages locally and stores its
+// rows to the anc = 1 half: the half is read once and both halves are written once.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;
+
+template <class R, int NB>
+__global__ void __launch_bounds__(kClusterThreads, 1) k_clock_cluster(typename Cx<R>::T* __restrict__ S,
+                                                                    const typename Cx<R>::T* __restrict__ rot,
+                                                                    int n_s, int m, R scale) {
+  using T = typename Cx<R>::T;
+  constexpr int LW = sizeof(T) == 8 ? 4 : 3;  // W = 128 bytes of amplitudes per row
+  constexpr int W = 1 << LW;
+  constexpr int J = 1 << NB;                  // local rows
+  constexpr int per = 16 / sizeof(T);
+  constexpr int upr = W / per;                // 16-byte units per row segment
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  T* X = t0 + twiddle_entries(m);
+  fill_twiddles<R>(t0, t1, m);
+  const Twiddle<T> tw{t0, t1};
+  const int64_t N = 1LL << n_s;
+  const int64_t half = N << m;
+  const int64_t j0 = (int64_t)(blockIdx.x / kClusterCtas) * W;  // first system column
+  T* S0 = S;
+  T* S1 = S + half;
+  const int64_t row_units = N / per;  // 16-byte units per state row
+  // load rows p = 8 j + r
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(S0 + j0);
+    uint4* dst = reinterpret_cast<uint4*>(X);
+    for (int u0 = threadIdx.x; u0 < J * upr; u0 += kClusterThreads * 4) {
+      uint4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int u = u0 + k * kClusterThreads;
+        if (u < J * upr) v[k] = src[((int64_t)kClusterCtas * (u / upr) + r) * row_units + (u % upr)];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int u = u0 + k * kClusterThreads;
+        if (u < J * upr) dst[u] = v[k];
+      }
+    }
+  }
+  __syncthreads();
+  // inverse QFT: DIF stages on register bits 3 .. m-1 (row index p = r + 8 j)
+  tile_stages<T, NB, false, 0, LW>(X, 3, r, m, tw, false);
+  cl.sync();
+  // the three cross-CTA stages, the rotation and the first three QFT stages on this CTA's share
+  {
+    T* rem[kClusterCtas];
+#pragma unroll
+    for (int q = 0; q < kClusterCtas; ++q) rem[q] = cl.map_shared_rank(X, q);
+    constexpr int share = (J / kClusterCtas) * W;  // positions per CTA
+    uint4* cos_out = reinterpret_cast<uint4*>(S0 + j0);
+    for (int e = threadIdx.x; e < share; e += kClusterThreads) {
+      const int jj = r * (J / kClusterCtas) + (e >> LW), w = e & (W - 1);
+      const int off = (jj << LW) + w;
+      T v[kClusterCtas];
+#pragma unroll
+      for (int q = 0; q < kClusterCtas; ++q) v[q] = rem[q][off];
+      group_butterflies<T, 3, false, 0>(v, 0, 0, m, tw, false);
+#pragma unroll
+      for (int q = 0; q < kClusterCtas; ++q) {
+        const int y = bitrev_m(kClusterCtas * jj + q, m);
+        const T rr = rot[y];
+        const T x = cscale(v[q], scale);
+        const T c = cscale(x, rr.x);
+        v[q] = cscale(x, rr.y * scale);
+        if constexpr (sizeof(T) == 8) {
+          // pairs of columns make one 16-byte unit: the even lane of each pair stores both
+          const T c1 = mk<R>(__shfl_down_sync(0xffffffffu, c.x, 1), __shfl_down_sync(0xffffffffu, c.y, 1));
+          if ((w & 1) == 0) {
+            uint4 pk;
+            T* pt = reinterpret_cast<T*>(&pk);
+            pt[0] = c;
+            pt[1] = c1;
+            cos_out[(int64_t)y * row_units + (w >> 1)] = pk;
+          }
+        } else {
+          reinterpret_cast<T*>(cos_out)[(int64_t)y * N + w] = c;
+        }
+      }
+      group_butterflies<T, 3, true, 0>(v, 0, 0, m, tw, true);
+#pragma unroll
+      for (int q = 0; q < kClusterCtas; ++q) rem[q][off] = v[q];
+    }
+  }
+  cl.sync();
+  // QFT: DIT stages on register bits 3 .. m-1
+  tile_stages<T, NB, true, 0, LW>(X, 3, r, m, tw, true);
+  // store rows p = 8 j + r of the anc = 1 half
+  {
+    uint4* dst = reinterpret_cast<uint4*>(S1 + j0);
+    const uint4* src = reinterpret_cast<const uint4*>(X);
+    for (int u = threadIdx.x; u < J * upr; u += kClusterThreads)
+      dst[((int64_t)kClusterCtas * (u / upr) + r) * row_units + (u % upr)] = src[u];
+  }
+}
+
+// The Hadamard layer on the clock of a large state in one pass, with the same cluster layout:
+// the Hadamard stages on bits 3 .. m-1 locally, the three on bits 2..0 through one exchange
+// (the stages commute, so their order is free), scaled by 2^(-m/2) on the way.
+template <class R, int NB>
+__global__ void __launch_bounds__(kClusterThreads, 1) k_hadamard_cluster(typename Cx<R>::T* __restrict__ S, int n_s,
+                                                                       int m, R scale) {
+  using T = typename Cx<R>::T;
+  constexpr int LW = sizeof(T) == 8 ? 4 : 3;
+  constexpr int W = 1 << LW;
+  constexpr int J = 1 << NB;
+  constexpr int per = 16 / sizeof(T);
+  constexpr int upr = W / per;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  T* X = reinterpret_cast<T*>(smem_raw);
+  const Twiddle<T> tw{X, X};  // unused by the Hadamard butterflies
+  const int64_t N = 1LL << n_s;
+  const int64_t j0 = (int64_t)(blockIdx.x / kClusterCtas) * W;
+  const int64_t row_units = N / per;
+  uint4* base = reinterpret_cast<uint4*>(S + j0);
+  for (int u0 = threadIdx.x; u0 < J * upr; u0 += kClusterThreads * 4) {
+    uint4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int u = u0 + k * kClusterThreads;
+      if (u < J * upr) v[k] = base[((int64_t)kClusterCtas * (u / upr) + r) * row_units + (u % upr)];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int u = u0 + k * kClusterThreads;
+      if (u < J * upr) reinterpret_cast<uint4*>(X)[u] = v[k];
+    }
+  }
+  __syncthreads();
+  tile_stages<T, NB, false, 1, LW>(X, 3, r, m, tw, false);
+  cl.sync();
+  {
+    T* rem[kClusterCtas];
+#pragma unroll
+    for (int q = 0; q < kClusterCtas; ++q) rem[q] = cl.map_shared_rank(X, q);
+    constexpr int share = (J / kClusterCtas) * W;
+    for (int e = threadIdx.x; e < share; e += kClusterThreads) {
+      const int off = ((r * (J / kClusterCtas) + (e >> LW)) << LW) + (e & (W - 1));
+      T v[kClusterCtas];
+#pragma unroll
+      for (int q = 0; q < kClusterCtas; ++q) v[q] = rem[q][off];
+      group_butterflies<T, 3, false, 1>(v, 0, 0, m, tw, false);
+#pragma unroll
+      for (int q = 0; q < kClusterCtas; ++q) rem[q][off] = cscale(v[q], scale);
+    }
+  }
+  cl.sync();
+  for (int u = threadIdx.x; u < J * upr; u += kClusterThreads)
+    base[((int64_t)kClusterCtas * (u / upr) + r) * row_units + (u % upr)] = reinterpret_cast<const uint4*>(X)[u];
+}
+
+template <class R, int NB>
+hhl_status hadamard_cluster_nb(void* half_base, int n_s, int m, int outer, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  constexpr int W = sizeof(T) == 8 ? 16 : 8;
+  auto kern = k_hadamard_cluster<R, NB>;
+  const size_t smem = ((size_t)1 << NB) * 128;
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  R scale = (R)(1.0 / sqrt((double)(1LL << m)));
+  for (int o = 0; o < outer; ++o) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(((1LL << n_s) / W) * kClusterCtas));
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    T* S = (T*)half_base + ((size_t)o << (n_s + m));
+    int ns = n_s, mm = m;
+    void* args[] = {&S, &ns, &mm, &scale};
+    HHL_PROF_BEGIN(st);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (g_prof_on.load(std::memory_order_relaxed)) prof_end("k_hadamard_cluster");
+      return cuda_fail(e, "k_hadamard_cluster");
+    }
+    HHL_LAUNCH_CHECK("k_hadamard_cluster");
+  }
+  return HHL_OK;
+}
+
+template <class R>
+hhl_status hadamard_cluster(void* half_base, int n_s, int m, int outer, cudaStream_t st) {
+  switch (m - 3) {
+    case 5: return hadamard_cluster_nb<R, 5>(half_base, n_s, m, outer, st);
+    case 6: return hadamard_cluster_nb<R, 6>(half_base, n_s, m, outer, st);
+    case 7: return hadamard_cluster_nb<R, 7>(half_base, n_s, m, outer, st);
+    case 8: return hadamard_cluster_nb<R, 8>(half_base, n_s, m, outer, st);
+    case 9: return hadamard_cluster_nb<R, 9>(half_base, n_s, m, outer, st);
+    default: return hadamard_cluster_nb<R, 10>(half_base, n_s, m, outer, st);
+  }
+}
+
+template <class R>
+bool hadamard_cluster_applies(int n_s, int m, long long region_amps) {  // opt-in, as above
+  (void)region_amps;
+  if (m < 8 || m > 13) return false;
+  if (((size_t)1 << n_s) * sizeof(typename Cx<R>::T) < 128) return false;
+  const char* env = getenv("HHL_CLOCK_CLUSTER");
+  return env != nullptr && atoi(env) != 0;
+}
+
+template <class R>
+size_t clock_cluster_smem(int m) {
+  using T = typename Cx<R>::T;
+  return (size_t)twiddle_entries(m) * sizeof(T) + ((size_t)1 << (m - 3)) * 128;
+}
+
+// The clustered one-pass clock block serves 8 <= m <= 13, postselect-early mode (the cos
+// part goes straight to the anc = 0 half) and rows of at least 128 bytes, when
+// HHL_CLOCK_CLUSTER=1: measured on GB300 it is slower than the three split passes (one CTA of
+// 128 KiB per SM cannot overlap its load, exchange and store phases, and the cluster barrier
+// after the exchange waits for the cos-part stores to drain), so it is not the default.
+template <class R>
+bool clock_cluster_applies(const Plan& p) {
+  if (p.full || p.n_c < 8 || p.n_c > 13) return false;
+  if ((size_t)p.N * sizeof(typename Cx<R>::T) < 128) return false;
+  const char* env = getenv("HHL_CLOCK_CLUSTER");
+  return env != nullptr && atoi(env) != 0;
+}
+
+template <class R, int NB>
+hhl_status clock_cluster_nb(const Plan& p, void* state, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  constexpr int W = sizeof(T) == 8 ? 16 : 8;
+  auto kern = k_clock_cluster<R, NB>;
+  const size_t smem = clock_cluster_smem<R>(p.n_c);
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((p.N / W) * kClusterCtas));
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  T* S = (T*)state;
+  const T* rot = (const T*)p.d_rot;
+  int n_s = p.n_s, m = p.n_c;
+  R scale = (R)(1.0 / sqrt((double)p.R));
+  void* args[] = {&S, &rot, &n_s, &m, &scale};
+  HHL_PROF_BEGIN(st);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (g_prof_on.load(std::memory_order_relaxed)) prof_end("k_clock_cluster");
+    return cuda_fail(e, "k_clock_cluster");
+  }
+  HHL_LAUNCH_CHECK("k_clock_cluster");
+  return HHL_OK;
+}
+
+template <class R>
+hhl_status clock_block_cluster(const Plan& p, void* state, cudaStream_t st) {
+  switch (p.n_c - 3) {
+    case 5: return clock_cluster_nb<R, 5>(p, state, st);
+    case 6: return clock_cluster_nb<R, 6>(p, state, st);
+    case 7: return clock_cluster_nb<R, 7>(p, state, st);
+    case 8: return clock_cluster_nb<R, 8>(p, state, st);
+    case 9: return clock_cluster_nb<R, 9>(p, state, st);
+    default: return clock_cluster_nb<R, 10>(p, state, st);
+  }
+}
+
 // Three-level twiddle tables of the 2^n-point transform, built on the host in FP64 once per
 // (device, n, precision) and kept for the process.
 template <class R>
@@ -1074,10 +1381,12 @@ hhl_status hadamard_split(void* base, int lo, int m, int outer, cudaStream_t st)
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
   const long long half = p.R * p.N;
   if (p.prec == HHL_PREC_C64) {
+    if (clock_cluster_applies<float>(p)) return clock_block_cluster<float>(p, state, st);
     if (split_applies<float>(p.n_s, p.n_c, half))
       return p.full ? clock_block_split<float, true>(p, state, st) : clock_block_split<float, false>(p, state, st);
     return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
   }
+  if (clock_cluster_applies<double>(p)) return clock_block_cluster<double>(p, state, st);
   if (split_applies<double>(p.n_s, p.n_c, half))
     return p.full ? clock_block_split<double, true>(p, state, st) : clock_block_split<double, false>(p, state, st);
   return p.full ? clock_block_impl<double, true>(p, state, st) : clock_block_impl<double, false>(p, state, st);
@@ -1089,9 +1398,14 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
   void* base = p.full ? state : (void*)((char*)state + half_amps * p.amp_bytes());
   const int n = p.full ? p.n : p.n - 1;
   const int outer = p.full ? 2 : 1;
-  if (p.prec == HHL_PREC_C64)
+  if (p.prec == HHL_PREC_C64) {
+    if (hadamard_cluster_applies<float>(p.n_s, p.n_c, half_amps))
+      return hadamard_cluster<float>(base, p.n_s, p.n_c, outer, st);
     return split_applies<float>(p.n_s, p.n_c, half_amps) ? hadamard_split<float>(base, p.n_s, p.n_c, outer, st)
                                                          : register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
+  }
+  if (hadamard_cluster_applies<double>(p.n_s, p.n_c, half_amps))
+    return hadamard_cluster<double>(base, p.n_s, p.n_c, outer, st);
   return split_applies<double>(p.n_s, p.n_c, half_amps) ? hadamard_split<double>(base, p.n_s, p.n_c, outer, st)
                                                         : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
 }

@@ -543,6 +543,40 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("flow,n_s,n_c", [("couette", 4, 8), ("poiseuille", 5, 9), ("couette", 6, 11),
+                                          ("poiseuille", 4, 13)])
+def test_cluster_clock_block_parity(hhl, monkeypatch, prec, flow, n_s, n_c):
+    """The one-pass clustered clock block and Hadamard layer (the path of large states),
+    forced on small states, against the oracle stage by stage; postselect-early mode."""
+    import torch
+    monkeypatch.setenv("HHL_CLOCK_CLUSTER", "1")
+    diag, off, b, walls = problem(flow, n_s)
+    pl = _oracle_plan(diag, off, n_c, "range_fill")
+    ref = run_stages(b, n_s, pl)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, gemm="simt")
+    st = plan.new_state()
+    plan.prepare_rhs(_b_dev(b), st)
+    plan.apply_stage("qpe_u", st)
+    tol = TOL[prec]
+    hhl.profile_reset()
+    hhl.profile_enable(True)
+    try:
+        plan.apply_stage("clock_block", st)
+        got = _np(st)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["clock_block"], n_s, n_c, 1), atol=tol)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 0), _half(ref["rotated"], n_s, n_c, 0), atol=tol)
+        plan.apply_stage("uncompute_u", st)
+        plan.apply_stage("final_h", st)
+        got = _np(st)
+        np.testing.assert_allclose(_half(got, n_s, n_c, 1), _half(ref["final_h"], n_s, n_c, 1), atol=tol)
+        torch.cuda.synchronize()
+        prof = hhl.profile_read()
+    finally:
+        hhl.profile_enable(False)
+    assert prof["k_clock_cluster"][0] == 1 and prof["k_hadamard_cluster"][0] == 1
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("flow,n_s,n_c", [("couette", 5, 8), ("poiseuille", 6, 9), ("couette", 7, 11)])
 def test_split_register_passes_parity(hhl, monkeypatch, prec, full, flow, n_s, n_c):
@@ -550,6 +584,7 @@ def test_split_register_passes_parity(hhl, monkeypatch, prec, full, flow, n_s, n
     take), forced on small states, stage by stage against the oracle."""
     import torch
     monkeypatch.setenv("HHL_FFT_SPLIT", "1")
+    monkeypatch.setenv("HHL_CLOCK_CLUSTER", "0")
     diag, off, b, walls = problem(flow, n_s)
     pl = _oracle_plan(diag, off, n_c, "range_fill")
     ref = run_stages(b, n_s, pl)
