@@ -960,15 +960,19 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
 // stages of the QFT, and writes the 8 results back to their owners: one exchange, no
 // butterfly computed twice. Then each CTA runs the remaining DIT stages locally and stores its
 // rows to the anc = 1 half: the half is read once and both halves are written once.
+template <class R>
+hhl_status whole_tables(int n, const void* out[3]);
+
 constexpr int kClusterCtas = 8;
-constexpr int kClusterThreads = 512;
+constexpr int kClusterThreads = 256;
+constexpr int kClusterSegBytes = 64;  // bytes per row segment: 64 KiB per CTA at m = 13, 2 CTAs per SM
 
 template <class R, int NB>
-__global__ void __launch_bounds__(kClusterThreads, 1) k_clock_cluster(typename Cx<R>::T* __restrict__ S,
+__global__ void __launch_bounds__(kClusterThreads, 2) k_clock_cluster(typename Cx<R>::T* __restrict__ S,
                                                                     const typename Cx<R>::T* __restrict__ rot,
-                                                                    int n_s, int m, R scale) {
+                                                                    int n_s, int m, R scale, Twiddle3<typename Cx<R>::T> tw) {
   using T = typename Cx<R>::T;
-  constexpr int LW = sizeof(T) == 8 ? 4 : 3;  // W = 128 bytes of amplitudes per row
+  constexpr int LW = sizeof(T) == 8 ? 3 : 2;  // W = kClusterSegBytes of amplitudes per row
   constexpr int W = 1 << LW;
   constexpr int J = 1 << NB;                  // local rows
   constexpr int per = 16 / sizeof(T);
@@ -976,11 +980,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_clock_cluster(typename C
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank();
-  T* t0 = reinterpret_cast<T*>(smem_raw);
-  T* t1 = t0 + 64;
-  T* X = t0 + twiddle_entries(m);
-  fill_twiddles<R>(t0, t1, m);
-  const Twiddle<T> tw{t0, t1};
+  T* X = reinterpret_cast<T*>(smem_raw);
   const int64_t N = 1LL << n_s;
   const int64_t half = N << m;
   const int64_t j0 = (int64_t)(blockIdx.x / kClusterCtas) * W;  // first system column
@@ -1065,10 +1065,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_clock_cluster(typename C
 // the Hadamard stages on bits 3 .. m-1 locally, the three on bits 2..0 through one exchange
 // (the stages commute, so their order is free), scaled by 2^(-m/2) on the way.
 template <class R, int NB>
-__global__ void __launch_bounds__(kClusterThreads, 1) k_hadamard_cluster(typename Cx<R>::T* __restrict__ S, int n_s,
+__global__ void __launch_bounds__(kClusterThreads, 2) k_hadamard_cluster(typename Cx<R>::T* __restrict__ S, int n_s,
                                                                        int m, R scale) {
   using T = typename Cx<R>::T;
-  constexpr int LW = sizeof(T) == 8 ? 4 : 3;
+  constexpr int LW = sizeof(T) == 8 ? 3 : 2;
   constexpr int W = 1 << LW;
   constexpr int J = 1 << NB;
   constexpr int per = 16 / sizeof(T);
@@ -1121,9 +1121,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_hadamard_cluster(typenam
 template <class R, int NB>
 hhl_status hadamard_cluster_nb(void* half_base, int n_s, int m, int outer, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  constexpr int W = sizeof(T) == 8 ? 16 : 8;
+  constexpr int W = kClusterSegBytes / (int)sizeof(T);
   auto kern = k_hadamard_cluster<R, NB>;
-  const size_t smem = ((size_t)1 << NB) * 128;
+  const size_t smem = ((size_t)1 << NB) * kClusterSegBytes;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   R scale = (R)(1.0 / sqrt((double)(1LL << m)));
   for (int o = 0; o < outer; ++o) {
@@ -1170,15 +1170,14 @@ template <class R>
 bool hadamard_cluster_applies(int n_s, int m, long long region_amps) {  // opt-in, as above
   (void)region_amps;
   if (m < 8 || m > 13) return false;
-  if (((size_t)1 << n_s) * sizeof(typename Cx<R>::T) < 128) return false;
+  if (((size_t)1 << n_s) * sizeof(typename Cx<R>::T) < kClusterSegBytes) return false;
   const char* env = getenv("HHL_CLOCK_CLUSTER");
   return env != nullptr && atoi(env) != 0;
 }
 
 template <class R>
 size_t clock_cluster_smem(int m) {
-  using T = typename Cx<R>::T;
-  return (size_t)twiddle_entries(m) * sizeof(T) + ((size_t)1 << (m - 3)) * 128;
+  return ((size_t)1 << (m - 3)) * kClusterSegBytes;
 }
 
 // The clustered one-pass clock block serves 8 <= m <= 13, postselect-early mode (the cos
@@ -1189,7 +1188,7 @@ size_t clock_cluster_smem(int m) {
 template <class R>
 bool clock_cluster_applies(const Plan& p) {
   if (p.full || p.n_c < 8 || p.n_c > 13) return false;
-  if ((size_t)p.N * sizeof(typename Cx<R>::T) < 128) return false;
+  if ((size_t)p.N * sizeof(typename Cx<R>::T) < kClusterSegBytes) return false;
   const char* env = getenv("HHL_CLOCK_CLUSTER");
   return env != nullptr && atoi(env) != 0;
 }
@@ -1197,7 +1196,11 @@ bool clock_cluster_applies(const Plan& p) {
 template <class R, int NB>
 hhl_status clock_cluster_nb(const Plan& p, void* state, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  constexpr int W = sizeof(T) == 8 ? 16 : 8;
+  constexpr int W = kClusterSegBytes / (int)sizeof(T);
+  const void* tabs[3];
+  hhl_status ts = whole_tables<R>(p.n_c, tabs);
+  if (ts != HHL_OK) return ts;
+  Twiddle3<T> tw{(const T*)tabs[0], (const T*)tabs[1], (const T*)tabs[2]};
   auto kern = k_clock_cluster<R, NB>;
   const size_t smem = clock_cluster_smem<R>(p.n_c);
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1217,7 +1220,7 @@ hhl_status clock_cluster_nb(const Plan& p, void* state, cudaStream_t st) {
   const T* rot = (const T*)p.d_rot;
   int n_s = p.n_s, m = p.n_c;
   R scale = (R)(1.0 / sqrt((double)p.R));
-  void* args[] = {&S, &rot, &n_s, &m, &scale};
+  void* args[] = {&S, &rot, &n_s, &m, &scale, &tw};
   HHL_PROF_BEGIN(st);
   cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
   if (e != cudaSuccess) {
