@@ -83,7 +83,7 @@ struct Plan {
   // device tables
   void* d_bfwd = nullptr;     // n_c matrices, B_fwd[k][m][n] = U_k[n][m]   (SIMT GEMM operand)
   void* d_badj = nullptr;     // n_c matrices, B_adj[k][m][n] = conj(U_k[m][n])
-  void* d_tc = nullptr;       // tcgen05 operands (split-TF32 real embeddings), see hhl_gemm_tc.cu
+  void* d_tc = nullptr;       // tcgen05 operands (split-FP16 real embeddings), see hhl_gemm_tc.cu
   void* d_rot = nullptr;      // 2^n_c (cos(theta/2), sin(theta/2)) pairs, amplitude precision
   double* d_scal = nullptr;   // device scalars: [0] |b|^2, [1..3] measure sums, [4] eps sum, [5] p_anc1
   double* d_b = nullptr;      // N complex128: host-prepared b

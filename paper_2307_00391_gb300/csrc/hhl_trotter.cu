@@ -6,12 +6,12 @@
 // S(tau) = E(tau/2) O(tau) E(tau/2) with E(s) = exp(i s E), and r steps merge into the
 // layer list E(tau/2), O(tau), [E(tau), O(tau)] x (r-1), E(tau/2) (2r + 1 layers).
 //
-// Every layer acts inside one system-register row, so a pass applies up to 16 layers to a
+// Every layer acts inside one system-register row, so a pass applies up to 17 layers to a
 // window of the row held in registers (temporal blocking): one warp owns 512 consecutive
 // amplitudes, 16 per lane, so E pairs and all but one O pair per lane are in the lane's
 // own registers and the remaining O pair crosses to the next lane by a warp shuffle. The
-// window has a 16-amplitude halo on each side (lanes 0 and 31), as wide as the number of
-// layers of a pass, and its 480-amplitude interior (lanes 1..30) is written back in place.
+// window has a 16-amplitude halo on each side (lanes 0 and 31), and its 480-amplitude
+// interior (lanes 1..30) is written back in place.
 // The halos are the edges of the neighbouring interiors, which the same pass overwrites,
 // so a small kernel first saves the 16 leading and 16 trailing amplitudes of every interior
 // into a side buffer and the pass reads its halos from there: each pass moves the rows
@@ -28,6 +28,10 @@
 // bit whose own list is longer gets passes over windows of its layers. For the 32-qubit
 // Poiseuille case (r_k = 1 for k < 8) 13 single-bit passes over half the rows each become 5
 // passes, 3 of them over half the rows.
+//
+// Warps are persistent: each walks windows with a stride of the grid's warp count, and the
+// 16-byte copies of its next window (interior from the state, halos from the side buffer) go
+// into a second staging buffer with cp.async while it computes the current one.
 #include <math.h>
 #include <string.h>
 

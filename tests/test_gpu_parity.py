@@ -437,7 +437,7 @@ def test_couette_1024_c64_fidelity_against_c128(hhl, couette_1024_oracle):
 
 @pytest.mark.parametrize("n_s,n_c", [(7, 8), (8, 9), (9, 10)])
 def test_tcgen05_gemm_parity(hhl, n_s, n_c):
-    """Split-TF32 tcgen05 controlled-U GEMMs (1 to 4 tiles in each direction) against the
+    """Split-FP16 tcgen05 controlled-U GEMMs (1 to 4 tiles in each direction) against the
     oracle, stage by stage, complex64 tolerance."""
     diag, off, b, walls = problem("couette", n_s)
     pl = _oracle_plan(diag, off, n_c, "range_fill")
