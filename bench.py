@@ -474,6 +474,9 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_clock_pass_b": ("byte", 3.0 * half / 3),
         "k_clock_pass_c": ("byte", 3.0 * half / 3),
         "k_hadamard_pass": ("byte", 2.0 * half / 2),
+        # the same stages as single L2-staged group launches
+        "k_clock_group": ("byte", 3.0 * half),
+        "k_hadamard_group": ("byte", 2.0 * half),
         "k_prep_fill": ("byte", 2.0 * half),
         "k_measure_sums": ("byte", 2.0 * half),
         # grouped Trotter passes change different row counts: the plan's total over its passes

@@ -801,6 +801,62 @@ __device__ __forceinline__ TilePos tile_pos(const SplitArgs& a, long long t) {
   return q;
 }
 
+// The work on one landed tile of a split pass (transform stages, the pass's epilogue and the
+// store back), shared by the streaming passes and the L2-staged group passes below.
+template <class R, int OP, bool FULL, int NB, bool WHOLE, class TW>
+__device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q, typename Cx<R>::T* X,
+                                           typename Cx<R>::T* Y, const TW& tw, int mt, long long row_units) {
+  using T = typename Cx<R>::T;
+  constexpr int upr = kSplitSegBytes / 16;
+  constexpr int per = 16 / sizeof(T);
+  T* dst = static_cast<T*>(a.dst) + q.base_amp;
+  if (WHOLE) {
+    // whole-register QFT (DIF, + sign) or inverse QFT (DIT, - sign)
+    if (OP == kSplitDif) tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, mt, tw, true, q.inner_base, a.lo);
+    else tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, mt, tw, false, q.inner_base, a.lo);
+    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+  } else if (OP == kSplitDif) {
+    tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
+    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+  } else if (OP == kSplitDit) {
+    tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, a.m, tw, true);
+    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+  } else if (OP == kSplitHad) {
+    tile_stages<T, NB, false, 1>(X, a.b0, q.lo_fixed, a.m, tw, false);
+    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
+  } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
+    tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
+    const R s = split_scale<R>(a);
+    const T* rot = static_cast<const T*>(a.rot);
+    uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + q.base_amp);
+    for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
+      const int j = u / upr, h = u - j * upr;
+      const int y = bitrev_m(j + (q.hi_fixed << NB), a.m);
+      const T r = rot[y];
+      uint4 xv = reinterpret_cast<uint4*>(X)[u];
+      uint4 keep, yv;
+      T* xt = reinterpret_cast<T*>(&xv);
+      T* kt = reinterpret_cast<T*>(&keep);
+      T* yt = reinterpret_cast<T*>(&yv);
+#pragma unroll
+      for (int e = 0; e < per; ++e) {
+        const T x = cscale(xt[e], s);
+        if (FULL) yt[e] = cscale(x, r.x * s);
+        else kt[e] = cscale(x, r.x);
+        xt[e] = cscale(x, r.y * s);
+      }
+      reinterpret_cast<uint4*>(X)[u] = xv;
+      if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
+      else cos_out[(long long)y * row_units + h] = keep;
+    }
+    __syncthreads();
+    tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
+    if (FULL) tile_stages<T, NB, true, 0>(Y, 0, 0, a.m, tw, true);
+    tile_store<T, NB>(dst, X, row_units, q.row0, 0, (R)1, false);
+    if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, q.row0, 0, (R)1, false);
+  }
+}
+
 // WHOLE: the register is the whole index range [0, lo + m) of each outer block, the tile
 // rows are its bits [lo + b0, lo + b0 + NB) and the twiddles are those of the 2^(lo + m) point
 // transform (three-level global tables); only the DIF and DIT passes are used this way.
@@ -808,7 +864,6 @@ template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
-  constexpr int upr = kSplitSegBytes / 16;
   constexpr int per = 16 / sizeof(T);
   constexpr size_t tile_amps = (size_t)1 << (NB + LW);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -849,53 +904,7 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
     split_cp_async_wait1();
     __syncthreads();  // the current tile has landed for every thread
     const TilePos q = tile_pos<NB, LW>(a, t);
-    T* X = Xb + buf * tile_amps;
-    T* dst = static_cast<T*>(a.dst) + q.base_amp;
-    if (WHOLE) {
-      // whole-register QFT (DIF, + sign) or inverse QFT (DIT, - sign)
-      if (OP == kSplitDif) tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, mt, tw, true, q.inner_base, a.lo);
-      else tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, mt, tw, false, q.inner_base, a.lo);
-      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
-    } else if (OP == kSplitDif) {
-      tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
-      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
-    } else if (OP == kSplitDit) {
-      tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, a.m, tw, true);
-      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
-    } else if (OP == kSplitHad) {
-      tile_stages<T, NB, false, 1>(X, a.b0, q.lo_fixed, a.m, tw, false);
-      tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
-    } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
-      tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
-      const R s = split_scale<R>(a);
-      const T* rot = static_cast<const T*>(a.rot);
-      uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + q.base_amp);
-      for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
-        const int j = u / upr, h = u - j * upr;
-        const int y = bitrev_m(j + (q.hi_fixed << NB), a.m);
-        const T r = rot[y];
-        uint4 xv = reinterpret_cast<uint4*>(X)[u];
-        uint4 keep, yv;
-        T* xt = reinterpret_cast<T*>(&xv);
-        T* kt = reinterpret_cast<T*>(&keep);
-        T* yt = reinterpret_cast<T*>(&yv);
-#pragma unroll
-        for (int e = 0; e < per; ++e) {
-          const T x = cscale(xt[e], s);
-          if (FULL) yt[e] = cscale(x, r.x * s);
-          else kt[e] = cscale(x, r.x);
-          xt[e] = cscale(x, r.y * s);
-        }
-        reinterpret_cast<uint4*>(X)[u] = xv;
-        if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
-        else cos_out[(long long)y * row_units + h] = keep;
-      }
-      __syncthreads();
-      tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
-      if (FULL) tile_stages<T, NB, true, 0>(Y, 0, 0, a.m, tw, true);
-      tile_store<T, NB>(dst, X, row_units, q.row0, 0, (R)1, false);
-      if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, q.row0, 0, (R)1, false);
-    }
+    split_tile<R, OP, FULL, NB, WHOLE>(a, q, Xb + buf * tile_amps, Y, tw, mt, row_units);
     __syncthreads();  // this buffer is read out before it is refilled
     buf ^= 1;
   }
@@ -947,6 +956,334 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
     case 7: return launch_split_nb<R, OP, FULL, 7, WHOLE>(a, st, name);
     default: return fail(HHL_ERR_UNSUPPORTED, "split register pass: tile bits out of range");
   }
+}
+
+// ------------------------------------------------------------- register-resident tiles
+// A tile of 2^NB rows x 32 columns (NB >= 6) held in registers, 2^(NB-3) amplitudes per
+// thread, in one of two layouts; in both, the 32 lanes of a warp cover the 32 columns of a
+// row (256 contiguous bytes: coalesced global access, conflict-free shared memory):
+//   layout 1: element k of warp w is row w + 8 k     (row bits 3.. in registers),
+//   layout 2: element k of warp w is row 8 (w + 8 (k >> 3)) + (k & 7)   (row bits 0..2).
+// A transform over the tile's bits runs the butterflies of one layout, swaps layouts through
+// shared memory once, and runs the rest: one shared-memory round trip per amplitude instead
+// of the staged tile's three (copy in, two radix passes, copy out).
+template <int LAY>
+__device__ __forceinline__ int reg_row(int w, int k) {
+  return LAY == 1 ? w + 8 * k : 8 * (w + 8 * (k >> 3)) + (k & 7);
+}
+
+template <class T, int NB, int LAY>
+__device__ __forceinline__ void reg_load(T (&v)[1 << (NB - 3)], const T* base, const TilePos& q, int lo, int b0) {
+  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const T* p = base + q.base_amp + c;
+#pragma unroll
+  for (int k = 0; k < (1 << (NB - 3)); ++k)
+    v[k] = __ldcg(p + ((q.row0 + ((long long)reg_row<LAY>(w, k) << b0)) << lo));
+}
+
+template <class T, int NB, int LAY, class S>
+__device__ __forceinline__ void reg_store(const T (&v)[1 << (NB - 3)], T* base, const TilePos& q, int lo, int b0,
+                                          S scale, bool scaled) {
+  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* p = base + q.base_amp + c;
+#pragma unroll
+  for (int k = 0; k < (1 << (NB - 3)); ++k)
+    p[(q.row0 + ((long long)reg_row<LAY>(w, k) << b0)) << lo] = scaled ? cscale(v[k], scale) : v[k];
+}
+
+// Swap layouts through the tile buffer Xs (2^NB x 32 amplitudes).
+template <class T, int NB, int FROM, int TO>
+__device__ __forceinline__ void reg_exchange(T (&v)[1 << (NB - 3)], T* Xs) {
+  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // the previous readers of Xs are done
+#pragma unroll
+  for (int k = 0; k < (1 << (NB - 3)); ++k) Xs[reg_row<FROM>(w, k) * 32 + c] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < (1 << (NB - 3)); ++k) v[k] = Xs[reg_row<TO>(w, k) * 32 + c];
+}
+
+// Stages on row bits 3..NB-1 (layout 1): the bits below are the warp index.
+template <class T, int NB, bool DIT, int MODE, class TW>
+__device__ __forceinline__ void reg_bfly_high(T (&v)[1 << (NB - 3)], int b0, int lo_fixed, int m, const TW& tw,
+                                              bool conj) {
+  const int w = threadIdx.x >> 5;
+  group_butterflies<T, NB - 3, DIT, MODE>(v, lo_fixed + (w << b0), b0 + 3, m, tw, conj);
+}
+
+// Stages on row bits 0..2 (layout 2): groups of 8 consecutive elements.
+template <class T, int NB, bool DIT, int MODE, class TW>
+__device__ __forceinline__ void reg_bfly_low(T (&v)[1 << (NB - 3)], int b0, int lo_fixed, int m, const TW& tw,
+                                             bool conj) {
+#pragma unroll
+  for (int s = 0; s < (1 << (NB - 6)); ++s) {
+    T g[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = v[8 * s + k];
+    group_butterflies<T, 3, DIT, MODE>(g, lo_fixed, b0, m, tw, conj);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[8 * s + k] = g[k];
+  }
+}
+
+// The layout a pass loads its tiles in: DIT passes start on the low bits.
+template <int OP>
+constexpr int reg_in_layout() { return OP == kSplitDit ? 2 : 1; }
+
+// One tile of a split pass in registers (the arithmetic of split_tile, postselect-early mode).
+template <class R, int OP, int NB>
+__device__ __forceinline__ void reg_tile(typename Cx<R>::T (&v)[1 << (NB - 3)], const SplitArgs& a, const TilePos& q,
+                                         typename Cx<R>::T* Xs, const Twiddle<typename Cx<R>::T>& tw) {
+  using T = typename Cx<R>::T;
+  T* dst = static_cast<T*>(a.dst);
+  if constexpr (OP == kSplitDif || OP == kSplitHad) {
+    constexpr int MODE = OP == kSplitHad ? 1 : 0;
+    reg_bfly_high<T, NB, false, MODE>(v, a.b0, q.lo_fixed, a.m, tw, false);
+    reg_exchange<T, NB, 1, 2>(v, Xs);
+    reg_bfly_low<T, NB, false, MODE>(v, a.b0, q.lo_fixed, a.m, tw, false);
+    if (OP == kSplitHad) reg_store<T, NB, 2>(v, dst, q, a.lo, a.b0, split_scale<R>(a), a.scaled != 0);
+    else reg_store<T, NB, 2>(v, dst, q, a.lo, a.b0, (R)1, false);
+  } else if constexpr (OP == kSplitDit) {
+    reg_bfly_low<T, NB, true, 0>(v, a.b0, q.lo_fixed, a.m, tw, true);
+    reg_exchange<T, NB, 2, 1>(v, Xs);
+    reg_bfly_high<T, NB, true, 0>(v, a.b0, q.lo_fixed, a.m, tw, true);
+    reg_store<T, NB, 1>(v, dst, q, a.lo, a.b0, (R)1, false);
+  } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
+    reg_bfly_high<T, NB, false, 0>(v, 0, 0, a.m, tw, false);
+    reg_exchange<T, NB, 1, 2>(v, Xs);
+    reg_bfly_low<T, NB, false, 0>(v, 0, 0, a.m, tw, false);
+    const R s = split_scale<R>(a);
+    const T* rot = static_cast<const T*>(a.rot);
+    T* cos_out = static_cast<T*>(a.dst_cos) + q.base_amp + (threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < (1 << (NB - 3)); ++k) {
+      const int y = bitrev_m(reg_row<2>(w, k) + (q.hi_fixed << NB), a.m);
+      const T r = rot[y];
+      const T x = cscale(v[k], s);
+      cos_out[(long long)y << a.lo] = cscale(x, r.x);
+      v[k] = cscale(x, r.y * s);
+    }
+    reg_bfly_low<T, NB, true, 0>(v, 0, 0, a.m, tw, true);
+    reg_exchange<T, NB, 2, 1>(v, Xs);
+    reg_bfly_high<T, NB, true, 0>(v, 0, 0, a.m, tw, true);
+    reg_store<T, NB, 1>(v, dst, q, a.lo, 0, (R)1, false);
+  }
+}
+
+// ------------------------------------------------------------- L2-staged group passes
+// The streaming split passes move the whole half through HBM once per pass. A group pass runs
+// every pass of a transform on one 256-byte column block of all 2^m rows of a half (a
+// "group": 2^m x 256 B, 2 MiB at m = 13 for complex64) before it moves on to the next: the
+// G CTAs of a cluster share the group's tiles in each pass, and a cluster barrier (release /
+// acquire at cluster scope, which orders the global stores of one pass before the loads of
+// the next) separates the passes. The intermediate results stay in L2 as long as the groups
+// in flight fit there, so the launch grid is bounded by an L2 budget, not only by occupancy;
+// then the clock block reads the anc = 0 half once and writes both halves once, and the
+// Hadamard layer reads and writes its half once.
+struct GroupArgs {
+  SplitArgs ph[3];   // the passes, in order (finished by split_finish)
+  long long groups;  // column blocks: 2^log_cb
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// One pass over the tiles of group ib: CTA `rank` of the cluster takes the group's tiles
+// rank, rank + G, ... Tiles of at least 64 rows are register-resident (with PF, the next
+// tile's loads are in flight during this one's work); smaller ones and the full-mode middle
+// pass are staged in shared memory, double-buffered as in k_split_pass.
+template <class R, int OP, bool FULL, int NB, bool PF>
+__device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, int rank, int G,
+                                            typename Cx<R>::T* Xb, typename Cx<R>::T* Y,
+                                            const Twiddle<typename Cx<R>::T>& tw) {
+  using T = typename Cx<R>::T;
+  constexpr int LW = SplitGeom<T>::LW;
+  constexpr int per = 16 / sizeof(T);
+  constexpr size_t tile_amps = (size_t)1 << (NB + LW);
+  const long long per_group = a.tiles >> a.log_cb;
+  const long long row_units = ((long long)1 << a.lo) / per;
+  long long u = rank;
+  if (u >= per_group) return;  // block-uniform
+  if constexpr (LW == 5 && NB >= 6 && !(OP == kSplitMid && FULL)) {
+    constexpr int E = 1 << (NB - 3), LAY = reg_in_layout<OP>();
+    T cur[E];
+    if constexpr (PF) {
+      T nxt[E];
+      reg_load<T, NB, LAY>(cur, static_cast<const T*>(a.src), tile_pos<NB, LW>(a, ib + (u << a.log_cb)), a.lo, a.b0);
+      for (; u < per_group; u += G) {
+        const long long un = u + G;
+        if (un < per_group)
+          reg_load<T, NB, LAY>(nxt, static_cast<const T*>(a.src), tile_pos<NB, LW>(a, ib + (un << a.log_cb)), a.lo,
+                               a.b0);
+        reg_tile<R, OP, NB>(cur, a, tile_pos<NB, LW>(a, ib + (u << a.log_cb)), Xb, tw);
+#pragma unroll
+        for (int k = 0; k < E; ++k) cur[k] = nxt[k];
+      }
+    } else {
+      for (; u < per_group; u += G) {
+        const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
+        reg_load<T, NB, LAY>(cur, static_cast<const T*>(a.src), q, a.lo, a.b0);
+        reg_tile<R, OP, NB>(cur, a, q, Xb, tw);
+      }
+    }
+    return;
+  }
+  {
+    const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
+    tile_issue<T, NB>(Xb, static_cast<const T*>(a.src) + q.base_amp, row_units, q.row0, a.b0);
+  }
+  split_cp_async_commit();
+  int buf = 0;
+  for (; u < per_group; u += G) {
+    const long long un = u + G;
+    if (un < per_group) {
+      const TilePos qn = tile_pos<NB, LW>(a, ib + (un << a.log_cb));
+      tile_issue<T, NB>(Xb + (buf ^ 1) * tile_amps, static_cast<const T*>(a.src) + qn.base_amp, row_units, qn.row0,
+                        a.b0);
+    }
+    split_cp_async_commit();
+    split_cp_async_wait1();
+    __syncthreads();  // the current tile has landed for every thread
+    const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
+    split_tile<R, OP, FULL, NB, false>(a, q, Xb + buf * tile_amps, Y, tw, a.m, row_units);
+    __syncthreads();  // this buffer is read out before it is refilled
+    buf ^= 1;
+  }
+}
+
+// KIND 0: the clock block (passes A, B, C of clock_block_split); KIND 1: the Hadamard layer
+// (high bits, then low bits with the final scale). NBH / NBL: tile bits of the high / low passes.
+template <class R, int KIND, bool FULL, int NBH, int NBL, bool PF>
+__global__ void __launch_bounds__(kSplitThreads, PF ? 2 : 3) k_group_pass(GroupArgs g) {
+  using T = typename Cx<R>::T;
+  constexpr int LW = SplitGeom<T>::LW;
+  constexpr size_t tile_amps = (size_t)1 << (NBH + LW);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  const int m = g.ph[0].m;
+  T* Xb = t0 + (KIND == 0 ? twiddle_entries(m) : 0);  // two tile buffers, then Y (full clock block)
+  T* Y = Xb + 2 * tile_amps;
+  if (KIND == 0) fill_twiddles<R>(t0, t1, m);  // first read after a barrier in group_phase
+  Twiddle<T> tw;
+  tw.t0 = t0;
+  tw.t1 = t1;
+  unsigned rank, G;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(G));
+  const long long cid = blockIdx.x / G, ncl = gridDim.x / G;
+  // every CTA of a cluster runs the same groups, so all of them reach every barrier
+  for (long long ib = cid; ib < g.groups; ib += ncl) {
+    if constexpr (KIND == 0) {
+      group_phase<R, kSplitDif, false, NBH, PF>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
+      cluster_barrier();
+      group_phase<R, kSplitMid, FULL, NBL, PF>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
+      cluster_barrier();
+      group_phase<R, kSplitDit, false, NBH, PF>(g.ph[2], ib, (int)rank, (int)G, Xb, Y, tw);
+    } else {
+      group_phase<R, kSplitHad, false, NBH, PF>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
+      cluster_barrier();
+      group_phase<R, kSplitHad, false, NBL, PF>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
+    }
+    // the next group touches other columns only: no barrier before its first pass
+  }
+}
+
+// Derived fields of a split pass over `outer` blocks (as launch_split sets them).
+template <class R>
+void split_finish(SplitArgs& a, int outer) {
+  using T = typename Cx<R>::T;
+  a.log_cb = a.lo - SplitGeom<T>::LW;
+  a.region = 1LL << (a.lo + a.m);
+  a.scale_f = (float)a.scale;
+  a.scaled = a.scale != 1.0;
+  a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
+}
+
+// CTAs per cluster and the L2 budget (MiB) for the groups in flight; HHL_GROUP_SHAPE="G,MiB"
+// overrides (tuning).
+inline void group_shape(int* G, int* budget_mib) {
+  *G = 8;
+  *budget_mib = 128;
+  if (const char* env = getenv("HHL_GROUP_SHAPE")) {
+    int g = 0, b = 0;
+    if (sscanf(env, "%d,%d", &g, &b) == 2 && (g == 1 || g == 2 || g == 4 || g == 8 || g == 16) && b >= 1 &&
+        b <= 4096) {
+      *G = g;
+      *budget_mib = b;
+    }
+  }
+}
+
+template <class R, int KIND, bool FULL, int NBH, int NBL, bool PF>
+hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
+  using T = typename Cx<R>::T;
+  constexpr int LW = SplitGeom<T>::LW;
+  const int m = g.ph[0].m;
+  const size_t tile = ((size_t)1 << (NBH + LW)) * sizeof(T);
+  const size_t smem = (KIND == 0 ? (size_t)twiddle_entries(m) * sizeof(T) : 0) + 2 * tile +
+                      ((KIND == 0 && FULL) ? ((size_t)1 << (NBL + LW)) * sizeof(T) : 0);
+  auto kern = k_group_pass<R, KIND, FULL, NBH, NBL, PF>;
+  int G = 8, budget = 128;
+  group_shape(&G, &budget);
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (G > 8) HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kSplitThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)G);
+  int max_clusters = 0;
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, (const void*)kern, &cfg));
+  if (max_clusters < 1) return fail(HHL_ERR_UNSUPPORTED, "group pass: no cluster fits");
+  const long long group_bytes = ((long long)outer << m) * kSplitSegBytes;
+  long long n_cl = std::min<long long>(max_clusters, std::max<long long>(1, ((long long)budget << 20) / group_bytes));
+  n_cl = std::min<long long>(n_cl, g.groups);
+  cfg.gridDim = dim3((unsigned)(n_cl * G));
+  if (getenv("HHL_GROUP_VERBOSE") != nullptr)
+    fprintf(stderr, "%s: m=%d G=%d clusters=%lld (max %d) groups=%lld smem=%zu\n", name, m, G, n_cl, max_clusters,
+            g.groups, smem);
+  GroupArgs ga = g;
+  void* args[1] = {&ga};
+  HHL_PROF_BEGIN(st);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (g_prof_on.load(std::memory_order_relaxed)) prof_end(name);
+    return cuda_fail(e, name);
+  }
+  HHL_LAUNCH_CHECK(name);
+  return HHL_OK;
+}
+
+template <class R, int KIND, bool FULL, bool PF>
+hhl_status launch_group_pf(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
+  switch (g.ph[0].m) {
+    case 8: return launch_group_nb<R, KIND, FULL, 4, 4, PF>(g, outer, st, name);
+    case 9: return launch_group_nb<R, KIND, FULL, 5, 4, PF>(g, outer, st, name);
+    case 10: return launch_group_nb<R, KIND, FULL, 5, 5, PF>(g, outer, st, name);
+    case 11: return launch_group_nb<R, KIND, FULL, 6, 5, PF>(g, outer, st, name);
+    case 12: return launch_group_nb<R, KIND, FULL, 6, 6, PF>(g, outer, st, name);
+    case 13: return launch_group_nb<R, KIND, FULL, 7, 6, PF>(g, outer, st, name);
+    case 14: return launch_group_nb<R, KIND, FULL, 7, 7, PF>(g, outer, st, name);
+    default: return fail(HHL_ERR_UNSUPPORTED, "group pass: register bits out of range");
+  }
+}
+
+template <class R, int KIND, bool FULL>
+hhl_status launch_group(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
+  const char* env = getenv("HHL_GROUP_PF");
+  if (env != nullptr && atoi(env) == 0) return launch_group_pf<R, KIND, FULL, false>(g, outer, st, name);
+  return launch_group_pf<R, KIND, FULL, true>(g, outer, st, name);
 }
 
 // ------------------------------------------------------------- one-pass clustered clock block
@@ -1379,14 +1716,84 @@ hhl_status hadamard_split(void* base, int lo, int m, int outer, cudaStream_t st)
   return launch_split<R, kSplitHad, false>(a, outer, st, "k_hadamard_pass");
 }
 
+// The group passes serve complex64 states on the split path when HHL_GROUP=1.
+inline bool group_applies() {
+  const char* env = getenv("HHL_GROUP");
+  return env != nullptr && atoi(env) != 0;
+}
+
+// The three passes of clock_block_split as one L2-staged group launch.
+template <bool FULL>
+hhl_status clock_block_group(const Plan& p, void* state, cudaStream_t st) {
+  using T = typename Cx<float>::T;
+  const int m = p.n_c, m_lo = m / 2, m_hi = m - m_lo;
+  T* S0 = static_cast<T*>(state);
+  T* S1 = S0 + p.R * p.N;
+  GroupArgs g = {};
+  SplitArgs a = {};
+  a.lo = p.n_s;
+  a.m = m;
+  a.rot = p.d_rot;
+  a.scale = 1.0;
+  a.src = S0;  // A: inverse-QFT stages on the high bits, anc = 0 -> anc = 1
+  a.dst = S1;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  g.ph[0] = a;
+  split_finish<float>(g.ph[0], 1);
+  a.src = S1;  // B: low-bit stages, rotation, low-bit QFT stages
+  a.dst = S1;
+  a.dst_cos = S0;
+  a.b0 = 0;
+  a.nb = m_lo;
+  a.scale = 1.0 / sqrt((double)p.R);
+  g.ph[1] = a;
+  split_finish<float>(g.ph[1], 1);
+  a.src = FULL ? S0 : S1;  // C: QFT stages on the high bits, in place (both halves when full)
+  a.dst = a.src;
+  a.dst_cos = nullptr;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  a.scale = 1.0;
+  g.ph[2] = a;
+  split_finish<float>(g.ph[2], FULL ? 2 : 1);
+  g.groups = 1LL << g.ph[0].log_cb;
+  return launch_group<float, 0, FULL>(g, FULL ? 2 : 1, st, "k_clock_group");
+}
+
+// The two passes of hadamard_split as one L2-staged group launch.
+inline hhl_status hadamard_group(void* base, int lo, int m, int outer, cudaStream_t st) {
+  const int m_lo = m / 2, m_hi = m - m_lo;
+  GroupArgs g = {};
+  SplitArgs a = {};
+  a.src = base;
+  a.dst = base;
+  a.lo = lo;
+  a.m = m;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  a.scale = 1.0;
+  g.ph[0] = a;
+  split_finish<float>(g.ph[0], outer);
+  a.b0 = 0;
+  a.nb = m_lo;
+  a.scale = 1.0 / sqrt((double)(1LL << m));
+  g.ph[1] = a;
+  split_finish<float>(g.ph[1], outer);
+  g.groups = 1LL << g.ph[0].log_cb;
+  return launch_group<float, 1, false>(g, outer, st, "k_hadamard_group");
+}
+
 }  // namespace
 
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
   const long long half = p.R * p.N;
   if (p.prec == HHL_PREC_C64) {
     if (clock_cluster_applies<float>(p)) return clock_block_cluster<float>(p, state, st);
-    if (split_applies<float>(p.n_s, p.n_c, half))
+    if (split_applies<float>(p.n_s, p.n_c, half)) {
+      if (group_applies()) return p.full ? clock_block_group<true>(p, state, st) : clock_block_group<false>(p, state, st);
       return p.full ? clock_block_split<float, true>(p, state, st) : clock_block_split<float, false>(p, state, st);
+    }
     return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
   }
   if (clock_cluster_applies<double>(p)) return clock_block_cluster<double>(p, state, st);
@@ -1404,8 +1811,10 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
   if (p.prec == HHL_PREC_C64) {
     if (hadamard_cluster_applies<float>(p.n_s, p.n_c, half_amps))
       return hadamard_cluster<float>(base, p.n_s, p.n_c, outer, st);
-    return split_applies<float>(p.n_s, p.n_c, half_amps) ? hadamard_split<float>(base, p.n_s, p.n_c, outer, st)
-                                                         : register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
+    if (!split_applies<float>(p.n_s, p.n_c, half_amps))
+      return register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
+    return group_applies() ? hadamard_group(base, p.n_s, p.n_c, outer, st)
+                           : hadamard_split<float>(base, p.n_s, p.n_c, outer, st);
   }
   if (hadamard_cluster_applies<double>(p.n_s, p.n_c, half_amps))
     return hadamard_cluster<double>(base, p.n_s, p.n_c, outer, st);
