@@ -1166,7 +1166,8 @@ __global__ void __launch_bounds__(kSplitThreads, PF ? 2 : 3) k_group_pass(GroupA
   const int m = g.ph[0].m;
   T* Xb = t0 + (KIND == 0 ? twiddle_entries(m) : 0);  // two tile buffers, then Y (full clock block)
   T* Y = Xb + 2 * tile_amps;
-  if (KIND == 0) fill_twiddles<R>(t0, t1, m);  // first read after a barrier in group_phase
+  if (KIND == 0) fill_twiddles<R>(t0, t1, m);
+  __syncthreads();  // the table is complete before the first butterfly
   Twiddle<T> tw;
   tw.t0 = t0;
   tw.t1 = t1;

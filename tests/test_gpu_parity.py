@@ -577,7 +577,7 @@ def test_cluster_clock_block_parity(hhl, monkeypatch, prec, flow, n_s, n_c):
 
 
 @pytest.mark.parametrize("prec,group", [("c128", None), ("c64", None), ("c64", "8,64"), ("c64", "2,1"),
-                                        ("c64", "16,1"), ("c64", "4,1,nopf")])
+                                        ("c64", "16,1"), ("c64", "4,1,nopf"), ("c64", "1,1")])
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("flow,n_s,n_c", [("couette", 5, 8), ("poiseuille", 6, 9), ("couette", 7, 11),
                                           ("poiseuille", 6, 12), ("couette", 5, 13)])
