@@ -481,8 +481,9 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_measure_sums": ("byte", 2.0 * half),
         # grouped Trotter passes change different row counts: the plan's total over its passes
         "k_trotter_pass": ("byte", tb_launch),
-        # the saved window edges are an overhead of the in-place passes, not algorithmic traffic
-        "k_trotter_edges": ("byte", 0.0),
+        # the halos saved at the boundaries between warps' runs are an overhead of the
+        # in-place passes, not algorithmic traffic
+        "k_trotter_bounds": ("byte", 0.0),
     }
 
 

@@ -12,10 +12,12 @@
 // own registers and the remaining O pair crosses to the next lane by a warp shuffle. The
 // window has a 16-amplitude halo on each side (lanes 0 and 31), and its 480-amplitude
 // interior (lanes 1..30) is written back in place.
-// The halos are the edges of the neighbouring interiors, which the same pass overwrites,
-// so a small kernel first saves the 16 leading and 16 trailing amplitudes of every interior
-// into a side buffer and the pass reads its halos from there: each pass moves the rows
-// through HBM once (plus about 7% for the edges), in place.
+// The halos are the edges of the neighbouring interiors, which the same pass overwrites in
+// place. Each warp owns a contiguous run of windows and walks it in order, so the left halo
+// of a window is the original right end of the interior the warp loaded just before (carried
+// in shared memory) and its right halo is the start of the next interior, which no one has
+// written yet; only the halos across the boundaries between two warps' runs are saved before
+// the pass, by a small kernel, into a side buffer. Each pass moves its rows through HBM once.
 //
 // A 16-amplitude halo is exact for up to 17 layers when the first layer is an E layer: the
 // E pairs never cross the window edge, and each later layer moves the wrong values in from
@@ -29,10 +31,12 @@
 // Poiseuille case (r_k = 1 for k < 8) 13 single-bit passes over half the rows each become 5
 // passes, 3 of them over half the rows.
 //
-// Warps are persistent: each walks windows with a stride of the grid's warp count, and the
-// 16-byte copies of its next window (interior from the state, halos from the side buffer) go
-// into a second staging buffer with cp.async while it computes the current one.
+// Warps are persistent: the windows of the pass (rows with a nonzero pattern only, so that
+// every window is work) are split into one contiguous run per warp, and the 16-byte copies
+// of a warp's next window go into a second staging buffer with cp.async while it computes
+// the current one.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -150,36 +154,50 @@ __device__ __forceinline__ void rot_apply(T& a, T& b, R c, R s) {
 }
 
 // Rows of a pass: single_k >= 0 enumerates the 2^(n_c - 1) rows with clock bit single_k set
-// (pattern 1); otherwise every row i, with pattern (i >> kb) & (2^gbits - 1) (rows whose
-// pattern is 0 are not touched).
+// (pattern 1); otherwise the rows whose pattern, clock bits [kb, kb + gbits), is nonzero:
+// pass row i = (hi, pattern - 1, lo) in mixed radix (.., 2^gbits - 1, 2^kb).
 __device__ __forceinline__ void pass_row(int64_t i, int single_k, int kb, int gbits, int64_t* row, int* pattern) {
   if (single_k >= 0) {
     *row = row_with_bit_t(i, single_k);
     *pattern = 1;
   } else {
-    *row = i;
-    *pattern = (int)((i >> kb) & ((1 << gbits) - 1));
+    const int64_t M = (1LL << gbits) - 1;
+    const int64_t lo = i & ((1LL << kb) - 1), t = i >> kb;
+    const int64_t hi = t / M;
+    const int pat = (int)(1 + t - hi * M);
+    *row = lo | ((int64_t)pat << kb) | (hi << (kb + gbits));
+    *pattern = pat;
   }
 }
 
-// side[(i * segs + s) * 32 + q]: q < 16 the first 16 interior amplitudes of segment s of
-// pass row i, q >= 16 its last 16 (zero beyond the row end).
+// The run of warp gw < nruns (nruns <= windows, so no run is empty): windows
+// [run_start(gw), run_start(gw + 1)) of the pass, window v = i * segs + s (pass row i,
+// segment s).
+__device__ __forceinline__ int run_start(int gw, int windows, int nruns) {
+  return (int)((int64_t)gw * windows / nruns);
+}
+
+// side[gw * 32 + q] for the boundary between the runs of warps gw - 1 and gw (window
+// v = run_start(gw) and v - 1, when both lie in one row): q < 16 the first 16 interior
+// amplitudes of window v (the right halo of v - 1), q >= 16 the last 16 of window v - 1 (the
+// left halo of v); zero beyond the row end.
 template <class R>
-__global__ void k_trotter_edges(const typename Cx<R>::T* __restrict__ half, typename Cx<R>::T* __restrict__ side,
-                                int n_s, int segs, int rows, int single_k, int kb, int gbits) {
+__global__ void k_trotter_bounds(const typename Cx<R>::T* __restrict__ half, typename Cx<R>::T* __restrict__ side,
+                                 int n_s, int segs, int windows, int nruns, int single_k, int kb, int gbits) {
   const int64_t N = 1LL << n_s;
-  const unsigned total = (unsigned)rows * (unsigned)segs * 32u;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const unsigned rs = e >> 5;
-    const int q = (int)(e & 31);
-    const unsigned i = rs / (unsigned)segs, s = rs - i * (unsigned)segs;
-    int64_t row;
-    int pattern;
-    pass_row(i, single_k, kb, gbits, &row, &pattern);
-    if (pattern == 0) continue;
-    const int64_t g = (int64_t)s * kInterior + (q < 16 ? q : kInterior - 32 + q);
-    side[e] = g < N ? half[row * N + g] : mk<R>((R)0, (R)0);
-  }
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nruns * 32) return;
+  const int gw = e >> 5, q = e & 31;
+  if (gw == 0) return;
+  const int v = run_start(gw, windows, nruns);
+  const int i = v / segs;
+  const int s = v - i * segs;
+  if (s == 0) return;  // a row boundary: the halos are zero
+  int64_t row;
+  int pattern;
+  pass_row(i, single_k, kb, gbits, &row, &pattern);
+  const int64_t g = q < 16 ? (int64_t)s * kInterior + q : (int64_t)s * kInterior - 32 + q;
+  side[e] = g < N ? half[row * N + g] : mk<R>((R)0, (R)0);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -189,33 +207,28 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// One warp window: pass row i, segment s.
+// One warp window: pass row i, segment s; first / last: the first / last window of the
+// warp's run (its left / right halo then comes from the side buffer, unless at a row end).
 struct Window {
   int i, s;
   int64_t row;
   int pattern;
   bool full;  // the 480-amplitude interior lies inside the row
+  bool first, last;
 };
-
-__device__ __forceinline__ Window window_at(int i, int s, int64_t N, int single_k, int kb, int gbits) {
-  Window d;
-  d.i = i;
-  d.s = s;
-  pass_row(i, single_k, kb, gbits, &d.row, &d.pattern);
-  d.full = (int64_t)s * kInterior + kInterior <= N;
-  return d;
-}
 
 // Staging buffer of a warp: 32 x kLaneAmps amplitudes as 16-byte chunks, window chunk c
 // stored at position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both the coalesced
 // copy (lane t <-> chunk q * 32 + t) and the per-lane gather (lane t <-> its CPL consecutive
 // chunks) spread over the banks. Lane 0's chunks hold the left halo, lane 31's the right.
+// The left halo of a window inside a run is not copied here: the previous iteration puts the
+// carried amplitudes there (carry_copy).
 template <class T>
-__device__ __forceinline__ void stage_issue(uint4* stage, const Window& d, const T* half, const T* side, int segs,
-                                            int64_t N, int lane) {
+__device__ __forceinline__ void stage_issue(uint4* stage, const Window& d, const T* half, const T* side, int gw,
+                                            int segs, int64_t N, int lane) {
   constexpr int per = 16 / sizeof(T);
   constexpr int CPL = kLaneAmps / per;
-  if (d.pattern == 0 || !d.full) return;
+  if (!d.full) return;
   const uint4* src = reinterpret_cast<const uint4*>(half + d.row * N + (int64_t)d.s * kInterior);
   constexpr int chunks = kInterior / per;  // 30 * CPL
 #pragma unroll
@@ -226,28 +239,51 @@ __device__ __forceinline__ void stage_issue(uint4* stage, const Window& d, const
       cp_async16(&stage[wc ^ ((wc / CPL) & 7)], src + c);
     }
   }
-  if (lane == 0 || lane == 31) {
-    const int ns = lane == 0 ? d.s - 1 : d.s + 1;
-    const int off = lane == 0 ? 16 : 0;  // the neighbour's last 16 / first 16
-    const int sw = lane & 7;
-    if (ns >= 0 && ns < segs) {
-      const uint4* hs = reinterpret_cast<const uint4*>(side + ((int64_t)d.i * segs + ns) * 32 + off);
+  const int sw = lane & 7;
+  if (lane == 0) {
+    if (d.s == 0) {
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) cp_async16(&stage[(lane * CPL + q) ^ sw], hs + q);
+      for (int q = 0; q < CPL; ++q) stage[q] = make_uint4(0u, 0u, 0u, 0u);
+    } else if (d.first) {
+      const uint4* hs = reinterpret_cast<const uint4*>(side + (int64_t)gw * 32 + 16);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) cp_async16(&stage[q], hs + q);
+    }
+  } else if (lane == 31) {
+    if (d.s == segs - 1) {
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) stage[(31 * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+    } else if (d.last) {
+      const uint4* hs = reinterpret_cast<const uint4*>(side + (int64_t)(gw + 1) * 32);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) cp_async16(&stage[(31 * CPL + q) ^ sw], hs + q);
     } else {
+      // the start of the next interior, unwritten until this warp gets there
+      const int64_t a0 = (int64_t)(d.s + 1) * kInterior;
+      const uint4* hs = reinterpret_cast<const uint4*>(half + d.row * N + a0);
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) stage[(lane * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+      for (int q = 0; q < CPL; ++q) {
+        if (a0 + (int64_t)(q + 1) * per <= N) cp_async16(&stage[(31 * CPL + q) ^ sw], hs + q);
+        else stage[(31 * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
   }
 }
 
-// Persistent warps: each warp walks the windows w = warp, warp + warps, ...; the copies of
-// its next window go to the second staging buffer (cp.async) while it computes the current.
+// The left halo of the next window of the run (same row): the original last 16 interior
+// amplitudes of the current, full window (lane 30's chunks) into lane 0's chunks of the
+// next staging buffer.
+__device__ __forceinline__ void carry_copy(uint4* next_stage, const uint4* stage, int lane, int cpl) {
+  if (lane < cpl) next_stage[lane] = stage[(30 * cpl + lane) ^ 6];
+}
+
+// Persistent warps: each warp walks its run of windows in order; the copies of its next
+// window go to the second staging buffer (cp.async) while it computes the current.
 template <class R>
 __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
                                                               const typename Cx<R>::T* __restrict__ side, int n_s,
-                                                              int segs, int rows, int single_k, int kb, int gbits,
-                                                              const LayerList* __restrict__ lists) {
+                                                              int segs, int windows, int nruns, int single_k,
+                                                              int kb, int gbits, const LayerList* __restrict__ lists) {
   using T = typename Cx<R>::T;
   constexpr int per = 16 / sizeof(T);  // amplitudes per 16-byte unit
   constexpr int CPL = kLaneAmps / per;
@@ -257,33 +293,40 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
   R* rot_w = reinterpret_cast<R*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)(kTrotThreads / 32) * 2 * 32 * CPL) +
              (size_t)wid * 4 * 32;
   const int64_t N = 1LL << n_s;
-  // windows w = warp, warp + nwarps, ... as (row i, segment s), stepped without division
-  const int nwarps = (int)gridDim.x * (kTrotThreads / 32);
-  const int w0 = (int)blockIdx.x * (kTrotThreads / 32) + wid;
-  const int step_i = nwarps / segs, step_s = nwarps - step_i * segs;
-  int i = w0 / segs, sg = w0 - (w0 / segs) * segs;
-  if (i >= rows) return;  // warp-uniform
-  Window cur = window_at(i, sg, N, single_k, kb, gbits);
-  stage_issue<T>(stage_w, cur, half, side, segs, N, lane);
+  const int gw = (int)blockIdx.x * (kTrotThreads / 32) + wid;
+  if (gw >= nruns) return;  // warp-uniform
+  const int v0 = run_start(gw, windows, nruns), v1 = run_start(gw + 1, windows, nruns);
+  Window cur;
+  cur.i = v0 / segs;
+  cur.s = v0 - cur.i * segs;
+  pass_row(cur.i, single_k, kb, gbits, &cur.row, &cur.pattern);
+  cur.full = (int64_t)cur.s * kInterior + kInterior <= N;
+  cur.first = true;
+  cur.last = v0 + 1 == v1;
+  stage_issue<T>(stage_w, cur, half, side, gw, segs, N, lane);
   cp_async_commit();
   int buf = 0;
-  while (i < rows) {
-    sg += step_s;
-    i += step_i;
-    if (sg >= segs) {
-      sg -= segs;
-      ++i;
-    }
-    Window nxt;
-    if (i < rows) {
-      nxt = window_at(i, sg, N, single_k, kb, gbits);
-      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, nxt, half, side, segs, N, lane);
+  for (int v = v0; v < v1; ++v) {
+    Window nxt = cur;
+    const bool more = v + 1 < v1;
+    if (more) {
+      nxt.first = false;
+      nxt.last = v + 2 == v1;
+      if (++nxt.s == segs) {
+        nxt.s = 0;
+        ++nxt.i;
+        pass_row(nxt.i, single_k, kb, gbits, &nxt.row, &nxt.pattern);
+      }
+      nxt.full = (int64_t)nxt.s * kInterior + kInterior <= N;
+      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, nxt, half, side, gw, segs, N, lane);
     }
     cp_async_commit();
     cp_async_wait1();  // the current window's copies have landed
     __syncwarp();
-    if (cur.pattern != 0) {
+    {
       uint4* stage = stage_w + buf * 32 * CPL;
+      // a full window followed by the next segment of its row: carry the left halo over
+      if (more && nxt.s > 0) carry_copy(stage_w + (buf ^ 1) * 32 * CPL, stage, lane, CPL);
       const LayerList* L = lists + cur.pattern;
       const int n_layers = L->n, first_o = L->first_o;
       if (lane < n_layers) {
@@ -304,12 +347,19 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
         if (lane > 0 && lane < 31) {
 #pragma unroll
           for (int q = 0; q < kLaneAmps; ++q) x[q] = lane0 + q < N ? row[lane0 + q] : mk<R>((R)0, (R)0);
-        } else {
-          const int ns = lane == 0 ? cur.s - 1 : cur.s + 1;
-          const int off = lane == 0 ? 16 : 0;
+        } else if (lane == 0 && cur.s > 0) {
+          // the left halo: from the side buffer at the start of the run, else carried
+          if (cur.first) {
 #pragma unroll
-          for (int q = 0; q < kLaneAmps; ++q)
-            x[q] = (ns >= 0 && ns < segs) ? side[((int64_t)cur.i * segs + ns) * 32 + off + q] : mk<R>((R)0, (R)0);
+            for (int q = 0; q < kLaneAmps; ++q) x[q] = side[(int64_t)gw * 32 + 16 + q];
+          } else {
+            uint4* d = reinterpret_cast<uint4*>(x);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) d[q] = stage[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < kLaneAmps; ++q) x[q] = mk<R>((R)0, (R)0);  // beyond the row ends
         }
       }
       __syncwarp();
@@ -420,22 +470,27 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
   HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trotter_pass<R>, kTrotThreads, smem));
   if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass does not fit an SM");
   for (const TrotPassDesc& d : p.trot_pass[adjoint ? 1 : 0]) {
-    const int64_t rows = d.single_k >= 0 ? p.R / 2 : p.R;
-    const int64_t warps = rows * segs;
-    const int64_t grid = (warps + kTrotThreads / 32 - 1) / (kTrotThreads / 32);
-    if (warps > 0x7fffffffLL - 4 * (int64_t)occ * sms * (kTrotThreads / 32))
-      return fail(HHL_ERR_UNSUPPORTED, "Trotter pass has too many windows");
-    const int64_t edge_total = rows * segs * 32;
-    int eg = (int)((edge_total + 255) / 256);
-    if (eg > 152 * 16) eg = 152 * 16;
+    // pass rows: those with clock bit single_k set, or with a nonzero pattern of the group
+    const int64_t rows = d.single_k >= 0 ? p.R / 2 : p.R - (p.R >> d.gbits);
+    const int64_t windows = rows * segs;
+    if (windows < 1) continue;
+    if (windows > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass has too many windows");
+    const int64_t max_warps = (int64_t)occ * sms * (kTrotThreads / 32);
+    int64_t runs = std::min<int64_t>(windows, max_warps);  // <= R * segs: the side buffer holds them
+    if (const char* env = getenv("HHL_TROTTER_RUNS")) {    // testing override: fewer, longer runs
+      const long long cap = atoll(env);
+      if (cap >= 1) runs = std::min<int64_t>(runs, cap);
+    }
+    const int nruns = (int)runs;
+    const unsigned pgrid = (unsigned)((nruns + kTrotThreads / 32 - 1) / (kTrotThreads / 32));
     HHL_PROF_BEGIN(st);
-    k_trotter_edges<R><<<eg, 256, 0, st>>>((const T*)half, side, p.n_s, (int)segs, (int)rows, d.single_k, d.kb,
-                                           d.gbits);
-    HHL_LAUNCH_CHECK("k_trotter_edges");
-    const unsigned pgrid = (unsigned)std::min<int64_t>(grid, (int64_t)occ * sms);
+    k_trotter_bounds<R><<<(unsigned)((nruns * 32 + 255) / 256), 256, 0, st>>>((const T*)half, side, p.n_s, (int)segs,
+                                                                                (int)windows, nruns, d.single_k, d.kb,
+                                                                                d.gbits);
+    HHL_LAUNCH_CHECK("k_trotter_bounds");
     HHL_PROF_BEGIN(st);
-    k_trotter_pass<R><<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)rows, d.single_k,
-                                                         d.kb, d.gbits, lists + d.list_off);
+    k_trotter_pass<R><<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)windows, nruns,
+                                                         d.single_k, d.kb, d.gbits, lists + d.list_off);
     HHL_LAUNCH_CHECK("k_trotter_pass");
   }
   return HHL_OK;
