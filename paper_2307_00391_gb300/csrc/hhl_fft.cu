@@ -958,119 +958,6 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   }
 }
 
-// ------------------------------------------------------------- register-resident tiles
-// A tile of 2^NB rows x 32 columns (NB >= 6) held in registers, 2^(NB-3) amplitudes per
-// thread, in one of two layouts; in both, the 32 lanes of a warp cover the 32 columns of a
-// row (256 contiguous bytes: coalesced global access, conflict-free shared memory):
-//   layout 1: element k of warp w is row w + 8 k     (row bits 3.. in registers),
-//   layout 2: element k of warp w is row 8 (w + 8 (k >> 3)) + (k & 7)   (row bits 0..2).
-// A transform over the tile's bits runs the butterflies of one layout, swaps layouts through
-// shared memory once, and runs the rest: one shared-memory round trip per amplitude instead
-// of the staged tile's three (copy in, two radix passes, copy out).
-template <int LAY>
-__device__ __forceinline__ int reg_row(int w, int k) {
-  return LAY == 1 ? w + 8 * k : 8 * (w + 8 * (k >> 3)) + (k & 7);
-}
-
-template <class T, int NB, int LAY>
-__device__ __forceinline__ void reg_load(T (&v)[1 << (NB - 3)], const T* base, const TilePos& q, int lo, int b0) {
-  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const T* p = base + q.base_amp + c;
-#pragma unroll
-  for (int k = 0; k < (1 << (NB - 3)); ++k)
-    v[k] = __ldcg(p + ((q.row0 + ((long long)reg_row<LAY>(w, k) << b0)) << lo));
-}
-
-template <class T, int NB, int LAY, class S>
-__device__ __forceinline__ void reg_store(const T (&v)[1 << (NB - 3)], T* base, const TilePos& q, int lo, int b0,
-                                          S scale, bool scaled) {
-  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
-  T* p = base + q.base_amp + c;
-#pragma unroll
-  for (int k = 0; k < (1 << (NB - 3)); ++k)
-    p[(q.row0 + ((long long)reg_row<LAY>(w, k) << b0)) << lo] = scaled ? cscale(v[k], scale) : v[k];
-}
-
-// Swap layouts through the tile buffer Xs (2^NB x 32 amplitudes).
-template <class T, int NB, int FROM, int TO>
-__device__ __forceinline__ void reg_exchange(T (&v)[1 << (NB - 3)], T* Xs) {
-  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();  // the previous readers of Xs are done
-#pragma unroll
-  for (int k = 0; k < (1 << (NB - 3)); ++k) Xs[reg_row<FROM>(w, k) * 32 + c] = v[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < (1 << (NB - 3)); ++k) v[k] = Xs[reg_row<TO>(w, k) * 32 + c];
-}
-
-// Stages on row bits 3..NB-1 (layout 1): the bits below are the warp index.
-template <class T, int NB, bool DIT, int MODE, class TW>
-__device__ __forceinline__ void reg_bfly_high(T (&v)[1 << (NB - 3)], int b0, int lo_fixed, int m, const TW& tw,
-                                              bool conj) {
-  const int w = threadIdx.x >> 5;
-  group_butterflies<T, NB - 3, DIT, MODE>(v, lo_fixed + (w << b0), b0 + 3, m, tw, conj);
-}
-
-// Stages on row bits 0..2 (layout 2): groups of 8 consecutive elements.
-template <class T, int NB, bool DIT, int MODE, class TW>
-__device__ __forceinline__ void reg_bfly_low(T (&v)[1 << (NB - 3)], int b0, int lo_fixed, int m, const TW& tw,
-                                             bool conj) {
-#pragma unroll
-  for (int s = 0; s < (1 << (NB - 6)); ++s) {
-    T g[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) g[k] = v[8 * s + k];
-    group_butterflies<T, 3, DIT, MODE>(g, lo_fixed, b0, m, tw, conj);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[8 * s + k] = g[k];
-  }
-}
-
-// The layout a pass loads its tiles in: DIT passes start on the low bits.
-template <int OP>
-constexpr int reg_in_layout() { return OP == kSplitDit ? 2 : 1; }
-
-// One tile of a split pass in registers (the arithmetic of split_tile, postselect-early mode).
-template <class R, int OP, int NB>
-__device__ __forceinline__ void reg_tile(typename Cx<R>::T (&v)[1 << (NB - 3)], const SplitArgs& a, const TilePos& q,
-                                         typename Cx<R>::T* Xs, const Twiddle<typename Cx<R>::T>& tw) {
-  using T = typename Cx<R>::T;
-  T* dst = static_cast<T*>(a.dst);
-  if constexpr (OP == kSplitDif || OP == kSplitHad) {
-    constexpr int MODE = OP == kSplitHad ? 1 : 0;
-    reg_bfly_high<T, NB, false, MODE>(v, a.b0, q.lo_fixed, a.m, tw, false);
-    reg_exchange<T, NB, 1, 2>(v, Xs);
-    reg_bfly_low<T, NB, false, MODE>(v, a.b0, q.lo_fixed, a.m, tw, false);
-    if (OP == kSplitHad) reg_store<T, NB, 2>(v, dst, q, a.lo, a.b0, split_scale<R>(a), a.scaled != 0);
-    else reg_store<T, NB, 2>(v, dst, q, a.lo, a.b0, (R)1, false);
-  } else if constexpr (OP == kSplitDit) {
-    reg_bfly_low<T, NB, true, 0>(v, a.b0, q.lo_fixed, a.m, tw, true);
-    reg_exchange<T, NB, 2, 1>(v, Xs);
-    reg_bfly_high<T, NB, true, 0>(v, a.b0, q.lo_fixed, a.m, tw, true);
-    reg_store<T, NB, 1>(v, dst, q, a.lo, a.b0, (R)1, false);
-  } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
-    reg_bfly_high<T, NB, false, 0>(v, 0, 0, a.m, tw, false);
-    reg_exchange<T, NB, 1, 2>(v, Xs);
-    reg_bfly_low<T, NB, false, 0>(v, 0, 0, a.m, tw, false);
-    const R s = split_scale<R>(a);
-    const T* rot = static_cast<const T*>(a.rot);
-    T* cos_out = static_cast<T*>(a.dst_cos) + q.base_amp + (threadIdx.x & 31);
-    const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < (1 << (NB - 3)); ++k) {
-      const int y = bitrev_m(reg_row<2>(w, k) + (q.hi_fixed << NB), a.m);
-      const T r = rot[y];
-      const T x = cscale(v[k], s);
-      cos_out[(long long)y << a.lo] = cscale(x, r.x);
-      v[k] = cscale(x, r.y * s);
-    }
-    reg_bfly_low<T, NB, true, 0>(v, 0, 0, a.m, tw, true);
-    reg_exchange<T, NB, 2, 1>(v, Xs);
-    reg_bfly_high<T, NB, true, 0>(v, 0, 0, a.m, tw, true);
-    reg_store<T, NB, 1>(v, dst, q, a.lo, 0, (R)1, false);
-  }
-}
-
 // ------------------------------------------------------------- L2-staged group passes
 // The streaming split passes move the whole half through HBM once per pass. A group pass runs
 // every pass of a transform on one 256-byte column block of all 2^m rows of a half (a
@@ -1091,10 +978,8 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // One pass over the tiles of group ib: CTA `rank` of the cluster takes the group's tiles
-// rank, rank + G, ... Tiles of at least 64 rows are register-resident (with PF, the next
-// tile's loads are in flight during this one's work); smaller ones and the full-mode middle
-// pass are staged in shared memory, double-buffered as in k_split_pass.
-template <class R, int OP, bool FULL, int NB, bool PF>
+// rank, rank + G, ... (double-buffered as in k_split_pass).
+template <class R, int OP, bool FULL, int NB>
 __device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, int rank, int G,
                                             typename Cx<R>::T* Xb, typename Cx<R>::T* Y,
                                             const Twiddle<typename Cx<R>::T>& tw) {
@@ -1106,30 +991,6 @@ __device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, in
   const long long row_units = ((long long)1 << a.lo) / per;
   long long u = rank;
   if (u >= per_group) return;  // block-uniform
-  if constexpr (LW == 5 && NB >= 6 && !(OP == kSplitMid && FULL)) {
-    constexpr int E = 1 << (NB - 3), LAY = reg_in_layout<OP>();
-    T cur[E];
-    if constexpr (PF) {
-      T nxt[E];
-      reg_load<T, NB, LAY>(cur, static_cast<const T*>(a.src), tile_pos<NB, LW>(a, ib + (u << a.log_cb)), a.lo, a.b0);
-      for (; u < per_group; u += G) {
-        const long long un = u + G;
-        if (un < per_group)
-          reg_load<T, NB, LAY>(nxt, static_cast<const T*>(a.src), tile_pos<NB, LW>(a, ib + (un << a.log_cb)), a.lo,
-                               a.b0);
-        reg_tile<R, OP, NB>(cur, a, tile_pos<NB, LW>(a, ib + (u << a.log_cb)), Xb, tw);
-#pragma unroll
-        for (int k = 0; k < E; ++k) cur[k] = nxt[k];
-      }
-    } else {
-      for (; u < per_group; u += G) {
-        const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
-        reg_load<T, NB, LAY>(cur, static_cast<const T*>(a.src), q, a.lo, a.b0);
-        reg_tile<R, OP, NB>(cur, a, q, Xb, tw);
-      }
-    }
-    return;
-  }
   {
     const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
     tile_issue<T, NB>(Xb, static_cast<const T*>(a.src) + q.base_amp, row_units, q.row0, a.b0);
@@ -1155,8 +1016,8 @@ __device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, in
 
 // KIND 0: the clock block (passes A, B, C of clock_block_split); KIND 1: the Hadamard layer
 // (high bits, then low bits with the final scale). NBH / NBL: tile bits of the high / low passes.
-template <class R, int KIND, bool FULL, int NBH, int NBL, bool PF>
-__global__ void __launch_bounds__(kSplitThreads, PF ? 2 : 3) k_group_pass(GroupArgs g) {
+template <class R, int KIND, bool FULL, int NBH, int NBL>
+__global__ void __launch_bounds__(kSplitThreads, 3) k_group_pass(GroupArgs g) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
   constexpr size_t tile_amps = (size_t)1 << (NBH + LW);
@@ -1178,15 +1039,15 @@ __global__ void __launch_bounds__(kSplitThreads, PF ? 2 : 3) k_group_pass(GroupA
   // every CTA of a cluster runs the same groups, so all of them reach every barrier
   for (long long ib = cid; ib < g.groups; ib += ncl) {
     if constexpr (KIND == 0) {
-      group_phase<R, kSplitDif, false, NBH, PF>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitDif, false, NBH>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
       cluster_barrier();
-      group_phase<R, kSplitMid, FULL, NBL, PF>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitMid, FULL, NBL>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
       cluster_barrier();
-      group_phase<R, kSplitDit, false, NBH, PF>(g.ph[2], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitDit, false, NBH>(g.ph[2], ib, (int)rank, (int)G, Xb, Y, tw);
     } else {
-      group_phase<R, kSplitHad, false, NBH, PF>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitHad, false, NBH>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
       cluster_barrier();
-      group_phase<R, kSplitHad, false, NBL, PF>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitHad, false, NBL>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
     }
     // the next group touches other columns only: no barrier before its first pass
   }
@@ -1218,7 +1079,7 @@ inline void group_shape(int* G, int* budget_mib) {
   }
 }
 
-template <class R, int KIND, bool FULL, int NBH, int NBL, bool PF>
+template <class R, int KIND, bool FULL, int NBH, int NBL>
 hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
@@ -1226,7 +1087,7 @@ hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const
   const size_t tile = ((size_t)1 << (NBH + LW)) * sizeof(T);
   const size_t smem = (KIND == 0 ? (size_t)twiddle_entries(m) * sizeof(T) : 0) + 2 * tile +
                       ((KIND == 0 && FULL) ? ((size_t)1 << (NBL + LW)) * sizeof(T) : 0);
-  auto kern = k_group_pass<R, KIND, FULL, NBH, NBL, PF>;
+  auto kern = k_group_pass<R, KIND, FULL, NBH, NBL>;
   int G = 8, budget = 128;
   group_shape(&G, &budget);
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1266,25 +1127,18 @@ hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const
   return HHL_OK;
 }
 
-template <class R, int KIND, bool FULL, bool PF>
-hhl_status launch_group_pf(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
-  switch (g.ph[0].m) {
-    case 8: return launch_group_nb<R, KIND, FULL, 4, 4, PF>(g, outer, st, name);
-    case 9: return launch_group_nb<R, KIND, FULL, 5, 4, PF>(g, outer, st, name);
-    case 10: return launch_group_nb<R, KIND, FULL, 5, 5, PF>(g, outer, st, name);
-    case 11: return launch_group_nb<R, KIND, FULL, 6, 5, PF>(g, outer, st, name);
-    case 12: return launch_group_nb<R, KIND, FULL, 6, 6, PF>(g, outer, st, name);
-    case 13: return launch_group_nb<R, KIND, FULL, 7, 6, PF>(g, outer, st, name);
-    case 14: return launch_group_nb<R, KIND, FULL, 7, 7, PF>(g, outer, st, name);
-    default: return fail(HHL_ERR_UNSUPPORTED, "group pass: register bits out of range");
-  }
-}
-
 template <class R, int KIND, bool FULL>
 hhl_status launch_group(const GroupArgs& g, int outer, cudaStream_t st, const char* name) {
-  const char* env = getenv("HHL_GROUP_PF");
-  if (env != nullptr && atoi(env) == 0) return launch_group_pf<R, KIND, FULL, false>(g, outer, st, name);
-  return launch_group_pf<R, KIND, FULL, true>(g, outer, st, name);
+  switch (g.ph[0].m) {
+    case 8: return launch_group_nb<R, KIND, FULL, 4, 4>(g, outer, st, name);
+    case 9: return launch_group_nb<R, KIND, FULL, 5, 4>(g, outer, st, name);
+    case 10: return launch_group_nb<R, KIND, FULL, 5, 5>(g, outer, st, name);
+    case 11: return launch_group_nb<R, KIND, FULL, 6, 5>(g, outer, st, name);
+    case 12: return launch_group_nb<R, KIND, FULL, 6, 6>(g, outer, st, name);
+    case 13: return launch_group_nb<R, KIND, FULL, 7, 6>(g, outer, st, name);
+    case 14: return launch_group_nb<R, KIND, FULL, 7, 7>(g, outer, st, name);
+    default: return fail(HHL_ERR_UNSUPPORTED, "group pass: register bits out of range");
+  }
 }
 
 // ------------------------------------------------------------- one-pass clustered clock block
@@ -1717,10 +1571,14 @@ hhl_status hadamard_split(void* base, int lo, int m, int outer, cudaStream_t st)
   return launch_split<R, kSplitHad, false>(a, outer, st, "k_hadamard_pass");
 }
 
-// The group passes serve complex64 states on the split path when HHL_GROUP=1.
-inline bool group_applies() {
+// The group passes serve complex64 states on the split path: the Hadamard layer by default
+// (measured faster than its two streaming passes), the clock block when HHL_GROUP=1 (measured
+// slower than its three streaming passes: its groups in flight either overflow L2 or leave
+// too few CTAs to hide the latency of the pass-by-pass barriers); HHL_GROUP=0 turns both off.
+inline bool group_applies(bool clock) {
   const char* env = getenv("HHL_GROUP");
-  return env != nullptr && atoi(env) != 0;
+  if (env != nullptr) return atoi(env) != 0;
+  return !clock;
 }
 
 // The three passes of clock_block_split as one L2-staged group launch.
@@ -1792,7 +1650,7 @@ hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
   if (p.prec == HHL_PREC_C64) {
     if (clock_cluster_applies<float>(p)) return clock_block_cluster<float>(p, state, st);
     if (split_applies<float>(p.n_s, p.n_c, half)) {
-      if (group_applies()) return p.full ? clock_block_group<true>(p, state, st) : clock_block_group<false>(p, state, st);
+      if (group_applies(true)) return p.full ? clock_block_group<true>(p, state, st) : clock_block_group<false>(p, state, st);
       return p.full ? clock_block_split<float, true>(p, state, st) : clock_block_split<float, false>(p, state, st);
     }
     return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
@@ -1814,7 +1672,7 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
       return hadamard_cluster<float>(base, p.n_s, p.n_c, outer, st);
     if (!split_applies<float>(p.n_s, p.n_c, half_amps))
       return register_transform_impl<float>(base, n, p.n_s, p.n_c, 2, st);
-    return group_applies() ? hadamard_group(base, p.n_s, p.n_c, outer, st)
+    return group_applies(false) ? hadamard_group(base, p.n_s, p.n_c, outer, st)
                            : hadamard_split<float>(base, p.n_s, p.n_c, outer, st);
   }
   if (hadamard_cluster_applies<double>(p.n_s, p.n_c, half_amps))

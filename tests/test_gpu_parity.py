@@ -585,7 +585,7 @@ def test_cluster_clock_block_parity(hhl, monkeypatch, prec, flow, n_s, n_c):
 
 
 @pytest.mark.parametrize("prec,group", [("c128", None), ("c64", None), ("c64", "8,64"), ("c64", "2,1"),
-                                        ("c64", "16,1"), ("c64", "4,1,nopf"), ("c64", "1,1")])
+                                        ("c64", "16,1"), ("c64", "4,1"), ("c64", "1,1")])
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("flow,n_s,n_c", [("couette", 5, 8), ("poiseuille", 6, 9), ("couette", 7, 11),
                                           ("poiseuille", 6, 12), ("couette", 5, 13)])
@@ -594,15 +594,13 @@ def test_split_register_passes_parity(hhl, monkeypatch, prec, group, full, flow,
     take), forced on small states, stage by stage against the oracle: streaming passes
     (group None) or L2-staged group passes with G CTAs per cluster and an L2 budget in MiB
     ("G,MiB": a budget of 1 MiB leaves fewer clusters than column blocks, so each cluster
-    runs several groups; "nopf": register tiles without the next tile's loads in flight).
-    12 and 13 clock bits take the register-resident tiles in every pass of a group launch."""
+    runs several groups)."""
     import torch
     monkeypatch.setenv("HHL_FFT_SPLIT", "1")
     monkeypatch.setenv("HHL_CLOCK_CLUSTER", "0")
     monkeypatch.setenv("HHL_GROUP", "0" if group is None else "1")
     if group is not None:
-        monkeypatch.setenv("HHL_GROUP_SHAPE", ",".join(group.split(",")[:2]))
-        monkeypatch.setenv("HHL_GROUP_PF", "0" if group.endswith("nopf") else "1")
+        monkeypatch.setenv("HHL_GROUP_SHAPE", group)
     diag, off, b, walls = problem(flow, n_s)
     pl = _oracle_plan(diag, off, n_c, "range_fill")
     ref = run_stages(b, n_s, pl)
