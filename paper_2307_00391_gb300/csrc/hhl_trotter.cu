@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
   stage_issue<T>(stage_w, cur, half, side, gw, segs, N, lane);
   cp_async_commit();
   int buf = 0;
+  int cached = 0, n_layers = 0, first_o = 0;  // the row pattern whose layers rot_w holds (patterns are >= 1)
   for (int v = v0; v < v1; ++v) {
     Window nxt = cur;
     const bool more = v + 1 < v1;
@@ -328,12 +329,16 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
       // a full window followed by the next segment of its row: carry the left halo over
       if (more && nxt.s > 0) carry_copy(stage_w + (buf ^ 1) * 32 * CPL, stage, lane, CPL);
       const LayerList* L = lists + cur.pattern;
-      const int n_layers = L->n, first_o = L->first_o;
-      if (lane < n_layers) {
-        rot_w[4 * lane] = layer_c<R>(L, lane);
-        rot_w[4 * lane + 1] = layer_s<R>(L, lane);
-        rot_w[4 * lane + 2] = layer_w<R>(L, lane);
-        rot_w[4 * lane + 3] = (R)L->form[lane];
+      if (cur.pattern != cached) {  // a new row pattern (runs change rows rarely)
+        cached = cur.pattern;
+        n_layers = L->n;
+        first_o = L->first_o;
+        if (lane < n_layers) {
+          rot_w[4 * lane] = layer_c<R>(L, lane);
+          rot_w[4 * lane + 1] = layer_s<R>(L, lane);
+          rot_w[4 * lane + 2] = layer_w<R>(L, lane);
+          rot_w[4 * lane + 3] = (R)L->form[lane];
+        }
       }
       const int64_t g0 = (int64_t)cur.s * kInterior;               // first interior amplitude
       const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
           if (lane0 + q < N) row[lane0 + q] = x[q];
       }
     }
-    __syncwarp();  // this buffer and the rotation table are free for the next issue
+    __syncwarp();  // this buffer is free for the next issue, the rotation table for a new pattern
     cur = nxt;
     buf ^= 1;
   }
