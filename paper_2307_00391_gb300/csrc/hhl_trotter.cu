@@ -277,10 +277,27 @@ __device__ __forceinline__ void carry_copy(uint4* next_stage, const uint4* stage
   if (lane < cpl) next_stage[lane] = stage[(30 * cpl + lane) ^ 6];
 }
 
+// The window after d in its run (window v of the pass; the run ends before v1).
+__device__ __forceinline__ Window window_next(Window d, int v, int v1, int segs, int64_t N, int single_k, int kb,
+                                              int gbits) {
+  d.first = false;
+  d.last = v + 2 == v1;
+  if (++d.s == segs) {
+    d.s = 0;
+    ++d.i;
+    pass_row(d.i, single_k, kb, gbits, &d.row, &d.pattern);
+  }
+  d.full = (int64_t)d.s * kInterior + kInterior <= N;
+  return d;
+}
+
 // Persistent warps: each warp walks its run of windows in order; the copies of its next
-// window go to the second staging buffer (cp.async) while it computes the current.
+// window go to the second staging buffer (cp.async) while it computes the current. (The next
+// window is formed again after the current one is done, so that it holds no registers
+// during the layers.) 16 warps per SM with up to 128 registers each: the paired layers need
+// them (with 24 warps and 80 registers the pass spilled and ran 10% slower).
 template <class R>
-__global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
+__global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 2 : 1) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
                                                               const typename Cx<R>::T* __restrict__ side, int n_s,
                                                               int segs, int windows, int nruns, int single_k,
                                                               int kb, int gbits, const LayerList* __restrict__ lists) {
@@ -308,26 +325,17 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
   int buf = 0;
   int cached = 0, n_layers = 0, first_o = 0;  // the row pattern whose layers rot_w holds (patterns are >= 1)
   for (int v = v0; v < v1; ++v) {
-    Window nxt = cur;
     const bool more = v + 1 < v1;
-    if (more) {
-      nxt.first = false;
-      nxt.last = v + 2 == v1;
-      if (++nxt.s == segs) {
-        nxt.s = 0;
-        ++nxt.i;
-        pass_row(nxt.i, single_k, kb, gbits, &nxt.row, &nxt.pattern);
-      }
-      nxt.full = (int64_t)nxt.s * kInterior + kInterior <= N;
-      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, nxt, half, side, gw, segs, N, lane);
-    }
+    if (more)
+      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, window_next(cur, v, v1, segs, N, single_k, kb, gbits), half, side,
+                     gw, segs, N, lane);
     cp_async_commit();
     cp_async_wait1();  // the current window's copies have landed
     __syncwarp();
     {
       uint4* stage = stage_w + buf * 32 * CPL;
       // a full window followed by the next segment of its row: carry the left halo over
-      if (more && nxt.s > 0) carry_copy(stage_w + (buf ^ 1) * 32 * CPL, stage, lane, CPL);
+      if (more && cur.s + 1 < segs) carry_copy(stage_w + (buf ^ 1) * 32 * CPL, stage, lane, CPL);
       const LayerList* L = lists + cur.pattern;
       if (cur.pattern != cached) {  // a new row pattern (runs change rows rarely)
         cached = cur.pattern;
@@ -372,11 +380,30 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
       // the window but possibly the halos', whose values do not reach the interior)
       const bool away = cur.full && g0 >= 2 && g0 + kInterior + 1 <= N;
       if (away) {
-        for (int l = 0; l < n_layers; ++l) {
-          const R wl = rot_w[4 * l + 2];
-          const bool e_layer = ((l + first_o) & 1) == 0;
-          if (rot_w[4 * l + 3] != (R)0) layer_factored<true>(x, e_layer, wl);
-          else layer_factored<false>(x, e_layer, wl);
+        // layers alternate E, O: an O layer first on its own, then (E, O) pairs in one loop
+        // body (the pair's second layer writes its outputs back into the registers the loop
+        // carries, so no register copies are needed between layers), then a last E layer
+        int l = 0;
+        if (first_o && n_layers > 0) {
+          if (rot_w[3] != (R)0) layer_factored<true>(x, false, rot_w[2]);
+          else layer_factored<false>(x, false, rot_w[2]);
+          l = 1;
+        }
+        for (; l + 1 < n_layers; l += 2) {
+          const R we = rot_w[4 * l + 2], wo = rot_w[4 * l + 6];
+          if (rot_w[4 * l + 3] != (R)0) {
+            layer_factored<true>(x, true, we);
+            if (rot_w[4 * l + 7] != (R)0) layer_factored<true>(x, false, wo);
+            else layer_factored<false>(x, false, wo);
+          } else {
+            layer_factored<false>(x, true, we);
+            if (rot_w[4 * l + 7] != (R)0) layer_factored<true>(x, false, wo);
+            else layer_factored<false>(x, false, wo);
+          }
+        }
+        if (l < n_layers) {
+          if (rot_w[4 * l + 3] != (R)0) layer_factored<true>(x, true, rot_w[4 * l + 2]);
+          else layer_factored<false>(x, true, rot_w[4 * l + 2]);
         }
       }
       // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
@@ -443,7 +470,7 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 3 : 1) k_trotte
       }
     }
     __syncwarp();  // this buffer is free for the next issue, the rotation table for a new pattern
-    cur = nxt;
+    if (more) cur = window_next(cur, v, v1, segs, N, single_k, kb, gbits);
     buf ^= 1;
   }
 }
@@ -468,11 +495,12 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
   T* side = (T*)p.d_scratch;  // sized by the planner for R * segs * 32 amplitudes
   const LayerList* lists = (const LayerList*)p.d_trot_lists;
   const size_t smem = trotter_smem<R>();
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_trotter_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = k_trotter_pass<R>;
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trotter_pass<R>, kTrotThreads, smem));
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTrotThreads, smem));
   if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass does not fit an SM");
   for (const TrotPassDesc& d : p.trot_pass[adjoint ? 1 : 0]) {
     // pass rows: those with clock bit single_k set, or with a nonzero pattern of the group
@@ -494,7 +522,7 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
                                                                                 d.gbits);
     HHL_LAUNCH_CHECK("k_trotter_bounds");
     HHL_PROF_BEGIN(st);
-    k_trotter_pass<R><<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)windows, nruns,
+    kern<<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)windows, nruns,
                                                          d.single_k, d.kb, d.gbits, lists + d.list_off);
     HHL_LAUNCH_CHECK("k_trotter_pass");
   }
