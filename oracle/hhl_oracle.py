@@ -136,6 +136,9 @@ def t0_total(rule: str, n_clock: int, kappa: float | None = None, t0: float | No
     """Hamiltonian-simulation time T0 in the "total" convention (U_k = exp(i Ahat T0 2^k/2^n_c))."""
     if rule == "range_fill":
         return 2.0 * math.pi * ((1 << n_clock) - 1)
+    if rule == "range_fill_signed":
+        # signed clock: lambdahat = +-1 maps to the clock values +-(2^(n_c-1) - 1)
+        return 2.0 * math.pi * ((1 << (n_clock - 1)) - 1)
     if rule == "power_law":
         per_unit = math.exp(0.918) * kappa ** (-0.363)
         return per_unit * (1 << n_clock)
@@ -144,16 +147,24 @@ def t0_total(rule: str, n_clock: int, kappa: float | None = None, t0: float | No
     raise ValueError(rule)
 
 
-def rotation_angles(n_clock: int, t0: float, c_const: float | None = None) -> np.ndarray:
+def rotation_angles(n_clock: int, t0: float, c_const: float | None = None,
+                    signed: bool = False) -> np.ndarray:
     """theta_y for clock values y = 0 .. 2^n_c - 1: the ancilla amplitude after the
     controlled RY is sin(theta_y/2) = min(1, C / lambda~_y), lambda~_y = 2 pi y / T0,
-    and theta_0 = 0 (Sec. IV/VI eigenvalue inversion, reading of C and y = 0)."""
+    and theta_0 = 0 (Sec. IV/VI eigenvalue inversion, reading of C and y = 0).
+
+    signed: the clock value is read in two's complement, y_s = y - 2^n_c for
+    y >= 2^(n_c-1), so that a negative eigenvalue (an indefinite A, such as the Hermitian
+    dilation of a one-shot time-stepping system) gets lambda~ = 2 pi y_s / T0 < 0 and a
+    negative amplitude, sin(theta_y/2) = max(-1, min(1, C / lambda~))."""
     if c_const is None:
         c_const = 2.0 * math.pi / t0
     th = np.zeros(1 << n_clock)
+    half = 1 << (n_clock - 1)
     for y in range(1, 1 << n_clock):
-        lam = 2.0 * math.pi * y / t0
-        th[y] = 2.0 * math.asin(min(1.0, c_const / lam))
+        ys = y - (1 << n_clock) if (signed and y >= half) else y
+        lam = 2.0 * math.pi * ys / t0
+        th[y] = 2.0 * math.asin(max(-1.0, min(1.0, c_const / lam)))
     return th
 
 
@@ -364,15 +375,18 @@ def apply_trotter_controlled(psi: np.ndarray, n: int, n_s: int, control: int,
 
 
 def plan(a: np.ndarray, n_clock: int, t0_rule: str = "range_fill", t0: float | None = None,
-         t0_convention: str = "total", c_const: float | None = None) -> dict:
-    """Classical pre-computation (Sec. II.A): Ahat, lambda_ub, kappa, T0, C and theta_y."""
+         t0_convention: str = "total", c_const: float | None = None, signed: bool = False) -> dict:
+    """Classical pre-computation (Sec. II.A): Ahat, lambda_ub, kappa, T0, C and theta_y.
+    signed: two's-complement clock reading for an indefinite A ("range_fill" then maps
+    lambdahat = +-1 to +-(2^(n_c-1) - 1))."""
     lam_ub = gershgorin_bound(a)
     a_hat = a / lam_ub
     kappa = condition_number(a)
-    t0_tot = t0_total(t0_rule, n_clock, kappa=kappa, t0=t0, convention=t0_convention)
+    rule = "range_fill_signed" if (signed and t0_rule == "range_fill") else t0_rule
+    t0_tot = t0_total(rule, n_clock, kappa=kappa, t0=t0, convention=t0_convention)
     c = (2.0 * math.pi / t0_tot) if c_const is None else c_const
     return dict(lam_ub=lam_ub, a_hat=a_hat, kappa=kappa, t0=t0_tot, C=c,
-                theta=rotation_angles(n_clock, t0_tot, c), n_clock=n_clock)
+                theta=rotation_angles(n_clock, t0_tot, c, signed=signed), n_clock=n_clock)
 
 
 def prepare_state(b: np.ndarray, n_s: int, n_c: int) -> np.ndarray:

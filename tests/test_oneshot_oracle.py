@@ -1,0 +1,113 @@
+"""Pins of the one-shot time-stepping systems (App. A, Eqs. FE_OBM / BE_OBM) and of the
+two's-complement clock reading used for their indefinite Hermitian dilations: against the
+time-marching recurrences, closed forms, the steady limit, library SVD / solves, and an
+exact (on-grid) HHL run with negative eigenvalues."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hhl_oracle as o
+from oracle import oneshot_oracle as os1
+
+
+def _setup(n_points=4, seed=3):
+    rng = np.random.default_rng(seed)
+    a = os1.time_operator(n_points, nu=1.0)
+    f = np.full(n_points, 8.0)
+    u_in = rng.uniform(0.0, 1.0, n_points)
+    return a, f, u_in
+
+
+@pytest.mark.parametrize("m,p", [(1, 0), (5, 2), (9, 6)])
+def test_fe_one_shot_solve_is_the_forward_euler_march(m, p):
+    a, f, u_in = _setup()
+    dt = 0.25 * (1.0 / 5) ** 2          # Courant number 0.25 at N_g = 4
+    big, rhs = os1.fe_system(a, f, u_in, dt, m, p)
+    x = np.linalg.solve(big, rhs)
+    us = os1.fe_march(a, f, u_in, dt, m, p)
+    np.testing.assert_allclose(x, np.concatenate(us), rtol=1e-12, atol=1e-12)
+    # closed form of the march: u^m = G^m u_in + sum_{j<m} G^j f dt, G = I + A dt
+    g = np.eye(4) + a * dt
+    um = np.linalg.matrix_power(g, m) @ u_in + sum(np.linalg.matrix_power(g, j) for j in range(m)) @ f * dt
+    np.testing.assert_allclose(os1.final_slice(x, 4, m, p), um, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,p", [(1, 1), (6, 1), (12, 3)])
+def test_be_one_shot_solve_is_the_backward_euler_march(m, p):
+    a, f, u_in = _setup(seed=5)
+    dt = 0.01
+    big, rhs = os1.be_system(a, f, u_in, dt, m, p)
+    x = np.linalg.solve(big, rhs)
+    np.testing.assert_allclose(x, np.concatenate(os1.be_march(a, f, u_in, dt, m, p)), rtol=1e-12, atol=1e-12)
+    # each block row is the implicit step itself
+    n = 4
+    for i in range(1, m + 1):
+        lhs = (np.eye(n) - dt * a) @ x[i * n:(i + 1) * n] - x[(i - 1) * n:i * n]
+        np.testing.assert_allclose(lhs, f * dt, atol=1e-12)
+
+
+def test_be_one_shot_reaches_the_steady_channel_flow():
+    """Many implicit steps: the last field solves A u + f = 0, i.e. the steady Poiseuille
+    profile of the discrete operator (Thomas solve of the SPD system -A u = f)."""
+    n = 8
+    a = os1.time_operator(n)
+    f = np.full(n, 2.0)
+    big, rhs = os1.be_system(a, f, np.zeros(n), 0.05, 400, 0)
+    u_last = os1.final_slice(np.linalg.solve(big, rhs), n, 400, 0)
+    diag, off = o.laplacian_tridiag(n)
+    steady = o.thomas_solve(diag, off, f)
+    np.testing.assert_allclose(u_last, steady, rtol=1e-9)
+    y = np.arange(1, n + 1) / (n + 1)
+    np.testing.assert_allclose(steady, y * (1 - y), rtol=1e-12)  # -u'' = 2: exact on the grid
+
+
+def test_dilation_spectrum_and_solution():
+    a, f, u_in = _setup(seed=7)
+    big, rhs = os1.fe_system(a, f, u_in, 0.01, 3, 1)
+    h = os1.dilation(big)
+    np.testing.assert_array_equal(h, h.T)
+    sv = np.linalg.svd(big, compute_uv=False)
+    ev = np.sort(np.linalg.eigvalsh(h))
+    np.testing.assert_allclose(ev, np.sort(np.concatenate([sv, -sv])), rtol=1e-11, atol=1e-12)
+    hp, rp = os1.dilated_problem(big, rhs)
+    assert hp.shape[0] == 64 and np.allclose(hp[40:, 40:], np.eye(24))
+    xd = np.linalg.solve(hp, rp)
+    k = big.shape[0]
+    np.testing.assert_allclose(xd[:k], 0.0, atol=1e-12)
+    np.testing.assert_allclose(xd[2 * k:], 0.0, atol=1e-12)
+    np.testing.assert_allclose(os1.solution_part(xd, k), np.linalg.solve(big, rhs), rtol=1e-11)
+
+
+def test_signed_rotation_angles():
+    n_c, t0 = 4, 2 * math.pi * 7
+    th = o.rotation_angles(n_c, t0, signed=True)
+    for y in range(16):
+        ys = y - 16 if y >= 8 else y
+        want = 0.0 if ys == 0 else 2 * math.asin(max(-1.0, min(1.0, 1.0 / (ys * 1.0))))
+        assert th[y] == pytest.approx(want, abs=1e-15)
+    assert o.t0_total("range_fill_signed", 6) == pytest.approx(2 * math.pi * 31)
+    # the unsigned reading is unchanged
+    np.testing.assert_allclose(o.rotation_angles(n_c, t0)[1:8], th[1:8])
+
+
+def test_signed_hhl_is_exact_on_the_clock_grid():
+    """An indefinite A whose eigenvalues sit on the two's-complement clock grid: phase
+    estimation is exact, so the postselected vector is C Ahat^{-1} bhat to rounding."""
+    rng = np.random.default_rng(11)
+    lam = np.array([3.0, -5.0, 7.0, -2.0])
+    q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    a = q @ np.diag(lam) @ q.T
+    lub = o.gershgorin_bound(a)
+    n_s, n_c = 2, 5
+    pl = o.plan(a, n_c, t0_rule="user", t0=2 * math.pi * lub, signed=True)  # y_j = lambda_j
+    b = rng.uniform(0.0, 1.0, 4)
+    psi = o.hhl_circuit(b, n_s, pl)
+    v = o.postselect(psi, n_s, n_c)["v"]
+    bh = b / np.linalg.norm(b)
+    want = pl["C"] * np.linalg.solve(a / lub, bh)
+    np.testing.assert_allclose(v, want, atol=1e-10)
+    # the unsigned reading of the same clock gets the negative eigen-components wrong
+    pl_u = o.plan(a, n_c, t0_rule="user", t0=2 * math.pi * lub)
+    v_u = o.postselect(o.hhl_circuit(b, n_s, pl_u), n_s, n_c)["v"]
+    assert np.abs(v_u - want).max() > 1e-2
