@@ -124,6 +124,13 @@ typedef struct hhl_params {
   int32_t trotter_steps_max; /* 0 = no cap */
   int32_t gemm_impl;         /* hhl_gemm_impl */
   double t0_scale;           /* multiplies the T0 of the rule (0 or 1: unchanged) */
+  int32_t signed_clock;      /* 1: read the clock in two's complement, y_s = y - 2^n_c for
+                                y >= 2^(n_c-1), so that an indefinite A (the Hermitian dilation
+                                [[0, M], [M^T, 0]] of a one-shot time-stepping system, App. A
+                                Eqs. FE_OBM / BE_OBM) is inverted with the sign of each
+                                eigenvalue: sin(theta_y / 2) = clip(C / lambda~_ys, -1, 1),
+                                lambda~_ys = 2 pi y_s / T0; RANGE_FILL then takes
+                                T0 = 2 pi (2^(n_c-1) - 1). 0: unsigned, A positive definite. */
 } hhl_params;
 
 typedef struct hhl_plan_info {
@@ -167,7 +174,8 @@ void hhl_params_default(hhl_params* p);
  * Validates A, normalises it by lambda_ub, computes kappa, T0, C, the rotation angles
  * theta_y in FP64, the U_k matrices (dense mode; on the device, FP64) or the Strang
  * blocks (Trotter mode), and uploads the tables. On success *out owns device memory.
- * Requires A positive definite (the clock value is read as an unsigned fraction). */
+ * Requires A positive definite (the clock value is read as an unsigned fraction) unless
+ * params.signed_clock = 1. */
 hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hhl_plan_t* out);
 void hhl_plan_destroy(hhl_plan_t plan);
 hhl_status hhl_plan_get_info(hhl_plan_t plan, hhl_plan_info* info);

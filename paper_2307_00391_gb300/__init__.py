@@ -77,7 +77,7 @@ class HHLPlan:
                  precision: str = "c64", t0_rule: str = "range_fill", t0: float = 0.0,
                  t0_convention: str = "total", C: float = 0.0, expm: str = "dense",
                  full_uncompute: bool = False, trotter_dt: float = 1.0, trotter_steps_max: int = 0,
-                 gemm: str = "auto", nu: float = 0.1, walls=(0.0, 0.0)):
+                 gemm: str = "auto", nu: float = 0.1, walls=(0.0, 0.0), signed_clock: bool = False):
         lib = load()
         self._lib = lib
         self._keep = []
@@ -113,6 +113,7 @@ class HHLPlan:
         par.trotter_dt = trotter_dt
         par.trotter_steps_max = trotter_steps_max
         par.gemm_impl = _GEMM[gemm]
+        par.signed_clock = int(signed_clock)
         h = ctypes.c_void_p()
         check(lib.hhl_plan_create(ctypes.byref(prob), ctypes.byref(par), ctypes.byref(h)), "hhl_plan_create")
         self._h = h

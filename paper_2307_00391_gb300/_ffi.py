@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n_clock", c_int32), ("t0_rule", c_int32), ("t0_convention", c_int32),
                 ("precision", c_int32), ("t0", c_double), ("C", c_double), ("expm_mode", c_int32),
                 ("full_uncompute", c_int32), ("trotter_dt", c_double), ("trotter_steps_max", c_int32),
-                ("gemm_impl", c_int32), ("t0_scale", c_double)]
+                ("gemm_impl", c_int32), ("t0_scale", c_double), ("signed_clock", c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

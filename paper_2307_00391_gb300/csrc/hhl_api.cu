@@ -198,6 +198,8 @@ hhl_status validate(const hhl_problem* pr, const hhl_params* pa) {
     return fail(HHL_ERR_UNSUPPORTED, "the tcgen05 GEMM is complex64 only");
   if (pa->expm_mode == HHL_EXPM_TROTTER && !(pa->trotter_dt > 0.0)) return fail(HHL_ERR_INVALID_ARG, "trotter_dt must be > 0");
   if (pa->trotter_steps_max < 0) return fail(HHL_ERR_INVALID_ARG, "trotter_steps_max < 0");
+  if (pa->signed_clock != 0 && pa->signed_clock != 1) return fail(HHL_ERR_INVALID_ARG, "signed_clock must be 0 or 1");
+  if (pa->signed_clock && pa->n_clock < 2) return fail(HHL_ERR_INVALID_ARG, "a signed clock needs n_clock >= 2");
   if (!std::isfinite(pr->nu) || !std::isfinite(pr->wall_lo) || !std::isfinite(pr->wall_hi))
     return fail(HHL_ERR_INVALID_ARG, "non-finite nu or wall value");
   const int64_t N = 1LL << pr->n_sys_qubits;
@@ -341,14 +343,15 @@ hhl_status plan_host(const hhl_problem* prob, const hhl_params* params, Plan& p,
     amax = std::max(amax, fabs(l));
   }
   if (amin <= 1e-14 * amax) { return fail(HHL_ERR_SINGULAR, "A is singular"); }
-  if (lmin <= 0.0) { return fail(HHL_ERR_UNSUPPORTED, "A must be positive definite (unsigned clock reading)"); }
+  if (lmin <= 0.0 && !params->signed_clock)
+    return fail(HHL_ERR_UNSUPPORTED, "A must be positive definite (unsigned clock reading; signed_clock = 1 for an indefinite A)");
   p.lam_min = lmin;
   p.lam_max = lmax;
   p.kappa = amax / amin;
 
   // T0 (total convention) and C
   switch (params->t0_rule) {
-    case HHL_T0_RANGE_FILL: p.t0 = 2.0 * kPi * (double)(p.R - 1); break;
+    case HHL_T0_RANGE_FILL: p.t0 = 2.0 * kPi * (double)(params->signed_clock ? p.R / 2 - 1 : p.R - 1); break;
     case HHL_T0_POWER_LAW: p.t0 = exp(0.918) * pow(p.kappa, -0.363) * (double)p.R; break;
     default: p.t0 = params->t0_convention == HHL_T0_PER_UNIT ? params->t0 * (double)p.R : params->t0; break;
   }
@@ -356,8 +359,10 @@ hhl_status plan_host(const hhl_problem* prob, const hhl_params* params, Plan& p,
   p.C = params->C > 0.0 ? params->C : 2.0 * kPi / p.t0;
   p.theta.assign(p.R, 0.0);
   for (int64_t y = 1; y < p.R; ++y) {
-    const double lam = 2.0 * kPi * (double)y / p.t0;
-    p.theta[y] = 2.0 * asin(std::min(1.0, p.C / lam));
+    // two's complement for a signed clock: the top half of the values are negative
+    const int64_t ys = (params->signed_clock && y >= p.R / 2) ? y - p.R : y;
+    const double lam = 2.0 * kPi * (double)ys / p.t0;
+    p.theta[y] = 2.0 * asin(std::max(-1.0, std::min(1.0, p.C / lam)));
   }
 
   return HHL_OK;

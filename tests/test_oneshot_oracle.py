@@ -111,3 +111,24 @@ def test_signed_hhl_is_exact_on_the_clock_grid():
     pl_u = o.plan(a, n_c, t0_rule="user", t0=2 * math.pi * lub)
     v_u = o.postselect(o.hhl_circuit(b, n_s, pl_u), n_s, n_c)["v"]
     assert np.abs(v_u - want).max() > 1e-2
+
+
+@pytest.mark.parametrize("scheme", ["fe", "be"])
+def test_library_builder_matches_the_oracle_systems(scheme):
+    """The library's host-side construction (Kronecker products) against the oracle's
+    block-by-block one (host logic; no GPU)."""
+    from paper_2307_00391_gb300 import oneshot as lib1
+    a, f, u_in = _setup(seed=9)
+    np.testing.assert_allclose(lib1.unsteady_operator(4, 1.0), a, rtol=1e-15)
+    dt, m, p = 0.01, 5, 2
+    mat, rhs = lib1.one_shot_system(a, f, u_in, dt, m, p, scheme)
+    big, brhs = (os1.fe_system if scheme == "fe" else os1.be_system)(a, f, u_in, dt, m, p)
+    np.testing.assert_allclose(mat, big, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(rhs, brhs, rtol=1e-15, atol=0)
+    h, r = lib1.hermitian_dilation(mat, rhs)
+    hp, rp = os1.dilated_problem(big, brhs)
+    np.testing.assert_array_equal(h, hp)
+    np.testing.assert_array_equal(r, rp)
+    x = np.linalg.solve(hp, rp)
+    np.testing.assert_allclose(lib1.final_field(x, big.shape[0], 4),
+                               os1.final_slice(os1.solution_part(x, big.shape[0]), 4, m, p), rtol=1e-14)
