@@ -17,7 +17,9 @@ library call per step (no blocking, fusion or reordering):
   Hadamards), and postselection on ancilla = 1, clock = 0;
 * the viscous dissipation rate eps = nu <(du/dy)^2> of Sec. VII / App. D, evaluated with
   the same finite-difference post-processing as the classical solution;
-* the Grover-Rudolph binary-tree state preparation QSP-1 of App. C;
+* the Grover-Rudolph binary-tree state preparation QSP-1 of App. C, and QSP-2 (Sec. III,
+  App. C): the same rotations only on the nodes of the decision tree that lie on a path to a
+  nonzero leaf, as multi-controlled gates (X gates around the controls that must read 0);
 * the second-order (Strang) Trotter product for exp(i Ahat t) on a tridiagonal Ahat, gate
   by gate (paper silent; reading below).
 
@@ -551,3 +553,66 @@ def qft_register(psi: np.ndarray, n: int, lo: int, m: int, inverse: bool) -> np.
     out = psi.astype(np.complex128).copy()
     qft(out, n, lo, m, inverse=inverse)
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# QSP-2 (Sec. III, App. C): sparse state preparation along the paths of a decision diagram
+# ---------------------------------------------------------------------------------------
+
+
+def qsp2_paths(idx: np.ndarray, val: np.ndarray, n: int) -> list[tuple[int, int, float]]:
+    """The branch nodes of the binary decision tree of a sparse real vector (nonzero values
+    ``val`` at positions ``idx``), root first: one (level l, prefix, theta) per node that lies
+    on a path to a nonzero leaf, where the node holds the l most significant bits ``prefix``
+    and theta = arccos sqrt(p(zero child) / p(node)) in the paper's R_y convention. Nodes off
+    every path (zero subtrees) get no gate; a node with a single nonzero child gets theta 0
+    (zero child) or pi/2 (one child)."""
+    order = np.argsort(idx)
+    idx = np.asarray(idx)[order]
+    prob = np.asarray(val, dtype=float)[order] ** 2
+    out = []
+    for l in range(n):
+        shift = n - l
+        prefixes = sorted(set(int(i) >> shift for i in idx))
+        for pre in prefixes:
+            mask = (idx >> shift) == pre
+            p_node = float(prob[mask].sum())
+            p_zero = float(prob[mask & (((idx >> (shift - 1)) & 1) == 0)].sum())
+            theta = math.acos(math.sqrt(min(1.0, p_zero / p_node))) if p_node > 0 else 0.0
+            out.append((l, pre, theta))
+    return out
+
+
+def qsp2_prepare(idx: np.ndarray, val: np.ndarray, n: int) -> np.ndarray:
+    """Prepare sum_k val_k |idx_k> / |val| from |0>: for every branch node, a rotation
+    R_y(theta) (our RY(2 theta)) on qubit n-1-l controlled by the l more significant qubits
+    holding ``prefix`` (X gates around the controls that must read 0), then the sign of each
+    negative value by a Z on its path (paper silent on signs: a Z on the last qubit
+    controlled by the leaf's other n-1 bits)."""
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    for l, pre, theta in qsp2_paths(idx, val, n):
+        target = n - 1 - l
+        ctrls = list(range(target + 1, n))
+        zeros = [q for q in ctrls if ((pre >> (q - target - 1)) & 1) == 0]
+        for q in zeros:
+            apply_1q(psi, n, q, X_GATE)
+        apply_1q(psi, n, target, ry(2.0 * theta), controls=ctrls)
+        for q in zeros:
+            apply_1q(psi, n, q, X_GATE)
+    z = np.array([[1.0, 0.0], [0.0, -1.0]])
+    for i, v in zip(idx, val):
+        if v < 0:
+            ctrls = list(range(1, n))
+            zeros = [q for q in ctrls if ((int(i) >> q) & 1) == 0]
+            for q in zeros:
+                apply_1q(psi, n, q, X_GATE)
+            if int(i) & 1:
+                apply_1q(psi, n, 0, z, controls=ctrls)
+            else:
+                apply_1q(psi, n, 0, X_GATE, controls=ctrls)
+                apply_1q(psi, n, 0, z, controls=ctrls)
+                apply_1q(psi, n, 0, X_GATE, controls=ctrls)
+            for q in zeros:
+                apply_1q(psi, n, q, X_GATE)
+    return psi

@@ -132,3 +132,42 @@ def test_library_builder_matches_the_oracle_systems(scheme):
     x = np.linalg.solve(hp, rp)
     np.testing.assert_allclose(lib1.final_field(x, big.shape[0], 4),
                                os1.final_slice(os1.solution_part(x, big.shape[0]), 4, m, p), rtol=1e-14)
+
+
+def test_qsp2_prepares_the_sparse_vector_and_counts_path_nodes():
+    """QSP-2 along decision-tree paths: the prepared state is the amplitude encoding of the
+    sparse vector (signs included), only nodes on paths get gates (at most n per nonzero),
+    and on a dense vector its angles are the QSP-1 tree's."""
+    rng = np.random.default_rng(21)
+    n = 7
+    idx = np.sort(rng.choice(1 << n, size=9, replace=False))
+    val = rng.uniform(0.2, 1.0, 9) * rng.choice([-1.0, 1.0], 9)
+    psi = o.qsp2_prepare(idx, val, n)
+    want = np.zeros(1 << n)
+    want[idx] = val / np.linalg.norm(val)
+    np.testing.assert_allclose(psi, want, atol=1e-13)
+    nodes = o.qsp2_paths(idx, val, n)
+    assert len(nodes) <= 9 * n
+    levels = {}
+    for l, pre, th in nodes:
+        levels.setdefault(l, []).append(pre)
+    assert levels[0] == [0] and all(len(v) <= 9 for v in levels.values())
+    # a dense vector: every node is on a path and the angles are QSP-1's
+    b = rng.uniform(0.1, 1.0, 16)
+    ang1 = o.qsp1_angles(b * b)
+    for l, pre, th in o.qsp2_paths(np.arange(16), b, 4):
+        assert th == pytest.approx(ang1[l][pre], abs=1e-14)
+    np.testing.assert_allclose(o.qsp2_prepare(np.arange(16), b, 4), b / np.linalg.norm(b), atol=1e-14)
+
+
+def test_qsp2_on_the_one_shot_right_hand_side():
+    """The dilated one-shot right-hand side [b_fe; 0] is sparse: u_in and m copies of f dt in
+    a 2^7 register; QSP-2 prepares it with at most n gates per nonzero."""
+    a, f, u_in = _setup(n_points=8, seed=4)
+    big, rhs = os1.fe_system(a, f, u_in, 0.003, 3, 4)
+    hp, rp = os1.dilated_problem(big, rhs)
+    nz = np.nonzero(rp)[0]
+    n = int(math.log2(len(rp)))
+    psi = o.qsp2_prepare(nz, rp[nz], n)
+    np.testing.assert_allclose(psi, rp / np.linalg.norm(rp), atol=1e-13)
+    assert len(nz) == 8 * 4 and len(o.qsp2_paths(nz, rp[nz], n)) <= len(nz) * n
