@@ -202,6 +202,20 @@ hhl_status hhl_prepare_rhs_host(hhl_plan_t plan, const double* b_re, const doubl
  * hhl_prepare_rhs. b_dev: DEVICE, N real doubles. Uses plan-owned scratch; asynchronous. */
 hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* state_dev, void* stream);
 
+/* a1, sparse gate-level form (Sec. III and App. C, QSP-2): for a right-hand side with `count`
+ * nonzero entries (the one-shot FE / BE systems of App. A, all registers but the data
+ * ones in |0>), only the nodes of the binary decision tree that lie on a path to a nonzero
+ * leaf get their rotation (the paper's R_y(theta), theta = arccos sqrt(p(zero child) /
+ * p(node)), on qubit n_s-1-l conditioned on the node's l more significant bits): O(count n_s)
+ * gates instead of O(N); a negative value gets its sign by a Z on its path. Then the clock
+ * Hadamard layer as in hhl_prepare_rhs_qsp1; |val| is recorded for the read-outs.
+ * idx_dev: DEVICE int64[count], strictly increasing positions in [0, N) (entries outside
+ * that range are ignored; unsorted or repeated positions give an undefined state, not a
+ * memory error); val_dev: DEVICE double[count], real. Uses plan-owned scratch; asynchronous.
+ * Errors: NULL pointers, count outside 1..N (HHL_ERR_INVALID_ARG). */
+hhl_status hhl_prepare_rhs_qsp2(hhl_plan_t plan, const int64_t* idx_dev, const double* val_dev, int64_t count,
+                                void* state_dev, void* stream);
+
 /* a2..a5 - the circuit after state preparation, in place (Sec. IV/VI, standard HHL):
  * clock-bit-controlled U_k for k = 0..n_c-1, inverse QFT on the clock, clock-controlled
  * RY on the ancilla, QFT on the clock, controlled U_k^dagger for k = n_c-1..0, Hadamard on

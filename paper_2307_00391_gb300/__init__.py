@@ -209,6 +209,14 @@ class HHLPlan:
                                              ctypes.c_void_p(state.data_ptr()),
                                              ctypes.c_void_p(_stream_handle(stream))), "hhl_prepare_rhs_qsp1")
 
+    def prepare_rhs_qsp2(self, idx_dev, val_dev, state, stream=None) -> None:
+        """Sparse gate-level RHS preparation (QSP-2 decision-tree paths + clock Hadamards);
+        idx_dev: torch int64 strictly increasing positions, val_dev: torch float64 values."""
+        check(self._lib.hhl_prepare_rhs_qsp2(self._h, ctypes.c_void_p(idx_dev.data_ptr()),
+                                             ctypes.c_void_p(val_dev.data_ptr()), int(idx_dev.numel()),
+                                             ctypes.c_void_p(state.data_ptr()),
+                                             ctypes.c_void_p(_stream_handle(stream))), "hhl_prepare_rhs_qsp2")
+
     def sample(self, state, uniforms_dev, counts_dev, stream=None) -> None:
         """Shots of the postselected system register: counts_dev (torch int64, N) from the
         uniforms in uniforms_dev (torch float64, one per shot)."""

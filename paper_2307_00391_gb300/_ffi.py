@@ -93,6 +93,7 @@ SIGNATURES = [
     ("hhl_qft_whole", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_sample", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("hhl_prepare_rhs_qsp1", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_prepare_rhs_qsp2", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
     ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_profile_enable", None, [c_int32]),

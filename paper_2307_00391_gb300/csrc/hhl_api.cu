@@ -724,6 +724,16 @@ hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* stat
   return hhl::launch_prep_qsp1(p, b_dev, plan->d_bsplit, (double2*)p.d_b, state_dev, (cudaStream_t)stream);
 }
 
+hhl_status hhl_prepare_rhs_qsp2(hhl_plan_t plan, const int64_t* idx_dev, const double* val_dev, int64_t count,
+                                void* state_dev, void* stream) {
+  if (plan == nullptr || idx_dev == nullptr || val_dev == nullptr || state_dev == nullptr)
+    return fail(HHL_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  if (p.N < 2) return fail(HHL_ERR_UNSUPPORTED, "QSP-2 needs at least one system qubit");
+  if (count < 1 || count > p.N) return fail(HHL_ERR_INVALID_ARG, "count must be in 1..N");
+  return hhl::launch_prep_qsp2(p, idx_dev, val_dev, count, (double2*)p.d_b, state_dev, (cudaStream_t)stream);
+}
+
 static hhl_status ctrl_u(const Plan& p, void* half, int k, bool adj, cudaStream_t st) {
   if (p.gemm_impl == HHL_GEMM_TCGEN05) return hhl::launch_ctrl_u_tc(p, half, k, adj, st);
   return hhl::launch_ctrl_u_dense(p, half, k, adj, st);

@@ -276,6 +276,57 @@ __global__ void k_qsp_level(int l, int n_s, const double* __restrict__ tree, dou
   }
 }
 
+// QSP-2 (Sec. III, App. C): the same tree, but only the nodes on a path to one of the
+// nonzero entries (idx strictly increasing, values val) get a rotation, so the work is
+// O(count n_s) instead of O(N). Level l: the first entry of each run of entries sharing the
+// l top bits (the node's prefix) sums the node's and its zero child's probability over the
+// run and rotates the node's amplitude, which still sits at prefix << (n_s - l) (the lower
+// qubits are |0>), into the pair (zero child, one child). Entries outside [0, N) are ignored
+// (they match no prefix). Negative values get their sign at the end (a Z on the leaf's path).
+// One block; acc = |val|^2 for the dissipation read-out.
+__global__ void __launch_bounds__(1024) k_qsp2_tree(const int64_t* __restrict__ idx, const double* __restrict__ val,
+                                                    int64_t count, int n_s, double2* __restrict__ psi,
+                                                    double* __restrict__ acc) {
+  const int64_t N = 1LL << n_s;
+  for (int l = 0; l < n_s; ++l) {
+    const int shift = n_s - l;
+    for (int64_t k = threadIdx.x; k < count; k += blockDim.x) {
+      const int64_t i = idx[k];
+      if (i < 0 || i >= N) continue;
+      const int64_t pre = i >> shift;
+      if (k > 0 && (idx[k - 1] >> shift) == pre) continue;  // not the first entry of its node
+      double p_node = 0.0, p_zero = 0.0;
+      for (int64_t j = k; j < count && (idx[j] >> shift) == pre; ++j) {
+        const double w = val[j] * val[j];
+        p_node += w;
+        if (((idx[j] >> (shift - 1)) & 1) == 0) p_zero += w;
+      }
+      const double th = p_node > 0.0 ? acos(sqrt(fmin(1.0, p_zero / p_node))) : 0.0;
+      const double c = cos(th), s = sin(th);
+      const int64_t i0 = pre << shift, i1 = i0 | (1LL << (shift - 1));
+      const double2 a0 = psi[i0], a1 = psi[i1];
+      psi[i0] = make_double2(c * a0.x - s * a1.x, c * a0.y - s * a1.y);
+      psi[i1] = make_double2(s * a0.x + c * a1.x, s * a0.y + c * a1.y);
+    }
+    __syncthreads();  // the next level rotates the children this level wrote
+  }
+  __shared__ double part[1024];
+  double w = 0.0;
+  for (int64_t k = threadIdx.x; k < count; k += blockDim.x) {
+    const int64_t i = idx[k];
+    if (i < 0 || i >= N) continue;
+    w += val[k] * val[k];
+    if (val[k] < 0.0) psi[i] = make_double2(-psi[i].x, -psi[i].y);
+  }
+  part[threadIdx.x] = w;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) acc[0] = part[0];
+}
+
 // psi = |0>, then (after the tree) bs = psi / 2^(n_c/2) in the amplitude precision.
 __global__ void k_qsp_init(double2* __restrict__ psi, int64_t N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
@@ -507,6 +558,28 @@ hhl_status launch_prep_qsp1(const Plan& p, const double* b, double* tree, double
   else k_qsp_scale<double><<<g, kThreads, 0, st>>>(psi, p.N, p.n_c, (double2*)p.d_bs);
   HHL_LAUNCH_CHECK("k_qsp_scale");
   // H on every clock qubit of |0>: every clock row holds the prepared system state
+  const int64_t row_units = p.N * (int64_t)p.amp_bytes() / 16;
+  const int64_t half_units = p.R * row_units;
+  HHL_PROF_BEGIN(st);
+  k_prep_fill<<<grid_for(2 * half_units, kThreads, 152 * 16), kThreads, 0, st>>>((const uint4*)p.d_bs, (uint4*)state,
+                                                                                row_units, half_units);
+  HHL_LAUNCH_CHECK("k_prep_fill");
+  return HHL_OK;
+}
+
+hhl_status launch_prep_qsp2(const Plan& p, const int64_t* idx, const double* val, int64_t count, double2* psi,
+                            void* state, cudaStream_t st) {
+  const int g = grid_for(p.N, kThreads, 152 * 4);
+  HHL_PROF_BEGIN(st);
+  k_qsp_init<<<g, kThreads, 0, st>>>(psi, p.N);
+  HHL_LAUNCH_CHECK("k_qsp_init");
+  HHL_PROF_BEGIN(st);
+  k_qsp2_tree<<<1, 1024, 0, st>>>(idx, val, count, p.n_s, psi, p.d_scal);
+  HHL_LAUNCH_CHECK("k_qsp2_tree");
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64) k_qsp_scale<float><<<g, kThreads, 0, st>>>(psi, p.N, p.n_c, (float2*)p.d_bs);
+  else k_qsp_scale<double><<<g, kThreads, 0, st>>>(psi, p.N, p.n_c, (double2*)p.d_bs);
+  HHL_LAUNCH_CHECK("k_qsp_scale");
   const int64_t row_units = p.N * (int64_t)p.amp_bytes() / 16;
   const int64_t half_units = p.R * row_units;
   HHL_PROF_BEGIN(st);

@@ -66,10 +66,12 @@ def final_field(x_dilated: np.ndarray, k: int, n_points: int) -> np.ndarray:
 
 def solve_one_shot(a, f, u_in, dt: float, m: int, p: int, n_clock: int, scheme: str = "fe",
                    precision: str = "c64", gemm: str = "auto", t0_rule: str = "range_fill",
-                   t0: float = 0.0) -> dict:
+                   t0: float = 0.0, prep: str = "amplitude") -> dict:
     """Plan the dilated system with a signed clock, run the whole circuit on the GPU and read
     the result: ``fields`` (all u^j estimated, (m+p+1) x N_g), ``final`` (u^{m+p}),
-    ``p_success``, the plan ``info`` and the dilated problem (``h``, ``r``)."""
+    ``p_success``, the plan ``info`` and the dilated problem (``h``, ``r``). ``prep``:
+    "amplitude" (hhl_prepare_rhs) or "qsp2" (the sparse gate-level preparation of the
+    right-hand side, whose nonzeros are u_in and the m forcing blocks)."""
     from . import HHLPlan
 
     mat, rhs = one_shot_system(a, f, u_in, dt, m, p, scheme)
@@ -78,7 +80,15 @@ def solve_one_shot(a, f, u_in, dt: float, m: int, p: int, n_clock: int, scheme: 
     plan = HHLPlan(n_s, n_clock, dense=h, precision=precision, gemm=gemm, t0_rule=t0_rule, t0=t0,
                    signed_clock=True)
     st = plan.new_state()
-    plan.prepare_rhs_host(r, st)
+    if prep == "qsp2":
+        import torch
+        nz = np.nonzero(r)[0]
+        plan.prepare_rhs_qsp2(torch.tensor(nz, dtype=torch.int64, device="cuda"),
+                              torch.tensor(r[nz], dtype=torch.float64, device="cuda"), st)
+    elif prep == "amplitude":
+        plan.prepare_rhs_host(r, st)
+    else:
+        raise ValueError(prep)
     plan.apply_circuit(st)
     meas = plan.measure(st)
     info = plan.info

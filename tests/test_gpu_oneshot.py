@@ -99,3 +99,49 @@ def test_one_shot_dilated_system_parity(hhl, scheme, prec, gemm, n, n_c):
     # classical solve of the block system (the oracle's own circuit is within 0.7-2.3%)
     exact = os1.final_slice(np.linalg.solve(big, rhs), n, m, p)
     assert np.abs(res["final"] - exact).max() <= 0.03 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_qsp2_sparse_preparation(hhl, prec):
+    """QSP-2 on a signed sparse vector (9 nonzeros of 2^7, plus one position outside the
+    register, which is ignored): every clock row holds the oracle's QSP-2 state / 2^(n_c/2),
+    the anc = 1 half is zero, and |val| is recorded."""
+    import torch
+    rng = np.random.default_rng(23)
+    n_s, n_c = 7, 4
+    N, R = 1 << n_s, 1 << n_c
+    idx = np.sort(rng.choice(N, size=9, replace=False))
+    val = rng.uniform(0.2, 1.0, 9) * rng.choice([-1.0, 1.0], 9)
+    ref_sys = o.qsp2_prepare(idx, val, n_s)
+    diag, off = o.laplacian_tridiag(N)
+    plan = hhl.HHLPlan(n_s, n_c, diag=diag, off=off, precision=prec)
+    st = plan.new_state()
+    idx_all = np.concatenate([idx, [N + 5]])
+    val_all = np.concatenate([val, [3.0]])
+    plan.prepare_rhs_qsp2(torch.tensor(idx_all, dtype=torch.int64, device="cuda"),
+                          torch.tensor(val_all, dtype=torch.float64, device="cuda"), st)
+    got = _np(st).reshape(2, R, N)
+    for c in range(R):
+        np.testing.assert_allclose(got[0, c], ref_sys / math.sqrt(R), atol=TOL[prec])
+    assert np.abs(got[1]).max() == 0.0
+    out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
+    plan.measure_async(st, out)   # before the circuit: only the recorded |b| and the norm
+    assert out[3].item() == pytest.approx(np.linalg.norm(val), rel=1e-12)
+    assert out[2].item() == pytest.approx(1.0, abs=10 * TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_one_shot_with_qsp2_preparation(hhl, prec):
+    """The one-shot FE system prepared by QSP-2 (its right-hand side has 24 nonzeros in 2^6):
+    the same circuit output as with amplitude encoding."""
+    from paper_2307_00391_gb300 import oneshot as lib1
+    rng = np.random.default_rng(29)
+    n, m, p, n_c = 4, 5, 2, 8
+    a = os1.time_operator(n)
+    f = np.full(n, 8.0)
+    u_in = rng.uniform(0.0, 1.0, n)
+    dt = 0.25 / 25.0
+    r1 = lib1.solve_one_shot(a, f, u_in, dt, m, p, n_c, precision=prec, gemm="simt", prep="amplitude")
+    r2 = lib1.solve_one_shot(a, f, u_in, dt, m, p, n_c, precision=prec, gemm="simt", prep="qsp2")
+    np.testing.assert_allclose(_np(r2["state"]), _np(r1["state"]), atol=TOL[prec])
+    np.testing.assert_allclose(r2["final"], r1["final"], rtol=1e-6 if prec == "c128" else 1e-3)
