@@ -199,7 +199,8 @@ hhl_status hhl_prepare_rhs_host(hhl_plan_t plan, const double* b_re, const doubl
  * significant qubits), and the Hadamard layer on the clock puts that state into every clock
  * row: the anc = 0 half holds |b|-amplitude encoding / 2^(n_c/2), the anc = 1 half is zero.
  * The tree encodes magnitudes: for b_i >= 0 (every flow right-hand side) the result equals
- * hhl_prepare_rhs. b_dev: DEVICE, N real doubles. Uses plan-owned scratch; asynchronous. */
+ * hhl_prepare_rhs. |b| is recorded for the read-outs. b_dev: DEVICE, N real doubles. Uses
+ * plan-owned scratch; asynchronous. */
 hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* state_dev, void* stream);
 
 /* a1, sparse gate-level form (Sec. III and App. C, QSP-2): for a right-hand side with `count`

@@ -134,3 +134,27 @@ def solution_part(x_dilated: np.ndarray, k: int) -> np.ndarray:
 def final_slice(x: np.ndarray, n_points: int, m: int, p: int) -> np.ndarray:
     """u^{m+p}: the last field of the stacked one-shot solution."""
     return x[(m + p) * n_points:(m + p + 1) * n_points]
+
+
+# ---------------------------------------------------------------------------------------
+# Iterative backward Euler (Sec. II: A_be1 u^{j+1} = b_be1 solved once per time step)
+# ---------------------------------------------------------------------------------------
+
+
+def be1_operator(a: np.ndarray, dt: float) -> np.ndarray:
+    """A_be1 = -(A dt - I) = I - A dt (symmetric positive definite for the Laplacian A)."""
+    return np.eye(a.shape[0]) - dt * a
+
+
+def iterative_be(a, f, u0, dt: float, max_steps: int, tol: float, solve) -> tuple[list, list]:
+    """u^{j+1} = solve(A_be1, u^j + f dt) until max_i |u^{j+1} - u^j| <= tol (the classical
+    residue check of the hybrid loop) or max_steps; returns (fields, residues)."""
+    a1 = be1_operator(a, dt)
+    us, res = [np.array(u0, dtype=float)], []
+    for _ in range(max_steps):
+        u_next = solve(a1, us[-1] + dt * np.asarray(f, dtype=float))
+        res.append(float(np.max(np.abs(u_next - us[-1]))))
+        us.append(u_next)
+        if res[-1] <= tol:
+            break
+    return us, res

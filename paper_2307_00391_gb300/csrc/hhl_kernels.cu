@@ -545,6 +545,8 @@ hhl_status launch_prep_qsp1(const Plan& p, const double* b, double* tree, double
     k_qsp_sum<<<grid_for(1LL << l, kThreads, 152 * 4), kThreads, 0, st>>>(l, tree);
     HHL_LAUNCH_CHECK("k_qsp_sum");
   }
+  // the root holds |b|^2: recorded for the read-outs, as hhl_prepare_rhs does
+  HHL_CUDA_TRY(cudaMemcpyAsync(p.d_scal, tree + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
   HHL_PROF_BEGIN(st);
   k_qsp_init<<<g, kThreads, 0, st>>>(psi, p.N);
   HHL_LAUNCH_CHECK("k_qsp_init");

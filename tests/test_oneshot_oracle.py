@@ -171,3 +171,27 @@ def test_qsp2_on_the_one_shot_right_hand_side():
     psi = o.qsp2_prepare(nz, rp[nz], n)
     np.testing.assert_allclose(psi, rp / np.linalg.norm(rp), atol=1e-13)
     assert len(nz) == 8 * 4 and len(o.qsp2_paths(nz, rp[nz], n)) <= len(nz) * n
+
+
+def test_iterative_be_with_exact_solves_is_the_march_and_converges():
+    """The hybrid loop with exact linear solves reproduces the backward-Euler march and stops
+    at the steady channel flow once the residue reaches 1e-6."""
+    n = 16
+    a = os1.time_operator(n)
+    f = np.full(n, 2.0)
+    u0 = np.zeros(n)
+    us, res = os1.iterative_be(a, f, u0, 0.01, 5000, 1e-6, np.linalg.solve)
+    march = os1.be_march(a, f, u0, 0.01, len(us) - 1, 0)
+    np.testing.assert_allclose(np.array(us), np.array(march), rtol=1e-12, atol=1e-14)
+    assert res[-1] <= 1e-6 < res[-2]
+    assert all(r2 < r1 for r1, r2 in zip(res, res[1:]))            # monotone approach
+    y = np.arange(1, n + 1) / (n + 1)
+    np.testing.assert_allclose(us[-1], y * (1 - y), atol=2e-4)     # steady parabola
+    # the HHL read-out as the linear solve (oracle circuit, 10 clock qubits) tracks it
+    def hhl_solve(a1, b):
+        pl = o.plan(a1, 10)
+        psi = o.hhl_circuit(b, 4, pl)
+        v = o.postselect(psi, 4, 10)["v"]
+        return o.velocity(v, np.linalg.norm(b), pl["C"], pl["lam_ub"])
+    uq, rq = os1.iterative_be(a, f, u0, 0.01, 3, 0.0, hhl_solve)
+    np.testing.assert_allclose(np.array(uq), np.array(march[:4]), atol=0.05 * np.abs(march[3]).max())
