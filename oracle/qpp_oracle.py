@@ -1,0 +1,57 @@
+"""Plain FP64 oracle of the quantum post-processing (QPP) of the dissipation rate by a
+linear combination of unitaries (App. D, LCU derivative). TEST INFRASTRUCTURE ONLY: only
+``tests/`` may import it; it shares no code with the library.
+
+The finite-difference derivative of the velocity field with its Dirichlet walls is written
+as the difference of two unitaries on a register of 2N points that holds the interior
+velocities u_1 .. u_N at positions 0 .. N-1, the wall value u_{N+1} at position N, the wall
+value u_0 at position 2N-1 and zeros elsewhere (w): with P the cyclic increment,
+(w - P w)_j = w_j - w_{j-1} gives every forward difference u_{i+1} - u_i, i = 0 .. N, plus two
+spurious terms -u_{N+1} (position N+1) and u_0 (position 2N-1) that involve only the known
+wall values. The LCU circuit (one ancilla, the most significant qubit): prepare the ancilla
+with H (the coefficients 1, 1 of I and -P), apply Z on the ancilla and P controlled by it,
+undo with H; the probability of ancilla 0 is ||(w~ - P w~) / 2||^2 for the normalised w~, so
+sum_i (u_{i+1} - u_i)^2 = 4 p0 |w|^2 - u_0^2 - u_{N+1}^2 and eps = nu / h times that
+(h = 1/(N+1)): the dissipation of Sec. VII read from one probability instead of the whole
+vector. (The paper's QADC / QDAC route to general nonlinear functions is not modelled here.)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import hhl_oracle as o
+
+
+def lcu_register(u: np.ndarray, wall_lo: float, wall_hi: float) -> np.ndarray:
+    """w: u at 0 .. N-1, wall_hi at N, wall_lo at 2N-1, zeros elsewhere."""
+    n = len(u)
+    w = np.zeros(2 * n)
+    w[:n] = u
+    w[n] = wall_hi
+    w[2 * n - 1] = wall_lo
+    return w
+
+
+def lcu_probability(w: np.ndarray) -> float:
+    """Run the LCU circuit gate by gate on [ancilla | data] and return P(ancilla = 0)."""
+    m = int(round(np.log2(len(w))))
+    n_q = m + 1
+    psi = np.zeros(2 * len(w), dtype=np.complex128)
+    psi[:len(w)] = w / np.linalg.norm(w)
+    o.apply_1q(psi, n_q, m, o.H_GATE)
+    o.apply_1q(psi, n_q, m, np.array([[1.0, 0.0], [0.0, -1.0]]))    # Z: the coefficient -1 of P
+    perm = np.zeros((len(w), len(w)))
+    for j in range(len(w)):
+        perm[(j + 1) % len(w), j] = 1.0                               # P |j> = |j + 1 mod 2N>
+    o.apply_register_unitary(psi, n_q, 0, m, perm, control=m)
+    o.apply_1q(psi, n_q, m, o.H_GATE)
+    return float(np.sum(np.abs(psi[:len(w)]) ** 2))
+
+
+def qpp_dissipation(u: np.ndarray, wall_lo: float, wall_hi: float, nu: float) -> tuple[float, float]:
+    """(eps, p0): the dissipation rate from the LCU circuit's ancilla-0 probability."""
+    w = lcu_register(u, wall_lo, wall_hi)
+    p0 = lcu_probability(w)
+    h = 1.0 / (len(u) + 1)
+    sq = 4.0 * p0 * float(w @ w) - wall_lo ** 2 - wall_hi ** 2
+    return nu * sq / h, p0
