@@ -217,6 +217,18 @@ hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* stat
 hhl_status hhl_prepare_rhs_qsp2(hhl_plan_t plan, const int64_t* idx_dev, const double* val_dev, int64_t count,
                                 void* state_dev, void* stream);
 
+/* a7, quantum post-processing form (App. D, the LCU derivative of the QPP protocol): the
+ * denormalised velocity u (as hhl_dissipation reads it from the postselected row) and the
+ * walls are loaded into a register of 2N points, w = (u_1 .. u_N, u_{N+1}, 0 ..., u_0),
+ * normalised; the LCU circuit for (I - P) / 2 (P the cyclic increment; one ancilla: H, Z,
+ * controlled P, H) runs on it gate by gate, and the probability p0 of ancilla 0 gives every
+ * forward difference at once: eps = nu / h (4 p0 |w|^2 - u_0^2 - u_{N+1}^2), h = 1/(N+1), the
+ * same quantity as hhl_dissipation (Sec. VII) read from one probability. *eps and *p0 (may be
+ * NULL) are HOST outputs; the call synchronises the stream. The first call on a plan
+ * allocates its LCU register (6N complex128 of device memory, freed with the plan).
+ * Errors: NULL arguments; HHL_ERR_SINGULAR for a zero register. */
+hhl_status hhl_qpp_dissipation(hhl_plan_t plan, const void* state_dev, double* eps, double* p0, void* stream);
+
 /* a2..a5 - the circuit after state preparation, in place (Sec. IV/VI, standard HHL):
  * clock-bit-controlled U_k for k = 0..n_c-1, inverse QFT on the clock, clock-controlled
  * RY on the ancilla, QFT on the clock, controlled U_k^dagger for k = n_c-1..0, Hadamard on

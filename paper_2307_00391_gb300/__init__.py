@@ -217,6 +217,15 @@ class HHLPlan:
                                              ctypes.c_void_p(state.data_ptr()),
                                              ctypes.c_void_p(_stream_handle(stream))), "hhl_prepare_rhs_qsp2")
 
+    def qpp_dissipation(self, state, stream=None) -> tuple[float, float]:
+        """(eps, p0): the dissipation rate from the LCU post-processing circuit's ancilla-0
+        probability p0 (synchronises the stream)."""
+        eps, p0 = ctypes.c_double(), ctypes.c_double()
+        check(self._lib.hhl_qpp_dissipation(self._h, ctypes.c_void_p(state.data_ptr()), ctypes.byref(eps),
+                                            ctypes.byref(p0), ctypes.c_void_p(_stream_handle(stream))),
+              "hhl_qpp_dissipation")
+        return eps.value, p0.value
+
     def sample(self, state, uniforms_dev, counts_dev, stream=None) -> None:
         """Shots of the postselected system register: counts_dev (torch int64, N) from the
         uniforms in uniforms_dev (torch float64, one per shot)."""

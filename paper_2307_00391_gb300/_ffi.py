@@ -94,6 +94,7 @@ SIGNATURES = [
     ("hhl_sample", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("hhl_prepare_rhs_qsp1", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_prepare_rhs_qsp2", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    ("hhl_qpp_dissipation", c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
     ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_profile_enable", None, [c_int32]),

@@ -391,6 +391,7 @@ struct hhl_plan_s {
   double* d_u = nullptr;   // N doubles + 1 (eps)
   double* d_cdf = nullptr; // N doubles: running sum of the outcome probabilities (shots)
   double* d_bsplit = nullptr;  // 2N doubles: host re / im staging
+  double2* d_qpp = nullptr;    // 6N complex128: the LCU register (two halves) and a spare half
 };
 
 extern "C" {
@@ -657,7 +658,7 @@ void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
   void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
-                  p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_cdf, plan->d_bsplit};
+                  p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_cdf, plan->d_bsplit, plan->d_qpp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   hhl::tc_free(p);
@@ -722,6 +723,27 @@ hhl_status hhl_prepare_rhs_qsp1(hhl_plan_t plan, const double* b_dev, void* stat
   Plan& p = plan->p;
   if (p.N < 2) return fail(HHL_ERR_UNSUPPORTED, "QSP-1 needs at least one system qubit");
   return hhl::launch_prep_qsp1(p, b_dev, plan->d_bsplit, (double2*)p.d_b, state_dev, (cudaStream_t)stream);
+}
+
+hhl_status hhl_qpp_dissipation(hhl_plan_t plan, const void* state_dev, double* eps, double* p0, void* stream) {
+  if (plan == nullptr || state_dev == nullptr || eps == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->d_qpp == nullptr) {  // first call: the plan-owned LCU register
+    HHL_CUDA_TRY(cudaStreamSynchronize(st));
+    HHL_CUDA_TRY(cudaMalloc((void**)&plan->d_qpp, (size_t)6 * p.N * sizeof(double2)));
+    p.workspace_bytes += (uint64_t)6 * p.N * sizeof(double2);
+  }
+  hhl_status s = hhl::launch_qpp_dissipation(p, state_dev, plan->d_qpp, p.d_scal + 5, st);
+  if (s != HHL_OK) return s;
+  double acc[2] = {0.0, 0.0};
+  HHL_CUDA_TRY(cudaMemcpyAsync(acc, p.d_scal + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!(acc[0] > 0.0)) return fail(HHL_ERR_SINGULAR, "the velocity register is zero");
+  const double h = 1.0 / (double)(p.N + 1);
+  *eps = p.nu / h * (4.0 * acc[1] * acc[0] - p.wall_lo * p.wall_lo - p.wall_hi * p.wall_hi);
+  if (p0 != nullptr) *p0 = acc[1];
+  return HHL_OK;
 }
 
 hhl_status hhl_prepare_rhs_qsp2(hhl_plan_t plan, const int64_t* idx_dev, const double* val_dev, int64_t count,

@@ -127,6 +127,7 @@ hhl_status launch_prep_qsp1(const Plan& p, const double* b, double* tree, double
                             cudaStream_t st);
 hhl_status launch_prep_qsp2(const Plan& p, const int64_t* idx, const double* val, int64_t count, double2* psi,
                             void* state, cudaStream_t st);
+hhl_status launch_qpp_dissipation(const Plan& p, const void* state, double2* reg, double* acc, cudaStream_t st);
 hhl_status launch_qft_register(void* state, int n, int lo, int m, bool inverse, int prec, cudaStream_t st);
 // Whole-register QFT (direction 0, output in bit-reversed order) or inverse QFT (direction 1,
 // input in bit-reversed order) of `outer` consecutive n-qubit states.

@@ -403,6 +403,59 @@ __global__ void k_diss_finish(const double* __restrict__ acc, double nu_over_h, 
   if (threadIdx.x == 0 && blockIdx.x == 0) eps[0] = nu_over_h * acc[0];
 }
 
+// ------------------------------------------------------------------------------ QPP (LCU)
+// Post-processing of the dissipation rate by a linear combination of unitaries (App. D):
+// the register [ancilla | data of 2N points] holds w = (u_1 .. u_N, u_{N+1} (wall), 0 ..., u_0
+// (wall)) normalised in its ancilla-0 half; H on the ancilla, Z on it (the coefficient -1),
+// the cyclic increment P of the data controlled by it, H again; P(ancilla = 0) =
+// ||(w - P w) / 2||^2 / |w|^2 holds every forward difference of u. One kernel per gate, FP64.
+template <class R>
+__global__ void k_qpp_load(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N,
+                           const double* __restrict__ scal, double inv_c_lam, double wlo, double whi,
+                           double2* __restrict__ reg0, double2* __restrict__ reg1, double* acc) {
+  const double scale = sqrt(scal[0]) * inv_c_lam;
+  double s[1] = {0.0};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * N; j += (int64_t)gridDim.x * blockDim.x) {
+    const double w = j < N ? scale * (double)S[half + j].x : (j == N ? whi : (j == 2 * N - 1 ? wlo : 0.0));
+    reg0[j] = make_double2(w, 0.0);
+    reg1[j] = make_double2(0.0, 0.0);
+    s[0] += w * w;
+  }
+  block_sum_atomic<1>(s, acc);
+}
+
+__global__ void k_qpp_normalize(double2* __restrict__ reg0, int64_t L, const double* __restrict__ acc) {
+  const double inv = acc[0] > 0.0 ? 1.0 / sqrt(acc[0]) : 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x)
+    reg0[j] = make_double2(reg0[j].x * inv, reg0[j].y * inv);
+}
+
+// H on the ancilla (the most significant qubit): (a, b) -> ((a + b), (a - b)) / sqrt 2.
+__global__ void k_qpp_h(double2* __restrict__ reg0, double2* __restrict__ reg1, int64_t L) {
+  const double r = 0.70710678118654752;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = reg0[j], b = reg1[j];
+    reg0[j] = make_double2(r * (a.x + b.x), r * (a.y + b.y));
+    reg1[j] = make_double2(r * (a.x - b.x), r * (a.y - b.y));
+  }
+}
+
+// Z on the ancilla, then the cyclic increment of the data controlled by it: out[(j+1) mod L] =
+// -reg1[j] (the ancilla-1 half only; out is a separate buffer, the halves are swapped after).
+__global__ void k_qpp_z_ctrl_inc(const double2* __restrict__ reg1, double2* __restrict__ out, int64_t L) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = reg1[j];
+    out[j + 1 == L ? 0 : j + 1] = make_double2(-a.x, -a.y);
+  }
+}
+
+__global__ void k_qpp_p0(const double2* __restrict__ reg0, int64_t L, double* acc) {
+  double s[1] = {0.0};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < L; j += (int64_t)gridDim.x * blockDim.x)
+    s[0] += reg0[j].x * reg0[j].x + reg0[j].y * reg0[j].y;
+  block_sum_atomic<1>(s, acc);
+}
+
 // ------------------------------------------------------------------------------ plan kernels
 // U[n][m] = wgt sum_j e^{i phi_j} (Vr + i Vi)[n][j] conj((Vr + i Vi)[m][j]), FP64.
 __global__ void __launch_bounds__(256) k_expm_eigen(int N, int J, const double* __restrict__ vr,
@@ -566,6 +619,38 @@ hhl_status launch_prep_qsp1(const Plan& p, const double* b, double* tree, double
   k_prep_fill<<<grid_for(2 * half_units, kThreads, 152 * 16), kThreads, 0, st>>>((const uint4*)p.d_bs, (uint4*)state,
                                                                                 row_units, half_units);
   HHL_LAUNCH_CHECK("k_prep_fill");
+  return HHL_OK;
+}
+
+hhl_status launch_qpp_dissipation(const Plan& p, const void* state, double2* reg, double* acc, cudaStream_t st) {
+  const int64_t half = p.R * p.N, L = 2 * p.N;
+  double2 *r0 = reg, *r1 = reg + L, *tmp = reg + 2 * L;
+  const int g = grid_for(L, kThreads, 152 * 4);
+  HHL_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  const double inv_c_lam = 1.0 / (p.C * p.lam_ub);
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64)
+    k_qpp_load<float><<<g, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal, inv_c_lam, p.wall_lo,
+                                              p.wall_hi, r0, r1, acc);
+  else
+    k_qpp_load<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, inv_c_lam, p.wall_lo,
+                                               p.wall_hi, r0, r1, acc);
+  HHL_LAUNCH_CHECK("k_qpp_load");
+  HHL_PROF_BEGIN(st);
+  k_qpp_normalize<<<g, kThreads, 0, st>>>(r0, L, acc);
+  HHL_LAUNCH_CHECK("k_qpp_normalize");
+  HHL_PROF_BEGIN(st);
+  k_qpp_h<<<g, kThreads, 0, st>>>(r0, r1, L);
+  HHL_LAUNCH_CHECK("k_qpp_h");
+  HHL_PROF_BEGIN(st);
+  k_qpp_z_ctrl_inc<<<g, kThreads, 0, st>>>(r1, tmp, L);
+  HHL_LAUNCH_CHECK("k_qpp_z_ctrl_inc");
+  HHL_PROF_BEGIN(st);
+  k_qpp_h<<<g, kThreads, 0, st>>>(r0, tmp, L);
+  HHL_LAUNCH_CHECK("k_qpp_h");
+  HHL_PROF_BEGIN(st);
+  k_qpp_p0<<<g, kThreads, 0, st>>>(r0, L, acc + 1);
+  HHL_LAUNCH_CHECK("k_qpp_p0");
   return HHL_OK;
 }
 
