@@ -471,6 +471,73 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_register_transform(typename 
   else store_block(base, inner, X, Lp, Lc, W, scale, true, rank, m);
 }
 
+// The low register of a whole-register transform (bits [0, m) of contiguous 2^m-amplitude
+// chunks; modes 3 / 4 of k_register_transform) as a persistent kernel: each CTA walks chunks
+// with a stride of the grid, and the next chunk is fetched by asynchronous copies straight
+// into the second of two padded shared-memory buffers (one copy per amplitude, 8 or 16
+// bytes) while the current one is transformed, so loads overlap the radix passes.
+__device__ __forceinline__ void cp_async_amp(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <class R>
+__global__ void __launch_bounds__(kFftThreads, 2) k_lowbits_transform(typename Cx<R>::T* __restrict__ S, int m,
+                                                                     int mode, R scale, long long chunks) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << m, Lp = L + L / 16 + 1;
+  T* t0 = reinterpret_cast<T*>(smem_raw);
+  T* t1 = t0 + 64;
+  T* Xb = t0 + twiddle_entries(m);
+  Xb += (reinterpret_cast<uintptr_t>(Xb) & 15) ? 1 : 0;  // 16-byte aligned buffers for complex128
+  const int Lpa = (Lp + 1) & ~1;
+  fill_twiddles<R>(t0, t1, m);
+  const Twiddle<T> tw{t0, t1};
+  long long c = blockIdx.x;
+  if (c >= chunks) return;  // block-uniform
+  for (int q = threadIdx.x; q < L; q += blockDim.x) cp_async_amp(Xb + pad16(q), S + c * L + q, (int)sizeof(T));
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  int buf = 0;
+  for (; c < chunks; c += gridDim.x) {
+    const long long cn = c + gridDim.x;
+    if (cn < chunks) {
+      T* Xn = Xb + (buf ^ 1) * Lpa;
+      for (int q = threadIdx.x; q < L; q += blockDim.x) cp_async_amp(Xn + pad16(q), S + cn * L + q, (int)sizeof(T));
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();  // the current chunk has landed (and the twiddles are in place)
+    T* X = Xb + buf * Lpa;
+    if (mode == 4) local_stages<T, true, 0>(X, Lp, 1, tw, m, m, false);
+    else local_stages<T, false, 0>(X, Lp, 1, tw, m, m, true);
+    store_block(S + c * L, 1, X, Lp, L, 1, scale, false, 0, m);
+    __syncthreads();  // this buffer is read out before it is refilled
+    buf ^= 1;
+  }
+}
+
+template <class R>
+hhl_status lowbits_transform(void* state, int n, int m, int mode, R scale, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  const int L = 1 << m, Lp = L + L / 16 + 1, Lpa = (Lp + 1) & ~1;
+  const size_t smem = ((size_t)twiddle_entries(m) + 1 + 2 * (size_t)Lpa) * sizeof(T);
+  auto kern = k_lowbits_transform<R>;
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  HHL_CUDA_TRY(cudaGetDevice(&dev));
+  HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kFftThreads, smem));
+  if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "low-bit transform does not fit an SM");
+  const long long chunks = 1LL << (n - m);
+  const long long grid = std::min<long long>(chunks, (long long)occ * sms);
+  HHL_PROF_BEGIN(st);
+  kern<<<(unsigned)grid, kFftThreads, smem, st>>>((T*)state, m, mode, scale, chunks);
+  HHL_LAUNCH_CHECK("k_lowbits_transform");
+  return HHL_OK;
+}
+
 template <class R>
 size_t fft_smem(int m, int cb, int W, int buffers) {
   const size_t sz = sizeof(typename Cx<R>::T);
@@ -566,6 +633,8 @@ hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, 
   size_t smem = 0;
   if (!choose_shape<R>(m, 1LL << lo, 1, &W, &cb, &smem))
     return fail(HHL_ERR_UNSUPPORTED, "register too large for one cluster");
+  if (lo == 0 && cb == 0 && (mode == 3 || mode == 4) && getenv("HHL_LOWBITS_PLAIN") == nullptr)
+    return lowbits_transform<R>(state, n, m, mode, (R)(scale != 0.0 ? scale : 1.0 / sqrt((double)(1LL << m))), st);
   const int64_t cols = (1LL << (n - m)) / W;
   if ((cols << cb) > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "too many columns for one launch");
   const int grid = (int)(cols << cb);
