@@ -73,6 +73,33 @@ struct Twiddle3 {
   }
 };
 
+// Four-level table in shared memory for the 2^n-point twiddles of a whole-register transform
+// (n <= 32): exp(-2 pi i q / 2^n) = T[0][q & 255] T[1][(q >> 8) & 255] T[2][(q >> 16) & 255]
+// T[3][q >> 24], level k holding exp(-2 pi i (j 2^(8k) mod 2^n) / 2^n), j < 256, from FP64
+// sincospi (8 KiB for complex64: the lookups stay in shared memory instead of reaching L2).
+template <class T>
+struct Twiddle4 {
+  const T* t;  // 4 x 256 entries
+  __device__ __forceinline__ T operator()(int q, bool conj) const {
+    const unsigned u = (unsigned)q;
+    T f = cmul(cmul(t[u & 255], t[256 + ((u >> 8) & 255)]), cmul(t[512 + ((u >> 16) & 255)], t[768 + (u >> 24)]));
+    if (conj) f.y = -f.y;
+    return f;
+  }
+};
+
+template <class R>
+__device__ void fill_twiddle4(typename Cx<R>::T* t, int n) {
+  const double inv = 1.0 / (double)(1ULL << n);
+  for (int j = threadIdx.x; j < 1024; j += blockDim.x) {
+    const int k = j >> 8;
+    const unsigned long long e = ((unsigned long long)(j & 255) << (8 * k)) & ((1ULL << n) - 1);
+    double sn = 0.0, cs = 1.0;
+    if (e != 0) sincospi(-2.0 * (double)e * inv, &sn, &cs);  // (levels above n bits are all 1)
+    t[j] = mk<R>((R)cs, (R)sn);
+  }
+}
+
 __host__ __device__ constexpr int twiddle_entries(int m) { return 64 + ((1 << m) / 64 > 1 ? (1 << m) / 64 : 1); }
 
 template <class R>
@@ -691,7 +718,6 @@ struct SplitArgs {
   double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
   float scale_f;       // the same in FP32 (GB300's FP64 pipe is narrow: no per-thread conversions)
   int scaled;          // scale != 1
-  const void* tw3[3];  // whole-register transform: the three-level twiddle tables of 2^m
 };
 
 template <class R>
@@ -928,7 +954,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
 
 // WHOLE: the register is the whole index range [0, lo + m) of each outer block, the tile
 // rows are its bits [lo + b0, lo + b0 + NB) and the twiddles are those of the 2^(lo + m) point
-// transform (three-level global tables); only the DIF and DIT passes are used this way.
+// transform (four-level shared-memory tables); only the DIF and DIT passes are used this way.
 template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
 __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
@@ -938,15 +964,14 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* t0 = reinterpret_cast<T*>(smem_raw);
   T* t1 = t0 + 64;
-  T* Xb = t0 + (WHOLE ? 0 : twiddle_entries(a.m));  // two tile buffers (double buffering), then Y
+  T* Xb = t0 + (WHOLE ? 1024 : twiddle_entries(a.m));  // two tile buffers (double buffering), then Y
   T* Y = Xb + 2 * tile_amps;
   if (!WHOLE && OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
-  using TW = typename std::conditional<WHOLE, Twiddle3<T>, Twiddle<T>>::type;
+  if (WHOLE) fill_twiddle4<R>(t0, a.lo + a.m);  // first read after the barrier of the first tile
+  using TW = typename std::conditional<WHOLE, Twiddle4<T>, Twiddle<T>>::type;
   TW tw;
   if constexpr (WHOLE) {
-    tw.t0 = static_cast<const T*>(a.tw3[0]);
-    tw.t1 = static_cast<const T*>(a.tw3[1]);
-    tw.t2 = static_cast<const T*>(a.tw3[2]);
+    tw.t = t0;
   } else {
     tw.t0 = t0;
     tw.t1 = t1;
@@ -995,7 +1020,7 @@ template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
 hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name) {
   using T = typename Cx<R>::T;
   const size_t tile = ((size_t)1 << (NB + SplitGeom<T>::LW)) * sizeof(T);
-  const size_t smem = (WHOLE ? 0 : (size_t)twiddle_entries(a.m) * sizeof(T)) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
+  const size_t smem = (size_t)(WHOLE ? 1024 : twiddle_entries(a.m)) * sizeof(T) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
   auto kern = k_split_pass<R, OP, FULL, NB, WHOLE>;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
@@ -1565,10 +1590,6 @@ hhl_status whole_register_impl(void* state, int n, int outer, int direction, cud
   a.lo = g;
   a.m = hbits;
   a.scale = 1.0;
-  if (hbits > 0) {
-    hhl_status s = whole_tables<R>(n, a.tw3);
-    if (s != HHL_OK) return s;
-  }
   if (direction == 0) {
     for (int q = ngroups - 1; q >= 0; --q) {
       a.b0 = groups[q].first;
