@@ -62,7 +62,12 @@ typedef enum hhl_status {
 
 typedef enum hhl_matrix_kind {
   HHL_MATRIX_TRIDIAG = 0, /* real symmetric tridiagonal: diag[N], off[N-1] */
-  HHL_MATRIX_DENSE = 1    /* Hermitian, row-major dense_re/dense_im (N <= 256) */
+  HHL_MATRIX_DENSE = 1,   /* Hermitian, row-major dense_re/dense_im (N <= 256) */
+  HHL_MATRIX_UNITARY = 2  /* a unitary Q, row-major dense_re/dense_im (N <= 256): the circuit is
+                             run with U_k = Q^(2^k) (phase estimation of Q itself) and with the
+                             rotation angles of params.theta_table; the QADC - controlled
+                             rotation - QDAC step of the QPP protocol (App. D) is this circuit
+                             with Q an amplitude-estimation iterate. Dense mode only. */
 } hhl_matrix_kind;
 
 typedef enum hhl_t0_rule {
@@ -124,6 +129,8 @@ typedef struct hhl_params {
   int32_t trotter_steps_max; /* 0 = no cap */
   int32_t gemm_impl;         /* hhl_gemm_impl */
   double t0_scale;           /* multiplies the T0 of the rule (0 or 1: unchanged) */
+  const double* theta_table; /* UNITARY: theta_y for y = 0 .. 2^n_c - 1 (HOST, read by
+                                hhl_plan_create); ignored otherwise */
   int32_t signed_clock;      /* 1: read the clock in two's complement, y_s = y - 2^n_c for
                                 y >= 2^(n_c-1), so that an indefinite A (the Hermitian dilation
                                 [[0, M], [M^T, 0]] of a one-shot time-stepping system, App. A

@@ -55,3 +55,63 @@ def qpp_dissipation(u: np.ndarray, wall_lo: float, wall_hi: float, nu: float) ->
     h = 1.0 / (len(u) + 1)
     sq = 4.0 * p0 * float(w @ w) - wall_lo ** 2 - wall_hi ** 2
     return nu * sq / h, p0
+
+
+# ---------------------------------------------------------------------------------------
+# QADC - squaring rotation - QDAC (App. D nonlinear transform): sum_k z_k |k> -> ~ sum_k z_k^2 |k>
+# ---------------------------------------------------------------------------------------
+
+
+def state_prep_unitary(zeta: np.ndarray) -> np.ndarray:
+    """A real orthogonal U_V with U_V |0> = |zeta> (the Householder reflection that swaps e_0
+    and zeta; the identity when zeta = e_0)."""
+    n = len(zeta)
+    v = -np.asarray(zeta, dtype=float).copy()
+    v[0] += 1.0
+    nv = float(v @ v)
+    if nv < 1e-300:
+        return np.eye(n)
+    return np.eye(n) - 2.0 * np.outer(v, v) / nv
+
+
+def amplitude_estimation_iterate(zeta: np.ndarray) -> np.ndarray:
+    """Q = sum_k |k><k|_address (x) G_k on [address | data] (system index d + k N, address the
+    high half): G_k = -U_V S_0 U_V^T S_k, S_0 / S_k the reflections flipping |0> / |k> of the
+    data register. G_k rotates by 2 theta_k in the plane of |zeta>, sin theta_k = |zeta_k|,
+    so phase estimation of Q from |k>|zeta> reads +- theta_k / pi (amplitude estimation,
+    the analog-to-digital conversion of the amplitudes)."""
+    n = len(zeta)
+    uv = state_prep_unitary(zeta)
+    s0 = np.eye(n)
+    s0[0, 0] = -1.0
+    q = np.zeros((n * n, n * n))
+    for k in range(n):
+        sk = np.eye(n)
+        sk[k, k] = -1.0
+        q[k * n:(k + 1) * n, k * n:(k + 1) * n] = -uv @ s0 @ uv.T @ sk
+    return q
+
+
+def squaring_angles(n_clock: int, c: float) -> np.ndarray:
+    """theta_y with sin(theta_y / 2) = c sin^2(pi y / 2^n_c): the ancilla amplitude becomes
+    c sin^2 theta_k = c zeta_k^2 for either estimated phase +- theta_k / pi."""
+    y = np.arange(1 << n_clock)
+    return 2.0 * np.arcsin(c * np.sin(np.pi * y / (1 << n_clock)) ** 2)
+
+
+def qadc_square(zeta: np.ndarray, n_clock: int, c: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """Run the HHL-shaped circuit (address uniform, data |zeta>; phase estimation of Q, the
+    squaring rotation, the inverse) gate by gate in the oracle; return (the final state, the
+    postselected [address | data] vector)."""
+    n = len(zeta)
+    a = int(round(np.log2(n)))
+    q = amplitude_estimation_iterate(zeta)
+    evolutions = []
+    u = q.copy()
+    for _ in range(n_clock):
+        evolutions.append(u.astype(np.complex128))
+        u = u @ u
+    b = np.kron(np.full(n, 1.0 / np.sqrt(n)), np.asarray(zeta, dtype=float))
+    pl = dict(n_clock=n_clock, theta=squaring_angles(n_clock, c), t0=2.0 * np.pi)
+    psi = o.hhl_circuit(b, 2 * a, pl, evolutions=evolutions)
+    return psi, o.postselect(psi, 2 * a, n_clock)["v"]

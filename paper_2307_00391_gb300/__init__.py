@@ -77,18 +77,24 @@ class HHLPlan:
                  precision: str = "c64", t0_rule: str = "range_fill", t0: float = 0.0,
                  t0_convention: str = "total", C: float = 0.0, expm: str = "dense",
                  full_uncompute: bool = False, trotter_dt: float = 1.0, trotter_steps_max: int = 0,
-                 gemm: str = "auto", nu: float = 0.1, walls=(0.0, 0.0), signed_clock: bool = False):
+                 gemm: str = "auto", nu: float = 0.1, walls=(0.0, 0.0), signed_clock: bool = False,
+                 unitary=None, theta_table=None):
+        """``unitary`` (with ``theta_table``, 2^n_clock angles): phase estimation of that unitary
+        itself (U_k = Q^(2^k)) with the given ancilla rotation per clock value, in place of
+        exp(i Ahat t_k) and the eigenvalue inversion."""
         lib = load()
         self._lib = lib
         self._keep = []
         prob = _ffi.Problem()
         prob.n_sys_qubits = n_sys_qubits
+        if unitary is not None:
+            dense = unitary
         if dense is not None:
             dense = np.asarray(dense)
             re = np.ascontiguousarray(dense.real, dtype=np.float64)
             im = np.ascontiguousarray(dense.imag, dtype=np.float64) if np.iscomplexobj(dense) else None
             self._keep += [re, im]
-            prob.kind = _ffi.MATRIX_DENSE
+            prob.kind = _ffi.MATRIX_UNITARY if unitary is not None else _ffi.MATRIX_DENSE
             prob.dense_re = _dptr(re)
             prob.dense_im = _dptr(im)
         else:
@@ -114,6 +120,10 @@ class HHLPlan:
         par.trotter_steps_max = trotter_steps_max
         par.gemm_impl = _GEMM[gemm]
         par.signed_clock = int(signed_clock)
+        if theta_table is not None:
+            th = np.ascontiguousarray(theta_table, dtype=np.float64)
+            self._keep.append(th)
+            par.theta_table = _dptr(th)
         h = ctypes.c_void_p()
         check(lib.hhl_plan_create(ctypes.byref(prob), ctypes.byref(par), ctypes.byref(h)), "hhl_plan_create")
         self._h = h

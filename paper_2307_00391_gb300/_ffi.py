@@ -12,7 +12,7 @@ HHL_OK = 0
 STATUS_NAMES = {0: "HHL_OK", 1: "HHL_ERR_INVALID_ARG", 2: "HHL_ERR_NOT_HERMITIAN", 3: "HHL_ERR_SINGULAR",
                 4: "HHL_ERR_OOM", 5: "HHL_ERR_CUDA", 6: "HHL_ERR_TIMEOUT", 7: "HHL_ERR_NUMERIC",
                 8: "HHL_ERR_UNSUPPORTED"}
-MATRIX_TRIDIAG, MATRIX_DENSE = 0, 1
+MATRIX_TRIDIAG, MATRIX_DENSE, MATRIX_UNITARY = 0, 1, 2
 T0_USER, T0_POWER_LAW, T0_RANGE_FILL = 0, 1, 2
 T0_TOTAL, T0_PER_UNIT = 0, 1
 EXPM_DENSE, EXPM_TROTTER = 0, 1
@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n_clock", c_int32), ("t0_rule", c_int32), ("t0_convention", c_int32),
                 ("precision", c_int32), ("t0", c_double), ("C", c_double), ("expm_mode", c_int32),
                 ("full_uncompute", c_int32), ("trotter_dt", c_double), ("trotter_steps_max", c_int32),
-                ("gemm_impl", c_int32), ("t0_scale", c_double), ("signed_clock", c_int32)]
+                ("gemm_impl", c_int32), ("t0_scale", c_double), ("theta_table", _DP), ("signed_clock", c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

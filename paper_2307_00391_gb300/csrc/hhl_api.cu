@@ -179,7 +179,8 @@ bool is_toeplitz(const double* d, const double* o, int64_t n) {
 
 hhl_status validate(const hhl_problem* pr, const hhl_params* pa) {
   if (pr == nullptr || pa == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL problem or params");
-  if (pr->kind != HHL_MATRIX_TRIDIAG && pr->kind != HHL_MATRIX_DENSE) return fail(HHL_ERR_INVALID_ARG, "bad matrix kind");
+  if (pr->kind != HHL_MATRIX_TRIDIAG && pr->kind != HHL_MATRIX_DENSE && pr->kind != HHL_MATRIX_UNITARY)
+    return fail(HHL_ERR_INVALID_ARG, "bad matrix kind");
   if (pa->expm_mode != HHL_EXPM_DENSE && pa->expm_mode != HHL_EXPM_TROTTER) return fail(HHL_ERR_INVALID_ARG, "bad expm_mode");
   if (pa->precision != HHL_PREC_C64 && pa->precision != HHL_PREC_C128) return fail(HHL_ERR_INVALID_ARG, "bad precision");
   if (pa->n_clock < 1 || pa->n_clock > 13) return fail(HHL_ERR_INVALID_ARG, "n_clock must be in 1..13");
@@ -219,13 +220,31 @@ hhl_status validate(const hhl_problem* pr, const hhl_params* pa) {
       if (!std::isfinite(pr->dense_re[i]) || !std::isfinite(im)) return fail(HHL_ERR_NUMERIC, "non-finite A entry");
       amax = std::max(amax, std::hypot(pr->dense_re[i], im));
     }
-    for (int64_t i = 0; i < N; ++i)
-      for (int64_t j = 0; j < N; ++j) {
-        const double re1 = pr->dense_re[i * N + j], re2 = pr->dense_re[j * N + i];
-        const double im1 = pr->dense_im ? pr->dense_im[i * N + j] : 0.0;
-        const double im2 = pr->dense_im ? pr->dense_im[j * N + i] : 0.0;
-        if (std::hypot(re1 - re2, im1 + im2) > 1e-12 * amax) return fail(HHL_ERR_NOT_HERMITIAN, "A is not Hermitian");
-      }
+    if (pr->kind == HHL_MATRIX_UNITARY) {
+      // Q Q^dagger = I to 1e-10, and a finite angle per clock value
+      for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+          double sr = 0.0, si = 0.0;
+          for (int64_t k = 0; k < N; ++k) {
+            const double ar = pr->dense_re[i * N + k], ai = pr->dense_im ? pr->dense_im[i * N + k] : 0.0;
+            const double br = pr->dense_re[j * N + k], bi = pr->dense_im ? -pr->dense_im[j * N + k] : 0.0;
+            sr += ar * br - ai * bi;
+            si += ar * bi + ai * br;
+          }
+          if (std::hypot(sr - (i == j ? 1.0 : 0.0), si) > 1e-10) return fail(HHL_ERR_INVALID_ARG, "Q is not unitary");
+        }
+      if (pa->theta_table == nullptr) return fail(HHL_ERR_INVALID_ARG, "a UNITARY plan needs theta_table");
+      for (int64_t y = 0; y < (1LL << pa->n_clock); ++y)
+        if (!std::isfinite(pa->theta_table[y])) return fail(HHL_ERR_NUMERIC, "non-finite theta_table entry");
+    } else {
+      for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+          const double re1 = pr->dense_re[i * N + j], re2 = pr->dense_re[j * N + i];
+          const double im1 = pr->dense_im ? pr->dense_im[i * N + j] : 0.0;
+          const double im2 = pr->dense_im ? pr->dense_im[j * N + i] : 0.0;
+          if (std::hypot(re1 - re2, im1 + im2) > 1e-12 * amax) return fail(HHL_ERR_NOT_HERMITIAN, "A is not Hermitian");
+        }
+    }
   }
   return HHL_OK;
 }
@@ -328,6 +347,15 @@ hhl_status plan_host(const hhl_problem* prob, const hhl_params* params, Plan& p,
   }
   if (!(lub > 0.0)) { return fail(HHL_ERR_SINGULAR, "A is zero"); }
   p.lam_ub = lub;
+  if (prob->kind == HHL_MATRIX_UNITARY) {
+    // phase estimation of Q itself: no spectrum to plan, the angles are the caller's
+    p.lam_ub = 1.0;
+    p.lam_min = p.lam_max = p.kappa = 1.0;
+    p.t0 = 2.0 * kPi;
+    p.C = 1.0;
+    p.theta.assign(params->theta_table, params->theta_table + p.R);
+    return HHL_OK;
+  }
 
   const bool dense = p.expm_mode == HHL_EXPM_DENSE;
   if (!dense && !(prob->kind == HHL_MATRIX_TRIDIAG && is_toeplitz(prob->diag, prob->off, N)))
@@ -561,6 +589,46 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       if (d_g) cudaFree(d_g);
     };
     hhl_status ts = HHL_OK;
+    if (prob->kind == HHL_MATRIX_UNITARY) {
+      // U_k = Q^(2^k) by repeated squaring in FP64 on the host, then the same operands
+      ts = dev_alloc((void**)&d_u, mat * sizeof(double2), &tmp_bytes);
+      if (ts != HHL_OK) { cudaStreamDestroy(st); hhl_plan_destroy(h); return ts; }
+      std::vector<double> qr(mat), qi(mat), tr(mat), ti(mat), up(2 * mat);
+      for (size_t e = 0; e < mat; ++e) {
+        qr[e] = prob->dense_re[e];
+        qi[e] = prob->dense_im ? prob->dense_im[e] : 0.0;
+      }
+      cudaError_t ue = cudaSuccess;
+      for (int k = 0; k < p.n_c && ue == cudaSuccess; ++k) {
+        if (k > 0) {
+          for (int64_t i = 0; i < N; ++i)
+            for (int64_t j = 0; j < N; ++j) {
+              double sr = 0.0, si = 0.0;
+              for (int64_t l = 0; l < N; ++l) {
+                sr += qr[i * N + l] * qr[l * N + j] - qi[i * N + l] * qi[l * N + j];
+                si += qr[i * N + l] * qi[l * N + j] + qi[i * N + l] * qr[l * N + j];
+              }
+              tr[i * N + j] = sr;
+              ti[i * N + j] = si;
+            }
+          qr.swap(tr);
+          qi.swap(ti);
+        }
+        for (size_t e = 0; e < mat; ++e) {
+          up[2 * e] = qr[e];
+          up[2 * e + 1] = qi[e];
+        }
+        ue = cudaMemcpyAsync(d_u, up.data(), 2 * mat * sizeof(double), cudaMemcpyHostToDevice, st);
+        hhl_status ks = ue == cudaSuccess ? (p.gemm_impl == HHL_GEMM_SIMT ? launch_store_operands(p, d_u, k, st)
+                                                                         : tc_prepare_operands(p, d_u, k, st))
+                                          : HHL_OK;
+        if (ks != HHL_OK) { cudaStreamSynchronize(st); cudaFree(d_u); cudaStreamDestroy(st); hhl_plan_destroy(h); return ks; }
+        if (ue == cudaSuccess) ue = cudaStreamSynchronize(st);  // the host buffer is reused next k
+      }
+      cudaFree(d_u);
+      if (ue != cudaSuccess) { cudaStreamDestroy(st); hhl_plan_destroy(h); return cuda_fail(ue, "plan powers of Q"); }
+      p.gemm_flops = (double)(p.full ? 3 : 2) * p.n_c * 8.0 * (double)(p.R / 2) * (double)N * (double)N;
+    } else {
     if (!eg.toeplitz) ts = dev_alloc((void**)&d_vr, (size_t)N * J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK && !eg.vi.empty()) ts = dev_alloc((void**)&d_vi, (size_t)N * J * sizeof(double), &tmp_bytes);
     if (ts == HHL_OK) ts = dev_alloc((void**)&d_c, (size_t)J * sizeof(double), &tmp_bytes);
@@ -603,6 +671,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
     if (ce != cudaSuccess) { cudaStreamDestroy(st); hhl_plan_destroy(h); return cuda_fail(ce, "plan exponentials"); }
     const int mult = p.full ? 3 : 2;
     p.gemm_flops = (double)mult * p.n_c * 8.0 * (double)(p.R / 2) * (double)N * (double)N;
+    }
   } else {
     // Strang blocks of exp(i s M) for the Toeplitz Ahat: E blocks [[d, o], [o, d]] on
     // pairs (2i, 2i+1) and O blocks [[0, o], [o, 0]] on pairs (2i+1, 2i+2).

@@ -34,3 +34,37 @@ def test_lcu_probability_brute_force():
     perm = np.roll(np.eye(16), 1, axis=0)
     d = (np.eye(16) - perm) / 2 @ (w / np.linalg.norm(w))
     assert q.lcu_probability(w) == pytest.approx(float(d @ d), rel=1e-12)
+
+
+def test_amplitude_estimation_iterate_eigenphases():
+    """Each block G_k of Q rotates by 2 theta_k with sin theta_k = |zeta_k| (eigenvalues
+    e^{+-2 i theta_k} on the plane of |zeta>, +-1 elsewhere); U_V |0> = |zeta>."""
+    rng = np.random.default_rng(4)
+    z = rng.uniform(0.1, 1.0, 4)
+    z /= np.linalg.norm(z)
+    np.testing.assert_allclose(q.state_prep_unitary(z)[:, 0], z, atol=1e-15)
+    qq = q.amplitude_estimation_iterate(z)
+    np.testing.assert_allclose(qq @ qq.T, np.eye(16), atol=1e-13)
+    for k in range(4):
+        ev = np.linalg.eigvals(qq[4 * k:4 * k + 4, 4 * k:4 * k + 4])
+        ang = np.sort(np.abs(np.angle(ev)))
+        want = 2 * np.arcsin(z[k])
+        assert np.min(np.abs(ang - want)) < 1e-12
+
+
+def test_qadc_square_is_exact_on_the_clock_grid():
+    """zeta = (sin pi/8, sin 3pi/8): both phases sit on the 4-bit clock grid, so the
+    postselected state is exactly (1/sqrt 2) sum_k zeta_k^2 |k> (x) |zeta>."""
+    z = np.array([np.sin(np.pi / 8), np.sin(3 * np.pi / 8)])
+    _, v = q.qadc_square(z, 4, c=1.0)
+    want = np.kron(z ** 2 / np.sqrt(2.0), z)
+    np.testing.assert_allclose(v, want, atol=1e-12)
+
+
+def test_qadc_square_off_grid_converges():
+    rng = np.random.default_rng(6)
+    z = rng.uniform(0.2, 1.0, 4)
+    z /= np.linalg.norm(z)
+    _, v = q.qadc_square(z, 8, c=1.0)
+    marg = v.reshape(4, 4) @ z             # project the data register on |zeta>
+    np.testing.assert_allclose(marg.real, z ** 2 / 2.0, atol=0.02)
