@@ -601,15 +601,22 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       cudaError_t ue = cudaSuccess;
       for (int k = 0; k < p.n_c && ue == cudaSuccess; ++k) {
         if (k > 0) {
+          // row i of Q^2 accumulates row l of Q scaled by Q[i][l], l in increasing order
+          // (unit-stride inner loop; the zero entries of a block-structured Q are skipped)
+          std::fill(tr.begin(), tr.end(), 0.0);
+          std::fill(ti.begin(), ti.end(), 0.0);
           for (int64_t i = 0; i < N; ++i)
-            for (int64_t j = 0; j < N; ++j) {
-              double sr = 0.0, si = 0.0;
-              for (int64_t l = 0; l < N; ++l) {
-                sr += qr[i * N + l] * qr[l * N + j] - qi[i * N + l] * qi[l * N + j];
-                si += qr[i * N + l] * qi[l * N + j] + qi[i * N + l] * qr[l * N + j];
+            for (int64_t l = 0; l < N; ++l) {
+              const double ar = qr[i * N + l], ai = qi[i * N + l];
+              if (ar == 0.0 && ai == 0.0) continue;
+              const double* br = &qr[l * N];
+              const double* bi = &qi[l * N];
+              double* cr = &tr[i * N];
+              double* ci = &ti[i * N];
+              for (int64_t j = 0; j < N; ++j) {
+                cr[j] += ar * br[j] - ai * bi[j];
+                ci[j] += ar * bi[j] + ai * br[j];
               }
-              tr[i * N + j] = sr;
-              ti[i * N + j] = si;
             }
           qr.swap(tr);
           qi.swap(ti);
