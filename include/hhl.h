@@ -67,7 +67,8 @@ typedef enum hhl_matrix_kind {
                              run with U_k = Q^(2^k) (phase estimation of Q itself) and with the
                              rotation angles of params.theta_table; the QADC - controlled
                              rotation - QDAC step of the QPP protocol (App. D) is this circuit
-                             with Q an amplitude-estimation iterate. Dense mode only. */
+                             with Q an amplitude-estimation iterate (on the data register, or
+                             on the swap-test register of STEPS 1-3). Dense mode only. */
 } hhl_matrix_kind;
 
 typedef enum hhl_t0_rule {

@@ -17,7 +17,8 @@ the address register carries c z_k^2 / sqrt(2^a) (with the data back in |zeta>).
 data register ua, a clone a1 of the address and a swap-test qubit a2 (system index
 ua + N a1 + N^2 a2 + 2 N^2 s, 3a + 1 qubits); the swap test of ua against a1 puts weight
 sin^2(pi beta) = (1 + z_s^2) / 2 on a2 = 0, phase estimation of its amplitude-estimation
-iterate reads beta or 1 - beta, and the rotation uses z_s^2 = 2 sin^2(pi beta) - 1.
+iterate reads beta or 1 - beta, and the rotation uses z_s^2 = 2 sin^2(pi beta) - 1. Its
+system register holds 2 N^3 amplitudes, so the dense UNITARY plan (at most 256) takes N <= 4.
 """
 from __future__ import annotations
 
