@@ -851,7 +851,7 @@ __device__ __forceinline__ void tile_issue(T* X, const T* base, long long row_un
   for (int k = 0; k < per_thread; ++k) split_cp_async16(dst + k * kSplitThreads, src + k * step);
 }
 
-template <class T, int NB, class S>
+template <class T, int NB, bool CS = false, class S>
 __device__ __forceinline__ void tile_store(T* base, const T* X, long long row_units, long long row0, int b0, S scale,
                                            bool scaled) {
   constexpr int upr = kSplitSegBytes / 16;
@@ -869,7 +869,8 @@ __device__ __forceinline__ void tile_store(T* base, const T* X, long long row_un
 #pragma unroll
       for (int q = 0; q < per; ++q) t[q] = cscale(t[q], scale);
     }
-    dst[k * step] = v;
+    if constexpr (CS) __stcs(dst + k * step, v);  // evict-first in L2
+    else dst[k * step] = v;
   }
 }
 
@@ -898,7 +899,7 @@ __device__ __forceinline__ TilePos tile_pos(const SplitArgs& a, long long t) {
 
 // The work on one landed tile of a split pass (transform stages, the pass's epilogue and the
 // store back), shared by the streaming passes and the L2-staged group passes below.
-template <class R, int OP, bool FULL, int NB, bool WHOLE, class TW>
+template <class R, int OP, bool FULL, int NB, bool WHOLE, bool CS = false, class TW>
 __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q, typename Cx<R>::T* X,
                                            typename Cx<R>::T* Y, const TW& tw, int mt, long long row_units) {
   using T = typename Cx<R>::T;
@@ -909,16 +910,16 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
     // whole-register QFT (DIF, + sign) or inverse QFT (DIT, - sign)
     if (OP == kSplitDif) tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, mt, tw, true, q.inner_base, a.lo);
     else tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, mt, tw, false, q.inner_base, a.lo);
-    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+    tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitDif) {
     tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
-    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+    tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitDit) {
     tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, a.m, tw, true);
-    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, (R)1, false);
+    tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitHad) {
     tile_stages<T, NB, false, 1>(X, a.b0, q.lo_fixed, a.m, tw, false);
-    tile_store<T, NB>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
+    tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
   } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
     tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
     const R s = split_scale<R>(a);
@@ -947,8 +948,8 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
     __syncthreads();
     tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
     if (FULL) tile_stages<T, NB, true, 0>(Y, 0, 0, a.m, tw, true);
-    tile_store<T, NB>(dst, X, row_units, q.row0, 0, (R)1, false);
-    if (FULL) tile_store<T, NB>(reinterpret_cast<T*>(cos_out), Y, row_units, q.row0, 0, (R)1, false);
+    tile_store<T, NB, CS>(dst, X, row_units, q.row0, 0, (R)1, false);
+    if (FULL) tile_store<T, NB, CS>(reinterpret_cast<T*>(cos_out), Y, row_units, q.row0, 0, (R)1, false);
   }
 }
 
@@ -1061,7 +1062,9 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
 // the next) separates the passes. The intermediate results stay in L2 as long as the groups
 // in flight fit there, so the launch grid is bounded by an L2 budget, not only by occupancy;
 // then the clock block reads the anc = 0 half once and writes both halves once, and the
-// Hadamard layer reads and writes its half once.
+// Hadamard layer reads and writes its half once. The last pass of a group stores with the
+// evict-first cache operator (st.global.cs): its columns are finished, so they should leave
+// L2 before the intermediates of the groups still in flight.
 struct GroupArgs {
   SplitArgs ph[3];   // the passes, in order (finished by split_finish)
   long long groups;  // column blocks: 2^log_cb
@@ -1073,7 +1076,7 @@ __device__ __forceinline__ void cluster_barrier() {
 
 // One pass over the tiles of group ib: CTA `rank` of the cluster takes the group's tiles
 // rank, rank + G, ... (double-buffered as in k_split_pass).
-template <class R, int OP, bool FULL, int NB>
+template <class R, int OP, bool FULL, int NB, bool CS = false>
 __device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, int rank, int G,
                                             typename Cx<R>::T* Xb, typename Cx<R>::T* Y,
                                             const Twiddle<typename Cx<R>::T>& tw) {
@@ -1102,7 +1105,7 @@ __device__ __forceinline__ void group_phase(const SplitArgs& a, long long ib, in
     split_cp_async_wait1();
     __syncthreads();  // the current tile has landed for every thread
     const TilePos q = tile_pos<NB, LW>(a, ib + (u << a.log_cb));
-    split_tile<R, OP, FULL, NB, false>(a, q, Xb + buf * tile_amps, Y, tw, a.m, row_units);
+    split_tile<R, OP, FULL, NB, false, CS>(a, q, Xb + buf * tile_amps, Y, tw, a.m, row_units);
     __syncthreads();  // this buffer is read out before it is refilled
     buf ^= 1;
   }
@@ -1137,11 +1140,11 @@ __global__ void __launch_bounds__(kSplitThreads, 3) k_group_pass(GroupArgs g) {
       cluster_barrier();
       group_phase<R, kSplitMid, FULL, NBL>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
       cluster_barrier();
-      group_phase<R, kSplitDit, false, NBH>(g.ph[2], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitDit, false, NBH, true>(g.ph[2], ib, (int)rank, (int)G, Xb, Y, tw);
     } else {
       group_phase<R, kSplitHad, false, NBH>(g.ph[0], ib, (int)rank, (int)G, Xb, Y, tw);
       cluster_barrier();
-      group_phase<R, kSplitHad, false, NBL>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
+      group_phase<R, kSplitHad, false, NBL, true>(g.ph[1], ib, (int)rank, (int)G, Xb, Y, tw);
     }
     // the next group touches other columns only: no barrier before its first pass
   }
