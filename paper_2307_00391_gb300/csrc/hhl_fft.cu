@@ -579,11 +579,12 @@ bool choose_shape(int m, int64_t limit, int buffers, int* W_out, int* cb_out, si
   // 32-byte row segments (W = 4 complex64 / 2 complex128): measured best on GB300 for the
   // 12- and 13-qubit clocks; wider blocks need larger clusters, whose barriers cost more.
   int W = (int)std::min<int64_t>(32 / (int)sizeof(typename Cx<R>::T), limit);
-  // tuning override "W,cb" (both powers of two; used when it fits the shared-memory cap)
+  // tuning override "W,cb" (W a power of two of at least one 16-byte unit per row, as the
+  // rotation of the clock block needs; used when it fits the shared-memory cap)
   if (const char* env = getenv("HHL_FFT_SHAPE")) {
     int w = 0, c = -1;
-    if (sscanf(env, "%d,%d", &w, &c) == 2 && w >= 1 && w <= W && (w & (w - 1)) == 0 && c >= 0 && c <= 3 && c < m &&
-        fft_smem<R>(m, c, w, buffers) <= kFftSmemCap) {
+    if (sscanf(env, "%d,%d", &w, &c) == 2 && w * (int)sizeof(typename Cx<R>::T) >= 16 && w <= W &&
+        (w & (w - 1)) == 0 && c >= 0 && c <= 3 && c < m && fft_smem<R>(m, c, w, buffers) <= kFftSmemCap) {
       *W_out = w;
       *cb_out = c;
       *smem_out = fft_smem<R>(m, c, w, buffers);
@@ -1208,9 +1209,6 @@ hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const
   long long n_cl = std::min<long long>(max_clusters, std::max<long long>(1, ((long long)budget << 20) / group_bytes));
   n_cl = std::min<long long>(n_cl, g.groups);
   cfg.gridDim = dim3((unsigned)(n_cl * G));
-  if (getenv("HHL_GROUP_VERBOSE") != nullptr)
-    fprintf(stderr, "%s: m=%d G=%d clusters=%lld (max %d) groups=%lld smem=%zu\n", name, m, G, n_cl, max_clusters,
-            g.groups, smem);
   GroupArgs ga = g;
   void* args[1] = {&ga};
   HHL_PROF_BEGIN(st);
