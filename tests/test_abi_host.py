@@ -132,6 +132,23 @@ def test_null_handles_and_qft_arguments(lib):
     assert lib.hhl_apply_qft(buf, 20, 0, 14, 0, 32, None) == 1
     assert lib.hhl_apply_qft(buf, 20, 0, 4, 0, 33, None) == 1
     assert lib.hhl_state_bytes(None) == 0
+    assert lib.hhl_sample(None, None, None, 0, None, None) == 1
+
+
+def test_empty_and_negative_counts_are_rejected(lib):
+    """An empty batch and a negative shot count are argument errors, found before any device
+    work."""
+    from paper_2307_00391_gb300 import _ffi
+    par = _ffi.Params()
+    lib.hhl_params_default(ctypes.byref(par))
+    prob, keep = _tridiag(3)
+    out = ctypes.c_void_p()
+    assert lib.hhl_batch_create(ctypes.byref(prob), ctypes.byref(par), 0, None, 0, ctypes.byref(out)) == 1
+    assert lib.hhl_batch_create(ctypes.byref(prob), ctypes.byref(par), -3, None, 0, ctypes.byref(out)) == 1
+    assert not out.value
+    fake = ctypes.c_void_p(1)
+    assert lib.hhl_sample(fake, fake, None, -1, fake, None) == 1
+    assert lib.hhl_sample(fake, fake, None, 5, fake, None) == 1      # shots without uniforms
 
 
 def test_host_fault_injection_plan():

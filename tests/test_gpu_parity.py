@@ -140,6 +140,8 @@ def test_shots_match_the_oracle_sampler(hhl, prec):
     margin = 1e-12 if prec == "c128" else 1e-4
     near = np.min(np.abs(u[:, None] - cdf[None, :]), axis=1) < margin
     assert np.abs(got - ref).sum() <= 2 * int(near.sum()), (int(near.sum()), np.abs(got - ref).sum())
+    plan.sample(st, torch.empty(0, dtype=torch.float64, device="cuda"), counts)   # zero shots
+    assert int(counts.abs().sum().item()) == 0
     # the GPU sampler on a state it did not compute: exact
     psi = np.zeros(2 << (n_s + n_c), dtype=np.complex128)
     vv = np.sqrt(np.arange(1, (1 << n_s) + 1, dtype=np.float64)) * np.exp(1j * np.arange(1 << n_s))
