@@ -293,7 +293,7 @@ def _oracle_trotter_sample(wl: dict, budget_s: float) -> dict:
     for q in range(n_c):
         o.apply_1q(hcol, n_c, q, o.H_GATE)
     t_h = time.perf_counter() - tt
-    # system rows through each U_k, round after round while the budget lasts (mean per k)
+    # system rows through each U_k, repeatedly while the budget lasts (mean per k)
     t_sum, t_cnt = {}, {}
     psi = np.zeros(2 * N, dtype=np.complex128)
     rounds = 0

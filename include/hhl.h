@@ -57,7 +57,7 @@ typedef enum hhl_status {
   HHL_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
   HHL_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
   HHL_ERR_NUMERIC = 7,       /* a non-finite value where a finite one is required */
-  HHL_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement */
+  HHL_ERR_UNSUPPORTED = 8    /* a valid request the library does not implement */
 } hhl_status;
 
 typedef enum hhl_matrix_kind {
