@@ -502,11 +502,13 @@ def test_tcgen05_matches_simt_gemm(hhl):
 
 
 @pytest.mark.slow
-def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
-    """The 32-qubit Poiseuille workload (N = 2^18, n_c = 13, complex64, Strang-Trotter U_k, the
-    bench's step bounds). After the controlled products, clock row 0 still holds
-    bhat / 2^(n_c/2) and clock row 2^k holds U_k bhat / 2^(n_c/2); the oracle computes each
-    sampled U_k bhat with its own gate sequence on one system vector."""
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl, prec):
+    """The 32-qubit Poiseuille workload (N = 2^18, n_c = 13, Strang-Trotter U_k, the bench's
+    step bounds; complex64 as benched, complex128 the 64 GiB maximum). After the controlled
+    products, clock row 0 still holds bhat / 2^(n_c/2) and clock row 2^k holds
+    U_k bhat / 2^(n_c/2); the oracle computes each sampled U_k bhat with its own gate sequence
+    on one system vector."""
     import torch
     from synth_inputs import rhs
     n_s, n_c = 18, 13
@@ -514,7 +516,10 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
     diag, off = o.laplacian_tridiag(N)
     b = rhs("poiseuille", N)
     dt, r_max = 1024.0, 8
-    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64", expm="trotter", trotter_dt=dt, trotter_steps_max=r_max)
+    # (absolute / relative bound on the sampled U_k rows, bound on transformed columns per unit
+    # of their largest input amplitude)
+    row_abs, row_rel, col = (1e-5, 1e-4, 2e-5) if prec == "c64" else (1e-10, 1e-9, 1e-10)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, expm="trotter", trotter_dt=dt, trotter_steps_max=r_max)
     st = plan.new_state()
     plan.prepare_rhs_host(b, st)
     plan.apply_stage("qpe_u", st)
@@ -523,7 +528,7 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
     t0 = o.t0_total("range_fill", n_c)
     assert plan.info["t0"] == pytest.approx(t0, rel=1e-12)
     bhat = b / np.linalg.norm(b) / math.sqrt(R)
-    np.testing.assert_allclose(_np(st[:N]), bhat, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(_np(st[:N]), bhat, rtol=1e-6 if prec == "c64" else 1e-13, atol=0)
     for k in (0, 4, 9, 11, 12):
         t_k = t0 * (1 << k) / R
         r = o.trotter_steps(t_k, dt, r_max)
@@ -532,11 +537,11 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
         o.apply_trotter_controlled(psi, n_s + 1, n_s, n_s, diag / lub, off / lub, t_k, r)
         got = _np(st[(1 << k) * N:((1 << k) + 1) * N])
         ref = psi[N:]
-        assert np.abs(got - ref).max() <= 1e-5
-        assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-4, k
+        assert np.abs(got - ref).max() <= row_abs
+        assert np.abs(got - ref).max() / np.abs(ref).max() < row_rel, k
     out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
     plan.measure_async(st, out)          # p_success is 0 before the inversion: read the norm only
-    assert out[2].item() == pytest.approx(1.0, abs=1e-4)
+    assert out[2].item() == pytest.approx(1.0, abs=1e-4 if prec == "c64" else 1e-10)
     # The clock block and the Hadamard layer at full size (split register passes) on a seeded
     # random state: every system column j is transformed on its own, so the oracle checks
     # sampled columns one by one.
@@ -556,8 +561,8 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
         rotated0 = psi[:R].copy()
         o.qft(psi, n_c + 1, 0, n_c, inverse=False)
         scale = np.abs(x).max()
-        assert np.abs(_np(view[0, :, j]) - rotated0).max() <= 2e-5 * scale, j
-        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= 2e-5 * scale, j
+        assert np.abs(_np(view[0, :, j]) - rotated0).max() <= col * scale, j
+        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= col * scale, j
     torch.view_as_real(view[1]).normal_(generator=g)
     before1 = [_np(view[1, :, j]) for j in cols]
     plan.apply_stage("final_h", st)
@@ -565,7 +570,7 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl):
         psi = x.copy()
         for q in range(n_c):
             o.apply_1q(psi, n_c, q, o.H_GATE)
-        assert np.abs(_np(view[1, :, j]) - psi).max() <= 2e-5 * np.abs(x).max(), j
+        assert np.abs(_np(view[1, :, j]) - psi).max() <= col * np.abs(x).max(), j
     del st
     torch.cuda.empty_cache()
 
