@@ -575,6 +575,61 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl, prec):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.slow
+def test_poiseuille_34_qubits_maximum_register(hhl):
+    """The largest register a plan accepts: n_s = 20, n_c = 13, one ancilla (34 qubits, a
+    128 GiB complex64 state). The controlled Strang products on sampled clock rows and the
+    clock block on sampled system columns against the oracle, and the norm after the whole
+    circuit; one qubit more is refused."""
+    import torch
+    from synth_inputs import rhs
+    n_s, n_c = 20, 13
+    N, R = 1 << n_s, 1 << n_c
+    diag, off = o.laplacian_tridiag(N)
+    b = rhs("poiseuille", N)
+    dt, r_max = 1024.0, 8
+    with pytest.raises(hhl.HHLError):
+        _gpu_plan(hhl, *o.laplacian_tridiag(2 * N), n_s + 1, n_c, "c64", expm="trotter", trotter_dt=dt,
+                  trotter_steps_max=r_max)
+    plan = _gpu_plan(hhl, diag, off, n_s, n_c, "c64", expm="trotter", trotter_dt=dt, trotter_steps_max=r_max)
+    st = plan.new_state()
+    plan.prepare_rhs_host(b, st)
+    plan.apply_stage("qpe_u", st)
+    lub = 4.0 * (N + 1) ** 2
+    t0 = o.t0_total("range_fill", n_c)
+    bhat = b / np.linalg.norm(b) / math.sqrt(R)
+    for k in (0, 10, 12):
+        t_k = t0 * (1 << k) / R
+        psi = np.zeros(2 * N, dtype=np.complex128)
+        psi[N:] = bhat
+        o.apply_trotter_controlled(psi, n_s + 1, n_s, n_s, diag / lub, off / lub, t_k, o.trotter_steps(t_k, dt, r_max))
+        got = _np(st[(1 << k) * N:((1 << k) + 1) * N])
+        assert np.abs(got - psi[N:]).max() / np.abs(psi[N:]).max() < 1e-4, k
+    g = torch.Generator(device="cuda")
+    g.manual_seed(20230702)
+    view = st.view(2, R, N)
+    torch.view_as_real(view[0]).normal_(generator=g)
+    cols = [0, 12345, N - 1]
+    before = [_np(view[0, :, j]) for j in cols]
+    plan.apply_stage("clock_block", st)
+    theta = o.rotation_angles(n_c, t0)
+    for j, x in zip(cols, before):
+        psi = np.zeros(2 * R, dtype=np.complex128)
+        psi[:R] = x
+        o.qft(psi, n_c + 1, 0, n_c, inverse=True)
+        o.apply_clock_controlled_ry(psi, 0, n_c, theta)
+        o.qft(psi, n_c + 1, 0, n_c, inverse=False)
+        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= 2e-5 * np.abs(x).max(), j
+    plan.prepare_rhs_host(b, st)
+    plan.apply_circuit(st)
+    out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
+    plan.measure_async(st, out)
+    assert out[2].item() == pytest.approx(1.0, abs=1e-4)
+    assert 0.0 < out[0].item() <= out[1].item() <= 1.0
+    del st, view
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("flow,n_s,n_c", [("couette", 4, 8), ("poiseuille", 5, 9), ("couette", 6, 11),
                                           ("poiseuille", 4, 13)])
