@@ -630,7 +630,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     out = {
         "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)" if args.precision == "c64" else "c128 (f64)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "c64" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
                    "expm": wl["expm"],
@@ -746,7 +746,7 @@ def run_qft(args, rank: int, world: int, local_rank: int) -> None:
             "metric": METRIC, "value": replica_rate(step_bytes * args.steps, world, total_s) / 1e9, "unit": wl["unit"],
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 (f32)" if args.precision == "c64" else "c128 (f64)", "data": "synthetic",
+            "dtype": "f32" if args.precision == "c64" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
                        "l2": "inputs larger than L2" if states * (1 << n) * amp_bytes > (256 << 20) else "L2-resident",
                        "parallelism": f"replicas x{world}"},
@@ -875,8 +875,8 @@ def run_batch(args, rank: int, world: int, local_rank: int) -> None:
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": wl["unit"], "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "instances": wl["count"],
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "precision": "c64", "instances": wl["count"],
                    "streams": binf["streams"], "gemm_choices": "tuning.json" if choices else "size rule",
                    "l2": "inputs larger than L2 (all states %.1f GB)" % (binf["state_bytes"] / 1e9),
                    "parallelism": f"replicas x{world}"},
