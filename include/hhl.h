@@ -263,9 +263,20 @@ hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void
 hhl_status hhl_measure_async(hhl_plan_t plan, const void* state_dev, double* out_dev, void* stream);
 
 /* Synchronous form: fills *out; if x_host != NULL writes xhat (HOST, 2N doubles,
- * re/im interleaved). Synchronises the stream. HHL_ERR_SINGULAR if p_success = 0. */
+ * re/im interleaved). Synchronises the stream. HHL_ERR_SINGULAR if p_success = 0;
+ * HHL_ERR_TIMEOUT / HHL_ERR_NUMERIC as hhl_plan_status. */
 hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* out,
                        double* x_host, void* stream);
+
+/* Device-side status of the last circuit on this plan (the bounded waits of Sec. IV's
+ * controlled-U_k products on the tensor cores): synchronises the stream and returns HHL_OK,
+ * HHL_ERR_TIMEOUT (a bounded wait of the tcgen05 GEMM ran out; its CTAs skipped the rest of
+ * their tile after their copies and products in flight had drained, so the state is wrong but
+ * the context is intact and the plan usable) or HHL_ERR_NUMERIC (an amplitude of magnitude
+ * >= 2 reached the FP16 operands). The flag is cleared when a circuit starts
+ * (hhl_apply_circuit, or hhl_apply_stage of HHL_STAGE_QPE_U), on the stream. Plans without
+ * tcgen05 operands always report HHL_OK. */
+hhl_status hhl_plan_status(hhl_plan_t plan, void* stream);
 
 /* a6 - shots: the system register measured `shots` times after postselection (ancilla 1,
  * clock 0; Sec. II.A reads the solution by repeated measurement): outcome j with probability
@@ -329,9 +340,15 @@ hhl_status hhl_batch_run(hhl_batch_t batch, const double* b_dev, double* out_dev
  * graph (for per-kernel timing with hhl_profile_*): reads the right-hand sides already in
  * the batch's device buffer (from the last run) and leaves the results there. */
 hhl_status hhl_batch_run_eager(hhl_batch_t batch, void* stream);
-/* As hhl_batch_run with HOST arrays (copies in and out on the stream, then synchronises). */
+/* As hhl_batch_run with HOST arrays (copies in and out on the stream, then synchronises);
+ * returns the hhl_batch_status of the run. */
 hhl_status hhl_batch_run_host(hhl_batch_t batch, const double* b_host, double* out_host, double* eps_host,
                               void* stream);
+/* Device-side status of the last run (hhl_batch_run, _eager or _host), as hhl_plan_status:
+ * synchronises the stream; HHL_OK, HHL_ERR_TIMEOUT or HHL_ERR_NUMERIC. Every run clears the
+ * flag first, so a status describes that run alone; hhl_batch_run itself does not wait for
+ * the GPU, so its results are valid only once this call returns HHL_OK. */
+hhl_status hhl_batch_status(hhl_batch_t batch, void* stream);
 
 /* ------------------------------------------------------------------- learned T0 predictor
  * A 6 -> 128 -> 128 -> 2 perceptron (tanh hidden layers) that maps features of the linear
@@ -389,6 +406,12 @@ hhl_status hhl_qft_whole(void* state_dev, int32_t n_qubits, int32_t n_states, in
 /* Number of kernels this library has launched since load (all entry points). */
 uint64_t hhl_kernel_launch_count(void);
 
+/* Testing the timeout path: with the environment variable HHL_FAULT=tc_wait set when a
+ * tcgen05 GEMM is launched (or a batch graph is captured), that GEMM issues no operand copy
+ * and bounds its waits by about a millisecond, so it ends with HHL_ERR_TIMEOUT (no copy or
+ * product in flight when its waits run out). HHL_FAULT=alloc|plan|launch inject host failures
+ * (HHL_ERR_OOM, HHL_ERR_INVALID_ARG, HHL_ERR_CUDA) into allocation, planning and launches. */
+
 /* Clock-controlled U for callers that cannot allocate device memory while they run (the
  * paper has no counterpart; this is an interface convenience). Hosts that hand all device
  * memory to their own pool allocator, or loops that cannot afford the device-wide
@@ -400,7 +423,9 @@ uint64_t hhl_kernel_launch_count(void);
  * The product rows are staged in one fixed 8 MiB device array inside the library (held on
  * every GPU that loads it, until exit); requests needing more than 2^20 complex64 values
  * (2^(n_clock-1) * N) are rejected with HHL_ERR_INVALID_ARG. The first call on each device
- * looks up that array's device address (set-up), so make it before any stream capture.
+ * looks up that array's device address (set-up), so make it before any stream capture; the
+ * address is kept per device and CUDA context, so after a device reset the next call looks it
+ * up again (again before any capture).
  * Each call overwrites the staging space before reading it; calls that may overlap on the
  * GPU (unordered streams) share the array and race. Asynchronous on `stream`. */
 hhl_status hhl_controlled_u_noalloc(const void* u_dev, void* half_dev, int32_t n_sys_qubits, int32_t n_clock,

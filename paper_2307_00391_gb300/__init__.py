@@ -201,6 +201,11 @@ class HHLPlan:
             out["xhat"] = x[0::2] + 1j * x[1::2]
         return out
 
+    def status(self, stream=None) -> None:
+        """Raise HHLError if the last circuit's tensor-core GEMMs reported a timeout or an
+        out-of-range operand (synchronises the stream)."""
+        check(self._lib.hhl_plan_status(self._h, ctypes.c_void_p(_stream_handle(stream))), "hhl_plan_status")
+
     def measure_async(self, state, out_dev, stream=None) -> None:
         check(self._lib.hhl_measure_async(self._h, ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(out_dev.data_ptr()),
                                           ctypes.c_void_p(_stream_handle(stream))), "hhl_measure_async")
@@ -352,11 +357,21 @@ class HHLBatch:
                             xhat=blk[4::2] + 1j * blk[5::2]))
         return res
 
-    def run(self, b_dev, out_dev, eps_dev, stream=None) -> None:
-        """Device arrays (torch float64): packed b, packed results, dissipation per instance."""
+    def run(self, b_dev, out_dev, eps_dev, stream=None, check_status: bool = True) -> None:
+        """Device arrays (torch float64): packed b, packed results, dissipation per instance.
+        With check_status (default) the call waits for the run and raises on a device-side
+        GEMM error; without it the run stays asynchronous and status() must be called before
+        the results are used."""
         check(self._lib.hhl_batch_run(self._h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(out_dev.data_ptr()),
                                       ctypes.c_void_p(eps_dev.data_ptr()), ctypes.c_void_p(_stream_handle(stream))),
               "hhl_batch_run")
+        if check_status:
+            self.status(stream)
+
+    def status(self, stream=None) -> None:
+        """Raise HHLError if the last run's tensor-core GEMMs reported a timeout or an
+        out-of-range operand (synchronises the stream)."""
+        check(self._lib.hhl_batch_status(self._h, ctypes.c_void_p(_stream_handle(stream))), "hhl_batch_status")
 
     def run_eager(self, stream=None) -> None:
         """The same work launch by launch (for per-kernel timing), on the inputs of the last run."""

@@ -81,6 +81,8 @@ SIGNATURES = [
     ("hhl_batch_run", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_batch_run_eager", c_int32, [c_void_p, c_void_p]),
     ("hhl_batch_run_host", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_batch_status", c_int32, [c_void_p, c_void_p]),
+    ("hhl_plan_status", c_int32, [c_void_p, c_void_p]),
     ("hhl_mlp_create", c_int32, [POINTER(c_void_p)]),
     ("hhl_mlp_destroy", None, [c_void_p]),
     ("hhl_mlp_set_params", c_int32, [c_void_p, c_void_p, c_void_p]),

@@ -848,6 +848,7 @@ hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void
   switch (stage) {
     case HHL_STAGE_QPE_U:
       if (p.expm_mode == HHL_EXPM_TROTTER) return hhl::launch_trotter(p, s0, false, st);
+      s = hhl::tc_reset_error(p, st);  // a new circuit: the GEMM status covers it alone
       for (int k = 0; k < p.n_c && s == HHL_OK; ++k) s = ctrl_u(p, s0, k, false, st);
       return s;
     case HHL_STAGE_CLOCK_BLOCK:
@@ -895,8 +896,7 @@ hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* 
   int tc_err = 0;
   if (int* ef = hhl::tc_error_flag(p)) HHL_CUDA_TRY(cudaMemcpyAsync(&tc_err, ef, sizeof(int), cudaMemcpyDeviceToHost, st));
   HHL_CUDA_TRY(cudaStreamSynchronize(st));
-  if (tc_err == 4) return fail(HHL_ERR_NUMERIC, "an amplitude of magnitude >= 2 reached the FP16 tensor-core operands");
-  if (tc_err != 0) return fail(HHL_ERR_TIMEOUT, "a bounded wait in the tcgen05 GEMM ran out (stage " + std::to_string(tc_err) + ")");
+  if (tc_err != 0) return hhl::tc_flag_status(tc_err);
   out->p_success = sc[0];
   out->p_anc1 = sc[1];
   out->norm = sc[2];
@@ -904,6 +904,16 @@ hhl_status hhl_measure(hhl_plan_t plan, const void* state_dev, hhl_measurement* 
   if (!(sc[3] > 0.0)) return fail(HHL_ERR_SINGULAR, "|b| = 0");
   if (!(sc[0] > 0.0)) return fail(HHL_ERR_SINGULAR, "postselection probability is 0");
   return HHL_OK;
+}
+
+hhl_status hhl_plan_status(hhl_plan_t plan, void* stream) {
+  if (plan == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  int tc_err = 0;
+  if (int* ef = hhl::tc_error_flag(plan->p))
+    HHL_CUDA_TRY(cudaMemcpyAsync(&tc_err, ef, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  return hhl::tc_flag_status(tc_err);
 }
 
 hhl_status hhl_sample(hhl_plan_t plan, const void* state_dev, const double* uniforms_dev, int64_t shots,

@@ -249,6 +249,8 @@ hhl_status capture(hhl_batch_s* B, cudaStream_t origin) {
   const uint64_t l0 = g_launches.load();
   hhl_status s = HHL_OK;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  // every replay starts with a clear GEMM error flag (a memset node ahead of the fork)
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_err, 0, sizeof(int), cap);
   if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
   for (auto& w : B->work)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(w.s, fork, 0);
@@ -427,8 +429,9 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
       B->maps.insert(B->maps.end(), 4, CUtensorMap{});
     }
   }
-  cudaMemset(B->d_err, 0, sizeof(int));
-  hhl_status s = tc_init_kernels();
+  hhl_status s = HHL_OK;
+  if (cudaError_t me = cudaMemset(B->d_err, 0, sizeof(int)); me != cudaSuccess) s = cuda_fail(me, "cudaMemset(error flag)");
+  if (s == HHL_OK) s = tc_init_kernels();
   if (s == HHL_OK) {
     int64_t maxN = 0;
     for (const Plan& p : B->plans) maxN = std::max<int64_t>(maxN, p.N);
@@ -506,6 +509,7 @@ hhl_status hhl_batch_run_eager(hhl_batch_t b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t fork = nullptr;
   HHL_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  HHL_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), st));
   HHL_CUDA_TRY(cudaEventRecord(fork, st));
   for (auto& w : b->work) HHL_CUDA_TRY(cudaStreamWaitEvent(w.s, fork, 0));
   hhl_status s = HHL_OK;
@@ -535,12 +539,17 @@ hhl_status hhl_batch_run_host(hhl_batch_t b, const double* b_host, double* out_h
   g_launches.fetch_add(b->graph_launches, std::memory_order_relaxed);
   HHL_CUDA_TRY(cudaMemcpyAsync(out_host, b->d_out, oo * sizeof(double), cudaMemcpyDeviceToHost, st));
   HHL_CUDA_TRY(cudaMemcpyAsync(eps_host, b->d_eps, b->count * sizeof(double), cudaMemcpyDeviceToHost, st));
-  HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  return hhl_batch_status(b, stream);
+}
+
+hhl_status hhl_batch_status(hhl_batch_t b, void* stream) {
+  using namespace hhl;
+  if (b == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL batch");
+  cudaStream_t st = (cudaStream_t)stream;
   int err = 0;
-  HHL_CUDA_TRY(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err == 4) return fail(HHL_ERR_NUMERIC, "an amplitude of magnitude >= 2 reached the FP16 tensor-core operands");
-  if (err) return fail(HHL_ERR_TIMEOUT, "a bounded wait in the tcgen05 GEMM ran out");
-  return HHL_OK;
+  HHL_CUDA_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HHL_CUDA_TRY(cudaStreamSynchronize(st));
+  return tc_flag_status(err);
 }
 
 }  // extern "C"

@@ -152,7 +152,12 @@ bool tc_supported(const Plan& p);
 hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t st);
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
 void tc_free(Plan& p);
-int* tc_error_flag(const Plan& p);  // device flag: 1-3 a bounded GEMM wait ran out, 4 operand out of range
+int* tc_error_flag(const Plan& p);  // device flag: 1-3, 5 a bounded GEMM wait ran out, 4 operand out of range
+// Clear that flag on the stream (at the start of each circuit, so that a status reports only
+// the GEMMs of the circuit since then).
+hhl_status tc_reset_error(const Plan& p, cudaStream_t st);
+// Map a read-back flag value to a status (HHL_OK for 0).
+hhl_status tc_flag_status(int flag);
 }  // namespace hhl
 #include <cuda.h>
 namespace hhl {

@@ -25,12 +25,18 @@
 // loads (128-byte swizzle) into a 2-stage shared-memory ring, warp 1 (one lane) issues the
 // MMAs (M = 128, N = BN, K = 16) into a BN-column TMEM accumulator, and all four warps
 // drain TMEM with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. output rows) and
-// store the rows. Every mbarrier wait is bounded; on expiry the CTA records an error flag
-// (read back as HHL_ERR_TIMEOUT), skips the remaining work, frees its TMEM and exits.
+// store the rows. Every mbarrier wait is bounded (wait_cycles, a kernel argument); on expiry
+// the CTA records an error flag (read back as HHL_ERR_TIMEOUT) and skips the remaining work,
+// but before it frees its TMEM and exits it drains what it started: the producer waits
+// (bounded) for every bulk copy it issued to land, and the MMA lane always commits its issued
+// MMAs to the final barrier, which the whole CTA waits on (bounded) before the dealloc.
+// Fault injection for the error path (fault = 1): the producer issues no copy at all, so the
+// MMA lane's first wait runs out with nothing in flight.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "hhl_common.cuh"
 
@@ -51,7 +57,8 @@ template <int BN> struct TcShape {
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
   static constexpr int kTmemCols = BN;                            // fp32 accumulator columns
 };
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;      // default bound of a wait: ~2 s at 2 GHz
+constexpr long long kFaultWaitCycles = 2000000LL;    // injected timeout: ~1 ms
 
 struct TcState {
   __half* a_hi = nullptr;  // M_sub x 2N
@@ -85,11 +92,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of the given parity to complete; false (and the error flag set) after
-// about two seconds.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err, int code) {
+// `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err, int code, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, code);
       return false;
     }
@@ -163,7 +170,8 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                    const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-                   float* __restrict__ state_half, int n_s, int k, int k_iters, int* err) {
+                   float* __restrict__ state_half, int n_s, int k, int k_iters, int* err, long long wait_cycles,
+                   int fault) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
@@ -200,9 +208,10 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     // producer: TMA loads of the four operand tiles of each K step
-    for (int it = 0; it < k_iters; ++it) {
+    int issued = 0;
+    for (int it = 0; it < (fault ? 0 : k_iters); ++it) {
       const int s = it % kStages;
-      if (!mbar_wait_bounded(&empty_bar[s], ((it / kStages) & 1) ^ 1, err, 1)) {
+      if (!mbar_wait_bounded(&empty_bar[s], ((it / kStages) & 1) ^ 1, err, 1, wait_cycles)) {
         abort_flag = 1;
         break;
       }
@@ -213,14 +222,19 @@ __global__ void __launch_bounds__(128, 1)
       tma_load_2d(st + kTileA, &map_alo, &full_bar[s], kx, m0);
       tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
       tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
+      issued = it + 1;
     }
+    // drain: the last copy issued into each stage has landed before shared memory is released
+    // (on the normal path the MMA lane has already consumed them, so these return at once)
+    for (int it = issued > kStages ? issued - kStages : 0; it < issued; ++it)
+      mbar_wait_bounded(&full_bar[it % kStages], (it / kStages) & 1, err, 5, wait_cycles);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     constexpr uint32_t idesc = idesc_f16(kBM, BN);
     bool ok = true;
     for (int it = 0; it < k_iters; ++it) {
       const int s = it % kStages;
-      if (!mbar_wait_bounded(&full_bar[s], (it / kStages) & 1, err, 2)) {
+      if (!mbar_wait_bounded(&full_bar[s], (it / kStages) & 1, err, 2, wait_cycles)) {
         ok = false;
         break;
       }
@@ -237,13 +251,16 @@ __global__ void __launch_bounds__(128, 1)
       }
       mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
     }
-    if (ok) mma_commit(&done_bar);
-    else abort_flag = 1;
+    // always commit: done_bar completes once every MMA this lane issued has finished (at once
+    // when none was), so the wait below also drains an aborted accumulation before the dealloc
+    mma_commit(&done_bar);
+    if (!ok) abort_flag = 1;
   }
   __syncwarp();
+  __syncthreads();  // the producer and MMA lanes have left their (bounded) loops
 
   // epilogue: all four warps drain their 32 TMEM lanes (= output rows)
-  if (!mbar_wait_bounded(&done_bar, 0, err, 3)) abort_flag = 1;
+  if (!mbar_wait_bounded(&done_bar, 0, err, 3, wait_cycles)) abort_flag = 1;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (abort_flag == 0) {  // uniform across the CTA: tcgen05.ld is warp-collective
@@ -418,6 +435,11 @@ hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi,
                           const CUtensorMap& map_alo, const CUtensorMap& map_bhi, const CUtensorMap& map_blo, int bn,
                           int* err, cudaStream_t st) {
   const int64_t N2 = 2LL << n_s;
+  // HHL_FAULT=tc_wait (testing the timeout path): no operand copy is issued and every wait is
+  // bounded by about a millisecond, so the MMA lane's first wait runs out with nothing in flight
+  const char* fenv = getenv("HHL_FAULT");
+  const int fault = (fenv != nullptr && strcmp(fenv, "tc_wait") == 0) ? 1 : 0;
+  const long long wait_cycles = fault ? kFaultWaitCycles : kWaitCycles;
   const int64_t total4 = m_sub * N2 / 4;
   int g = (int)((total4 + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
@@ -428,12 +450,14 @@ hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi,
     dim3 grid((unsigned)(N2 / 256), (unsigned)(m_sub / kBM));
     HHL_PROF_BEGIN(st);
     k_ctrl_gemm_tc<256><<<grid, 128, TcShape<256>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
-                                                                     n_s, k, (int)(N2 / kBK), err);
+                                                                     n_s, k, (int)(N2 / kBK), err, wait_cycles,
+                                                                     fault);
   } else {
     dim3 grid((unsigned)(N2 / 128), (unsigned)(m_sub / kBM));
     HHL_PROF_BEGIN(st);
     k_ctrl_gemm_tc<128><<<grid, 128, TcShape<128>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
-                                                                     n_s, k, (int)(N2 / kBK), err);
+                                                                     n_s, k, (int)(N2 / kBK), err, wait_cycles,
+                                                                     fault);
   }
   HHL_LAUNCH_CHECK("k_ctrl_gemm_tc");
   return HHL_OK;
@@ -454,6 +478,22 @@ hhl_status tc_make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64
 int* tc_error_flag(const Plan& p) {
   const TcState* t = static_cast<const TcState*>(p.d_tc);
   return t ? t->err : nullptr;
+}
+
+hhl_status tc_flag_status(int flag) {
+  if (flag == 0) return HHL_OK;
+  if (flag == 4) return fail(HHL_ERR_NUMERIC, "an amplitude of magnitude >= 2 reached the FP16 tensor-core operands");
+  static const char* const where[] = {"", "producer (free stage)", "MMA issuer (operands)", "epilogue (accumulator)", "",
+                                      "producer (copies in flight)"};
+  return fail(HHL_ERR_TIMEOUT, std::string("a bounded wait in the tcgen05 GEMM ran out: ") +
+                                   (flag > 0 && flag <= 5 ? where[flag] : "unknown"));
+}
+
+hhl_status tc_reset_error(const Plan& p, cudaStream_t st) {
+  const TcState* t = static_cast<const TcState*>(p.d_tc);
+  if (t == nullptr || t->err == nullptr) return HHL_OK;
+  HHL_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), st));
+  return HHL_OK;
 }
 
 void tc_free(Plan& p) {

@@ -12,10 +12,15 @@
 // complex64 values = 8 MiB, held on every GPU that loads the library until the process
 // exits). Host code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device current)
-// and caches it; that first call should therefore come before any stream capture. Every
+// and caches it together with the unique id of the CUDA context it belongs to; that first
+// call should therefore come before any stream capture. A device reset (cudaDeviceReset by
+// the caller or by another library) ends that context: the next call sees a new context id
+// and looks the address up again instead of writing through a stale one. Every
 // call overwrites the part of the array it uses before reading it, so no state is carried
 // from one call to the next, but all calls share the one array: calls whose kernels may
 // overlap on the GPU (different streams without ordering between them) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "hhl_common.cuh"
@@ -31,6 +36,7 @@ static __device__ __align__(256) float2 g_noalloc_scratch[kMaxScratchAmps];
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {0};  // context id each cached address belongs to
 
 __device__ __forceinline__ int64_t row_with_bit_na(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
@@ -113,17 +119,48 @@ __global__ void k_rows_scatter_noalloc(float2* __restrict__ S, const float2* __r
   }
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Unique id of the current CUDA context (cuCtxGetId: never reused within a process), 0 when
+// the driver does not provide it (the cache is then per device only).
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)p;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and
+// context.
 hhl_status scratch_address(void** out) {
   int dev = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(HHL_ERR_UNSUPPORTED, "device ordinal beyond the scratch table");
+  // (before the runtime has made a context current on this thread the id reads 0, and the
+  // next call looks the address up once more: harmless, the address is the same)
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
+  if (g_noalloc_ptr[dev] == nullptr || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
     g_noalloc_ptr[dev] = p;
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_ptr[dev];
   return HHL_OK;

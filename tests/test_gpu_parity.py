@@ -1,6 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (max absolute amplitude error): 1e-10 for complex128, 1e-5 for complex64.
+Tolerances (max absolute amplitude error): 1e-10 for complex128, 1e-5 for complex64. Where the
+amplitudes of a register are themselves of order 1e-5 (the 32- and 34-qubit states), the same
+bound is applied relative to the largest amplitude of the compared row or column. Quantities
+derived from the postselected vector v are checked against the bound that the amplitude bound
+implies for them: xhat = v / |v| moves by at most (1 + sqrt(N)) max|dv| / |v| per entry.
 """
 import math
 
@@ -44,6 +48,13 @@ def _b_dev(b):
 
 def _half(psi, n_s, n_c, anc):
     return psi.reshape(2, 1 << n_c, 1 << n_s)[anc]
+
+
+def xhat_bound(dv_max, v_norm, n):
+    """Entry-wise bound on the change of xhat = v / |v| when every entry of v moves by at most
+    dv_max: |dx_i| <= |dv_i| / |v'| + |v_i| | |v| - |v'| | / (|v| |v'|) <= (1 + sqrt(n)) dv_max / |v'|
+    (|v_i| <= |v|, | |v| - |v'| | <= |dv|_2 <= sqrt(n) dv_max), plus FP64 rounding slack."""
+    return (1.0 + math.sqrt(n)) * dv_max / (v_norm - math.sqrt(n) * dv_max) + 1e-13
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -174,7 +185,13 @@ def test_measure_and_dissipation_parity(hhl, prec, flow):
     assert m["b_norm"] == pytest.approx(np.linalg.norm(b), rel=1e-14)
     # norm of the whole buffer: 1 (the early mode keeps the rotated anc = 0 half)
     assert m["norm"] == pytest.approx(1.0, abs=1e-12 if prec == "c128" else 1e-5)
-    np.testing.assert_allclose(m["xhat"], ref["xhat"], atol=10 * tol)
+    # the postselected vector v (anc = 1, clock = 0 after the final Hadamards) at the amplitude
+    # bound; xhat at the bound that implies
+    v_got = _half(_np(st), n_s, n_c, 1)[0]
+    v_ref = _half(psi, n_s, n_c, 1)[0]
+    dv = np.abs(v_got - v_ref).max()
+    assert dv <= tol
+    np.testing.assert_allclose(m["xhat"], ref["xhat"], atol=xhat_bound(dv, np.linalg.norm(v_got), 1 << n_s))
     eps, u = plan.dissipation(st, want_u=True)
     np.testing.assert_allclose(u, u_ref, rtol=1e-9 if prec == "c128" else 2e-4,
                                atol=1e-12 * np.abs(u_ref).max())
@@ -321,7 +338,7 @@ def test_trotter_parity(hhl, prec, dt, r_max):
     st = plan.new_state()
     plan.prepare_rhs_host(b, st)
     plan.apply_stage("qpe_u", st)
-    tol = TOL[prec] * (4 if prec == "c64" else 1)
+    tol = TOL[prec]
     np.testing.assert_allclose(_np(st), ref["qpe_u"], atol=tol)
     for stage in ("clock_block", "uncompute_u", "final_h"):
         plan.apply_stage(stage, st)
@@ -343,7 +360,7 @@ def test_trotter_grouped_clock_bits_parity(hhl, monkeypatch, prec, runs, n_c, dt
     lub = pl["lam_ub"]
     tro = dict(diag=diag / lub, off=off / lub, dt=dt, r_max=r_max)
     ref = run_stages(b, n_s, pl, trotter=tro)
-    tol = TOL[prec] * (4 if prec == "c64" else 1)
+    tol = TOL[prec]
     for full in (False, True):
         plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, expm="trotter", trotter_dt=dt, trotter_steps_max=r_max,
                          full_uncompute=full)
@@ -439,7 +456,9 @@ def test_couette_1024_full_size_parity(hhl, couette_1024_oracle, prec):
     got = _np(st)
     np.testing.assert_allclose(_half(got, 10, 12, 1), _half(ref["psi"], 10, 12, 1), atol=TOL[prec])
     m = plan.measure(st)
-    np.testing.assert_allclose(m["xhat"], ref["post"]["xhat"], atol=10 * TOL[prec])
+    v_got = _half(got, 10, 12, 1)[0]
+    dv = np.abs(v_got - _half(ref["psi"], 10, 12, 1)[0]).max()
+    np.testing.assert_allclose(m["xhat"], ref["post"]["xhat"], atol=xhat_bound(dv, np.linalg.norm(v_got), 1024))
     assert m["p_success"] == pytest.approx(ref["post"]["p_success"], rel=1e-8 if prec == "c128" else 1e-4)
 
 
@@ -516,9 +535,10 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl, prec):
     diag, off = o.laplacian_tridiag(N)
     b = rhs("poiseuille", N)
     dt, r_max = 1024.0, 8
-    # (absolute / relative bound on the sampled U_k rows, bound on transformed columns per unit
-    # of their largest input amplitude)
-    row_abs, row_rel, col = (1e-5, 1e-4, 2e-5) if prec == "c64" else (1e-10, 1e-9, 1e-10)
+    # Bounds on the sampled U_k rows (relative to the row's largest amplitude: the amplitudes
+    # are ~2e-5 here, so an absolute 1e-5 would pin nothing) and on transformed columns (per unit
+    # of their largest input amplitude); complex128 keeps its absolute 1e-10 as well.
+    row_abs, row_rel, col = (None, TOL["c64"], TOL["c64"]) if prec == "c64" else (1e-10, 1e-9, 1e-10)
     plan = _gpu_plan(hhl, diag, off, n_s, n_c, prec, expm="trotter", trotter_dt=dt, trotter_steps_max=r_max)
     st = plan.new_state()
     plan.prepare_rhs_host(b, st)
@@ -537,11 +557,12 @@ def test_poiseuille_2p18_trotter_full_size_sampled_rows(hhl, prec):
         o.apply_trotter_controlled(psi, n_s + 1, n_s, n_s, diag / lub, off / lub, t_k, r)
         got = _np(st[(1 << k) * N:((1 << k) + 1) * N])
         ref = psi[N:]
-        assert np.abs(got - ref).max() <= row_abs
-        assert np.abs(got - ref).max() / np.abs(ref).max() < row_rel, k
+        if row_abs is not None:
+            assert np.abs(got - ref).max() <= row_abs
+        assert np.abs(got - ref).max() <= row_rel * np.abs(ref).max(), k
     out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
     plan.measure_async(st, out)          # p_success is 0 before the inversion: read the norm only
-    assert out[2].item() == pytest.approx(1.0, abs=1e-4 if prec == "c64" else 1e-10)
+    assert out[2].item() == pytest.approx(1.0, abs=TOL[prec])
     # The clock block and the Hadamard layer at full size (split register passes) on a seeded
     # random state: every system column j is transformed on its own, so the oracle checks
     # sampled columns one by one.
@@ -604,7 +625,7 @@ def test_poiseuille_34_qubits_maximum_register(hhl):
         psi[N:] = bhat
         o.apply_trotter_controlled(psi, n_s + 1, n_s, n_s, diag / lub, off / lub, t_k, o.trotter_steps(t_k, dt, r_max))
         got = _np(st[(1 << k) * N:((1 << k) + 1) * N])
-        assert np.abs(got - psi[N:]).max() / np.abs(psi[N:]).max() < 1e-4, k
+        assert np.abs(got - psi[N:]).max() <= TOL["c64"] * np.abs(psi[N:]).max(), k
     g = torch.Generator(device="cuda")
     g.manual_seed(20230702)
     view = st.view(2, R, N)
@@ -619,12 +640,12 @@ def test_poiseuille_34_qubits_maximum_register(hhl):
         o.qft(psi, n_c + 1, 0, n_c, inverse=True)
         o.apply_clock_controlled_ry(psi, 0, n_c, theta)
         o.qft(psi, n_c + 1, 0, n_c, inverse=False)
-        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= 2e-5 * np.abs(x).max(), j
+        assert np.abs(_np(view[1, :, j]) - psi[R:]).max() <= TOL["c64"] * np.abs(x).max(), j
     plan.prepare_rhs_host(b, st)
     plan.apply_circuit(st)
     out = torch.empty(4 + 2 * N, dtype=torch.float64, device="cuda")
     plan.measure_async(st, out)
-    assert out[2].item() == pytest.approx(1.0, abs=1e-4)
+    assert out[2].item() == pytest.approx(1.0, abs=TOL["c64"])
     assert 0.0 < out[0].item() <= out[1].item() <= 1.0
     del st, view
     torch.cuda.empty_cache()

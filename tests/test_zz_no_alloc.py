@@ -68,6 +68,43 @@ def test_noalloc_controlled_u_matches_plan_path(lib):
     assert (got - ref).abs().max().item() < 1e-5
 
 
+def test_noalloc_at_the_size_limit_on_a_side_stream(lib):
+    """The largest accepted request, 2^(n_c-1) * 2^n_s = 2^20 complex64 values (the whole fixed
+    array: n_s = 10, n_c = 11), on a non-default stream, forward then adjoint, against the plan
+    path; one clock qubit more is refused."""
+    import torch
+    from synth_inputs import random_state
+    n_s, n_c = 10, 11
+    N, half = 1 << n_s, 1 << (n_s + n_c)
+    diag, off = lib.laplacian(N)
+    plan = lib.HHLPlan(n_s, n_c, diag=diag, off=off, precision="c64", gemm="simt")
+    us = _u_matrices(n_s, n_c, plan.info["t0"])
+    u_dev = [torch.tensor(u, dtype=torch.complex64, device="cuda") for u in us]
+    psi = random_state(n_s + n_c + 1, seed_offset=43)
+    ref = torch.tensor(psi, dtype=torch.complex64, device="cuda")
+    got = ref.clone()
+    c = lib.load()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    handle = ctypes.c_void_p(side.cuda_stream)
+    plan.apply_stage("qpe_u", ref)
+    for k in range(n_c):
+        st = c.hhl_controlled_u_noalloc(ctypes.c_void_p(u_dev[k].data_ptr()), ctypes.c_void_p(got.data_ptr()),
+                                        n_s, n_c, k, 0, handle)
+        assert st == 0, c.hhl_last_error()
+    anc1 = got[half:]
+    plan.apply_stage("uncompute_u", ref)
+    for k in range(n_c - 1, -1, -1):
+        st = c.hhl_controlled_u_noalloc(ctypes.c_void_p(u_dev[k].data_ptr()), ctypes.c_void_p(anc1.data_ptr()),
+                                        n_s, n_c, k, 1, handle)
+        assert st == 0, c.hhl_last_error()
+    side.synchronize()
+    torch.cuda.synchronize()
+    assert (got - ref).abs().max().item() < 1e-5
+    dummy = ctypes.c_void_p(16)
+    assert c.hhl_controlled_u_noalloc(dummy, dummy, n_s, n_c + 1, 0, 0, handle) == 1
+
+
 def test_noalloc_rejects_oversize_requests(lib):
     c = lib.load()
     dummy = ctypes.c_void_p(16)
