@@ -556,7 +556,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
   {
     // GEMM output rows (dense) or the Trotter pass's interior edges (32 per warp window)
     size_t scratch_amps = (size_t)(p.R / 2) * N;
-    if (!dense) scratch_amps = (size_t)p.R * trotter_segments(N) * 32;
+    if (!dense) scratch_amps = (size_t)trotter_side_amps(N, p.R);
     HHL_ALLOC(p.d_scratch, scratch_amps * ab, &p.workspace_bytes);
   }
   if (dense) {

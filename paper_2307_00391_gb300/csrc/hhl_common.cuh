@@ -61,6 +61,111 @@ template <class T> __host__ __device__ __forceinline__ T cconjmul(T a, T b) {  /
 }
 template <class T, class S> __host__ __device__ __forceinline__ T cscale(T a, S s) { T z; z.x = a.x * s; z.y = a.y * s; return z; }
 
+// ------------------------------------------------------------------ double-float arithmetic
+// The complex128 kernels keep FP64 amplitudes in memory but compute on GB300's FP32 pipe (the
+// FP64 pipe is about 1/32 of its rate): a value is the unevaluated sum h + l of two floats
+// (about 48 significant bits; Dekker's error-free transformations, Knuth's two-sum). Loads
+// split a double into its truncated top 24 significant bits and the rest with integer
+// operations only; stores rebuild the double exactly from the two floats and add them with
+// one FP64 addition.
+struct df {
+  float h, l;
+};
+struct dfc {
+  df x, y;  // real, imaginary
+};
+
+// s + e = a + b exactly (any a, b)
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// s + e = a + b exactly when |a| >= |b| (or a = 0)
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = df_two_sum(a.h, b.h);
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return df_fast_two_sum(p, e);
+}
+// a + w b and a - w b in one go (the two-FMA rotation forms)
+__device__ __forceinline__ df df_fma(df w, df b, df a) {
+  const float p = __fmul_rn(w.h, b.h);
+  float pe = __fmaf_rn(w.h, b.h, -p);
+  pe = __fmaf_rn(w.h, b.l, pe);
+  pe = __fmaf_rn(w.l, b.h, pe);
+  const df s = df_two_sum(a.h, p);
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, pe)));
+}
+__device__ __forceinline__ df df_fnma(df w, df b, df a) { return df_fma(df_neg(w), b, a); }
+// The same without the final renormalisation (12 instead of 15 operations): the tail may grow
+// to a few units in the last place of the head over a run of such steps, which the error-free
+// head sum absorbs; a chain of them ends with df_renorm.
+__device__ __forceinline__ df df_fma_lazy(df w, df b, df a) {
+  const float p = __fmul_rn(w.h, b.h);
+  float pe = __fmaf_rn(w.h, b.h, -p);
+  pe = __fmaf_rn(w.h, b.l, pe);
+  pe = __fmaf_rn(w.l, b.h, pe);
+  const df s = df_two_sum(a.h, p);
+  return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, pe))};
+}
+__device__ __forceinline__ df df_fnma_lazy(df w, df b, df a) { return df_fma_lazy(df_neg(w), b, a); }
+__device__ __forceinline__ df df_renorm(df a) { return df_two_sum(a.h, a.l); }
+__device__ __forceinline__ df df_scale(df a, float s) {  // s a power of two or any float
+  const float p = __fmul_rn(a.h, s);
+  const float e = __fmaf_rn(a.h, s, -p);
+  return df_fast_two_sum(p, __fmaf_rn(a.l, s, e));
+}
+
+// FP64 -> double-float without the FP64 pipe: h = the sign, exponent and top 23 stored
+// significand bits of x (truncation), l = the 29 remaining bits scaled to their weight.
+// Magnitudes below 2^-126 read as zero (their l below 2^-74), far below any amplitude bound.
+__device__ __forceinline__ df df_from_double(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  const unsigned m23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m23);
+  const float tail = __fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), __uint_as_float((unsigned)(e - 948) << 23));
+  const float l = __uint_as_float(__float_as_uint(tail) | sign);
+  return {e > 896 ? h : 0.0f, e > 948 ? l : 0.0f};
+}
+// float -> double exactly, integer operations only (normal floats; zero and subnormals -> 0)
+__device__ __forceinline__ double df_f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
+  return e == 0 ? 0.0 : __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double df_to_double(df v) { return __dadd_rn(df_f2d(v.h), df_f2d(v.l)); }
+
+__device__ __forceinline__ dfc dfc_from(double2 z) { return {df_from_double(z.x), df_from_double(z.y)}; }
+__device__ __forceinline__ double2 dfc_to(dfc z) { return make_double2(df_to_double(z.x), df_to_double(z.y)); }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_sub(a.x, b.x), df_sub(a.y, b.y)}; }
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return {df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
+}
+__device__ __forceinline__ dfc dfc_scale(dfc a, df s) { return {df_mul(a.x, s), df_mul(a.y, s)}; }
+// host: the double-float pair of an FP64 constant
+inline void df_split(double v, float* h, float* l) {
+  *h = (float)v;
+  *l = (float)(v - (double)*h);
+}
+
 // ------------------------------------------------------------------ the plan
 // One Trotter pass: clock bits [kb, kb + gbits) (single_k >= 0: the one bit single_k, rows
 // with that bit set) and the offset of its per-row-pattern layer lists in the plan's table.
@@ -144,7 +249,7 @@ hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, con
 // Plan time: group the clock bits into passes, fill p.trot_pass and the layer-list table
 // (bytes, to be uploaded to p.d_trot_lists); returns the number of lists.
 size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table);
-int64_t trotter_segments(int64_t N);  // warp windows per system row in a Trotter pass
+int64_t trotter_side_amps(int64_t N, int64_t R);  // side-buffer amplitudes of a Trotter plan
 hhl_status launch_interleave(const double* re, const double* im, int64_t n, double* out, cudaStream_t st);
 
 // tcgen05 GEMM (hhl_gemm_tc.cu)

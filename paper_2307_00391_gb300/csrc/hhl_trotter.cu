@@ -48,12 +48,22 @@ namespace hhl {
 
 namespace {
 
-constexpr int kLaneAmps = 16;                 // amplitudes per lane
+constexpr int kLaneAmps = 16;                 // amplitudes per lane (8 in the double-float kernel)
 constexpr int kHalo = 16;                     // halo per side = max layers per pass
 constexpr int kWin = 32 * kLaneAmps;          // 512 amplitudes per warp window
 constexpr int kInterior = kWin - 2 * kHalo;   // 480 written back per warp
 constexpr int kTrotThreads = 256;
 constexpr int kMaxPassLayers = kHalo + 1;     // exact with a kHalo halo when layer 0 is E
+constexpr int64_t kMaxRuns = 1 << 16;         // warps of one pass (the side buffer holds 32 amplitudes each)
+
+// Window geometry for LA amplitudes per lane: HL = kHalo / LA halo lanes on each side,
+// 32 LA amplitudes per window, 32 LA - 2 kHalo of them interior.
+template <int LA>
+struct Geo {
+  static constexpr int HL = kHalo / LA;
+  static constexpr int WIN = 32 * LA;
+  static constexpr int INTER = WIN - 2 * kHalo;
+};
 
 // A layer list also carries each rotation in factored form, used by windows away from the
 // row ends: with |cos th| >= |sin th| (form 0)
@@ -74,69 +84,160 @@ struct LayerList {
   // the same values rounded to FP32 on the host (GB300's FP64 conversions are slow)
   float pcf, psf, pc2f, ps2f;
   float cf[kMaxPassLayers], sf[kMaxPassLayers], wf[kMaxPassLayers];
+  // and the FP32 remainders (value - rounded value) of the double-float complex128 kernel
+  float pcl, psl, pc2l, ps2l;
+  float cl[kMaxPassLayers], sl[kMaxPassLayers], wl[kMaxPassLayers];
 };
 
-template <class R>
-__device__ __forceinline__ R layer_c(const LayerList* L, int l) {
-  if constexpr (sizeof(R) == 4) return L->cf[l];
-  else return L->c[l];
+// Arithmetic of the pass in registers. V is the amplitude type the layers work on, W its
+// real scalar: complex64 amplitudes in float2 / float; complex128 amplitudes either in
+// double2 / double (FP64 pipe) or, by default, in double-float dfc / df (FP32 pipe, the
+// FP64 amplitudes split on load and rebuilt on store: GB300's FP64 pipe is about 1/32 of
+// the FP32 one, so the FP64 form of this pass is compute bound at about ten times its memory
+// time).
+template <class R, bool DF> struct TrotArith;
+template <> struct TrotArith<float, false> {
+  using T = float2;
+  using V = float2;
+  using W = float;
+  static __device__ __forceinline__ V load(T t) { return t; }
+  static __device__ __forceinline__ T store(V v) { return v; }
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ W coef(const float* f, const float*, const double*, int l) { return f[l]; }
+  static __device__ __forceinline__ W coef1(float f, float, double) { return f; }
+  static __device__ __forceinline__ V finish(V v) { return v; }
+};
+template <> struct TrotArith<double, false> {
+  using T = double2;
+  using V = double2;
+  using W = double;
+  static __device__ __forceinline__ V load(T t) { return t; }
+  static __device__ __forceinline__ T store(V v) { return v; }
+  static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ W coef(const float*, const float*, const double* d, int l) { return d[l]; }
+  static __device__ __forceinline__ W coef1(float, float, double d) { return d; }
+  static __device__ __forceinline__ V finish(V v) { return v; }
+};
+template <> struct TrotArith<double, true> {
+  using T = double2;
+  using V = dfc;
+  using W = df;
+  static __device__ __forceinline__ V load(T t) { return dfc_from(t); }
+  static __device__ __forceinline__ T store(V v) { return dfc_to(v); }
+  static __device__ __forceinline__ V zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+  static __device__ __forceinline__ W coef(const float* f, const float* fl, const double*, int l) { return {f[l], fl[l]}; }
+  static __device__ __forceinline__ W coef1(float f, float fl, double) { return {f, fl}; }
+  static __device__ __forceinline__ V finish(V v) { return {df_renorm(v.x), df_renorm(v.y)}; }
+};
+
+// p + i w q = (p.x - w q.y, p.y + w q.x): one output of the factored two-FMA rotation
+__device__ __forceinline__ float2 fac1(float2 p, float2 q, float w) { return make_float2(p.x - w * q.y, p.y + w * q.x); }
+__device__ __forceinline__ double2 fac1(double2 p, double2 q, double w) {
+  return make_double2(p.x - w * q.y, p.y + w * q.x);
 }
-template <class R>
-__device__ __forceinline__ R layer_s(const LayerList* L, int l) {
-  if constexpr (sizeof(R) == 4) return L->sf[l];
-  else return L->s[l];
+__device__ __forceinline__ dfc fac1(dfc p, dfc q, df w) { return {df_fnma_lazy(w, q.y, p.x), df_fma_lazy(w, q.x, p.y)}; }
+// c p + i s q: one output of the plain rotation R(th) = [[c, i s], [i s, c]]
+__device__ __forceinline__ float2 rot1(float2 p, float2 q, float c, float s) {
+  return make_float2(c * p.x - s * q.y, c * p.y + s * q.x);
 }
+__device__ __forceinline__ double2 rot1(double2 p, double2 q, double c, double s) {
+  return make_double2(c * p.x - s * q.y, c * p.y + s * q.x);
+}
+__device__ __forceinline__ dfc rot1(dfc p, dfc q, df c, df s) {
+  return {df_fnma_lazy(s, q.y, df_mul(c, p.x)), df_fma_lazy(s, q.x, df_mul(c, p.y))};
+}
+__device__ __forceinline__ float2 phase_mul(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 phase_mul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ dfc phase_mul(dfc a, dfc b) { return dfc_mul(a, b); }
+
 __device__ __forceinline__ int64_t row_with_bit_t(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
 }
 
-template <class T>
-__device__ __forceinline__ T shfl_down1(T v) {
-  T r;
-  r.x = __shfl_down_sync(0xffffffffu, v.x, 1);
-  r.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+__device__ __forceinline__ float shfl_d(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_d(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ df shfl_d(df v) { return {shfl_d(v.h), shfl_d(v.l)}; }
+__device__ __forceinline__ float shfl_u(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_u(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ df shfl_u(df v) { return {shfl_u(v.h), shfl_u(v.l)}; }
+template <class V>
+__device__ __forceinline__ V shfl_down1(V v) {
+  V r;
+  r.x = shfl_d(v.x);
+  r.y = shfl_d(v.y);
   return r;
 }
-
-template <class T>
-__device__ __forceinline__ T shfl_up1(T v) {
-  T r;
-  r.x = __shfl_up_sync(0xffffffffu, v.x, 1);
-  r.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+template <class V>
+__device__ __forceinline__ V shfl_up1(V v) {
+  V r;
+  r.x = shfl_u(v.x);
+  r.y = shfl_u(v.y);
   return r;
-}
-
-template <class R>
-__device__ __forceinline__ R layer_w(const LayerList* L, int l) {
-  if constexpr (sizeof(R) == 4) return L->wf[l];
-  else return L->w[l];
 }
 
 // (a, b) <- (a + i w b, b + i w a), or with SWAP (b + i w a, a + i w b).
-template <bool SWAP, class T, class R>
-__device__ __forceinline__ void rot_factored(T& a, T& b, R w) {
-  const T na = mk<R>(a.x - w * b.y, a.y + w * b.x);
-  const T nb = mk<R>(b.x - w * a.y, b.y + w * a.x);
+template <bool SWAP, class V, class W>
+__device__ __forceinline__ void rot_factored(V& a, V& b, W w) {
+  const V na = fac1(a, b, w);
+  const V nb = fac1(b, a, w);
   a = SWAP ? nb : na;
   b = SWAP ? na : nb;
 }
 
 // All layers of a list on a window away from the row ends, in factored form (the result is
 // off by the product of the factors, applied with the end-of-pass scalar).
-template <bool SWAP, class T, class R>
-__device__ __forceinline__ void layer_factored(T (&x)[kLaneAmps], bool e_layer, R w) {
+template <bool SWAP, int LA, class V, class W>
+__device__ __forceinline__ void layer_factored(V (&x)[LA], bool e_layer, W w) {
   if (e_layer) {
 #pragma unroll
-    for (int q = 0; q < kLaneAmps; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
+    for (int q = 0; q < LA; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
   } else {
-    const T right = shfl_down1(x[0]);           // next lane's first amplitude
-    const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
+    const V right = shfl_down1(x[0]);    // next lane's first amplitude
+    const V left = shfl_up1(x[LA - 1]);  // previous lane's last amplitude
 #pragma unroll
-    for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
-    const T a = x[kLaneAmps - 1], b = x[0];
+    for (int q = 1; q + 1 < LA; q += 2) rot_factored<SWAP>(x[q], x[q + 1], w);
+    const V a = x[LA - 1], b = x[0];
     // (this lane's last a, next lane's first) and (previous lane's last, this lane's first b)
-    x[kLaneAmps - 1] = SWAP ? mk<R>(right.x - w * a.y, right.y + w * a.x) : mk<R>(a.x - w * right.y, a.y + w * right.x);
-    x[0] = SWAP ? mk<R>(left.x - w * b.y, left.y + w * b.x) : mk<R>(b.x - w * left.y, b.y + w * left.x);
+    x[LA - 1] = SWAP ? fac1(right, a, w) : fac1(a, right, w);
+    x[0] = SWAP ? fac1(left, b, w) : fac1(b, left, w);
+  }
+}
+
+// The double-float kernel writes the second form without the exchange of its two outputs:
+// R(th) (a, b) / sin th = (v a + i b, v b + i a), v = cot th = -w, so that both forms are one
+// fused multiply-add per output component with the operands in place, and its factors are
+// sin th instead of i sin th (the end-of-pass scalar is multiplied by (-i)^(number of such
+// layers)). One layer per loop iteration with a branch on the form keeps four copies of the
+// layer code (E / O, two forms): the fully unrolled double-float arithmetic of the paired
+// loop above overflows the instruction cache (measured: issue stalled on instruction fetch).
+__device__ __forceinline__ dfc fac2(dfc p, dfc q, df v) {  // v p + i q
+  return {df_fma_lazy(v, p.x, df_neg(q.y)), df_fma_lazy(v, p.y, q.x)};
+}
+template <bool F1>
+__device__ __forceinline__ void rot_factored_df(dfc& a, dfc& b, df w) {
+  if (F1) {
+    const dfc na = fac2(a, b, w), nb = fac2(b, a, w);
+    a = na;
+    b = nb;
+  } else {
+    const dfc na = fac1(a, b, w), nb = fac1(b, a, w);
+    a = na;
+    b = nb;
+  }
+}
+template <bool F1, int LA>
+__device__ __forceinline__ void layer_df(dfc (&x)[LA], bool e_layer, df w) {
+  if (e_layer) {
+#pragma unroll
+    for (int q = 0; q < LA; q += 2) rot_factored_df<F1>(x[q], x[q + 1], w);
+  } else {
+    const dfc right = shfl_down1(x[0]);
+    const dfc left = shfl_up1(x[LA - 1]);
+#pragma unroll
+    for (int q = 1; q + 1 < LA; q += 2) rot_factored_df<F1>(x[q], x[q + 1], w);
+    // (this lane's last a, next lane's first) and (previous lane's last, this lane's first b)
+    x[LA - 1] = F1 ? fac2(x[LA - 1], right, w) : fac1(x[LA - 1], right, w);
+    x[0] = F1 ? fac2(x[0], left, w) : fac1(x[0], left, w);
   }
 }
 
@@ -145,13 +246,20 @@ __device__ __forceinline__ void layer_factored(T (&x)[kLaneAmps], bool e_layer, 
 // pattern's layers in one pass: their rotations and the summed E phase, applied once at
 // the end of the pass (it is a scalar on the row).
 // (a, b) <- R(th) (a, b) with c = cos th, s = sin th.
-template <class T, class R>
-__device__ __forceinline__ void rot_apply(T& a, T& b, R c, R s) {
-  const T na = mk<R>(c * a.x - s * b.y, c * a.y + s * b.x);
-  const T nb = mk<R>(c * b.x - s * a.y, c * b.y + s * a.x);
+template <class V, class W>
+__device__ __forceinline__ void rot_apply(V& a, V& b, W c, W s) {
+  const V na = rot1(a, b, c, s);
+  const V nb = rot1(b, a, c, s);
   a = na;
   b = nb;
 }
+
+// The layer coefficients of the row pattern a warp is on (per warp, in shared memory).
+template <class W>
+struct LayerCoefs {
+  W c[32], s[32], w[32];
+  int form[32];
+};
 
 // Rows of a pass: single_k >= 0 enumerates the 2^(n_c - 1) rows with clock bit single_k set
 // (pattern 1); otherwise the rows whose pattern, clock bits [kb, kb + gbits), is nonzero:
@@ -181,9 +289,10 @@ __device__ __forceinline__ int run_start(int gw, int windows, int nruns) {
 // v = run_start(gw) and v - 1, when both lie in one row): q < 16 the first 16 interior
 // amplitudes of window v (the right halo of v - 1), q >= 16 the last 16 of window v - 1 (the
 // left halo of v); zero beyond the row end.
-template <class R>
+template <class R, int LA>
 __global__ void k_trotter_bounds(const typename Cx<R>::T* __restrict__ half, typename Cx<R>::T* __restrict__ side,
                                  int n_s, int segs, int windows, int nruns, int single_k, int kb, int gbits) {
+  constexpr int kInterior = Geo<LA>::INTER;
   const int64_t N = 1LL << n_s;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nruns * 32) return;
@@ -217,69 +326,62 @@ struct Window {
   bool first, last;
 };
 
-// Staging buffer of a warp: 32 x kLaneAmps amplitudes as 16-byte chunks, window chunk c
-// stored at position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both the coalesced
-// copy (lane t <-> chunk q * 32 + t) and the per-lane gather (lane t <-> its CPL consecutive
-// chunks) spread over the banks. Lane 0's chunks hold the left halo, lane 31's the right.
-// The left halo of a window inside a run is not copied here: the previous iteration puts the
-// carried amplitudes there (carry_copy).
-template <class T>
+// Staging buffer of a warp: 32 x LA amplitudes as 16-byte chunks, window chunk c stored at
+// position c ^ ((c / CPL) & 7) (CPL = chunks per lane) so that both the coalesced copy (lane t
+// <-> chunk q * 32 + t) and the per-lane gather (lane t <-> its CPL consecutive chunks) spread
+// over the banks. The first HL lanes' chunks hold the left halo (16 amplitudes), the last HL
+// lanes' the right one. The left halo of a window inside a run is not copied here: the
+// previous iteration puts the carried amplitudes there (carry_copy).
+template <int CPL>
+__device__ __forceinline__ int swz(int c) {
+  return c ^ ((c / CPL) & 7);
+}
+template <class T, int LA>
 __device__ __forceinline__ void stage_issue(uint4* stage, const Window& d, const T* half, const T* side, int gw,
                                             int segs, int64_t N, int lane) {
   constexpr int per = 16 / sizeof(T);
-  constexpr int CPL = kLaneAmps / per;
+  constexpr int CPL = LA / per;
+  constexpr int HC = kHalo / per;  // chunks of one halo
+  constexpr int kInterior = Geo<LA>::INTER;
   if (!d.full) return;
   const uint4* src = reinterpret_cast<const uint4*>(half + d.row * N + (int64_t)d.s * kInterior);
-  constexpr int chunks = kInterior / per;  // 30 * CPL
+  constexpr int chunks = kInterior / per;
 #pragma unroll
-  for (int q = 0; q < CPL; ++q) {
+  for (int q = 0; q < (chunks + 31) / 32; ++q) {
     const int c = q * 32 + lane;
-    if (c < chunks) {
-      const int wc = c + CPL;
-      cp_async16(&stage[wc ^ ((wc / CPL) & 7)], src + c);
-    }
+    if (c < chunks) cp_async16(&stage[swz<CPL>(c + HC)], src + c);
   }
-  const int sw = lane & 7;
-  if (lane == 0) {
-    if (d.s == 0) {
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) stage[q] = make_uint4(0u, 0u, 0u, 0u);
-    } else if (d.first) {
-      const uint4* hs = reinterpret_cast<const uint4*>(side + (int64_t)gw * 32 + 16);
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) cp_async16(&stage[q], hs + q);
-    }
-  } else if (lane == 31) {
+  if (lane < HC) {  // left halo chunk `lane`
+    if (d.s == 0) stage[swz<CPL>(lane)] = make_uint4(0u, 0u, 0u, 0u);
+    else if (d.first) cp_async16(&stage[swz<CPL>(lane)], reinterpret_cast<const uint4*>(side + (int64_t)gw * 32 + 16) + lane);
+  } else if (lane >= 32 - HC) {  // right halo chunk q
+    const int q = lane - (32 - HC);
+    const int pos = swz<CPL>(HC + chunks + q);
     if (d.s == segs - 1) {
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) stage[(31 * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+      stage[pos] = make_uint4(0u, 0u, 0u, 0u);
     } else if (d.last) {
-      const uint4* hs = reinterpret_cast<const uint4*>(side + (int64_t)(gw + 1) * 32);
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) cp_async16(&stage[(31 * CPL + q) ^ sw], hs + q);
+      cp_async16(&stage[pos], reinterpret_cast<const uint4*>(side + (int64_t)(gw + 1) * 32) + q);
     } else {
       // the start of the next interior, unwritten until this warp gets there
       const int64_t a0 = (int64_t)(d.s + 1) * kInterior;
-      const uint4* hs = reinterpret_cast<const uint4*>(half + d.row * N + a0);
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        if (a0 + (int64_t)(q + 1) * per <= N) cp_async16(&stage[(31 * CPL + q) ^ sw], hs + q);
-        else stage[(31 * CPL + q) ^ sw] = make_uint4(0u, 0u, 0u, 0u);
-      }
+      if (a0 + (int64_t)(q + 1) * per <= N) cp_async16(&stage[pos], reinterpret_cast<const uint4*>(half + d.row * N + a0) + q);
+      else stage[pos] = make_uint4(0u, 0u, 0u, 0u);
     }
   }
 }
 
 // The left halo of the next window of the run (same row): the original last 16 interior
-// amplitudes of the current, full window (lane 30's chunks) into lane 0's chunks of the
-// next staging buffer.
-__device__ __forceinline__ void carry_copy(uint4* next_stage, const uint4* stage, int lane, int cpl) {
-  if (lane < cpl) next_stage[lane] = stage[(30 * cpl + lane) ^ 6];
+// amplitudes of the current, full window into the left-halo chunks of the next staging buffer.
+template <int CPL, int HC, int CHUNKS>
+__device__ __forceinline__ void carry_copy(uint4* next_stage, const uint4* stage, int lane) {
+  if (lane < HC) next_stage[swz<CPL>(lane)] = stage[swz<CPL>(CHUNKS + lane)];
 }
 
 // The window after d in its run (window v of the pass; the run ends before v1).
+template <int LA>
 __device__ __forceinline__ Window window_next(Window d, int v, int v1, int segs, int64_t N, int single_k, int kb,
                                               int gbits) {
+  constexpr int kInterior = Geo<LA>::INTER;
   d.first = false;
   d.last = v + 2 == v1;
   if (++d.s == segs) {
@@ -296,21 +398,43 @@ __device__ __forceinline__ Window window_next(Window d, int v, int v1, int segs,
 // window is formed again after the current one is done, so that it holds no registers
 // during the layers.) 16 warps per SM with up to 128 registers each: the paired layers need
 // them (with 24 warps and 80 registers the pass spilled and ran 10% slower).
-template <class R>
-__global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 2 : 1) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
+// Threads per block: 256. Blocks per SM: 2 for complex64 (128 registers), 1 for the FP64 form
+// of complex128, 3 for the double-float form (8 amplitudes per lane: two 4 KiB staging buffers
+// per warp, 80 registers, 24 warps per SM to hide its latencies).
+template <class R, bool DF>
+constexpr int trot_threads() { return kTrotThreads; }
+template <class R, bool DF>
+constexpr int trot_min_blocks() { return DF ? 3 : (sizeof(R) == 4 ? 2 : 1); }
+// Amplitudes per lane: 16; 8 in the double-float kernel (its unrolled layer code for 16 per
+// lane, about 60 KB per window, missed the instruction cache: measured, issue stalled on
+// instruction fetch; 8 per lane halve the code and the registers at 2 halo lanes per side).
+template <class R, bool DF>
+constexpr int trot_lane_amps() { return DF ? 8 : kLaneAmps; }
+
+template <class R, bool DF>
+__global__ void __launch_bounds__(trot_threads<R, DF>(), trot_min_blocks<R, DF>()) k_trotter_pass(typename Cx<R>::T* __restrict__ half,
                                                               const typename Cx<R>::T* __restrict__ side, int n_s,
                                                               int segs, int windows, int nruns, int single_k,
                                                               int kb, int gbits, const LayerList* __restrict__ lists) {
-  using T = typename Cx<R>::T;
+  using A = TrotArith<R, DF>;
+  using T = typename A::T;
+  using V = typename A::V;
+  using W = typename A::W;
+  constexpr int LA = trot_lane_amps<R, DF>();
+  constexpr int HL = Geo<LA>::HL;
+  constexpr int kInterior = Geo<LA>::INTER;
   constexpr int per = 16 / sizeof(T);  // amplitudes per 16-byte unit
-  constexpr int CPL = kLaneAmps / per;
+  constexpr int CPL = LA / per;
+  constexpr int HC = kHalo / per;
+  constexpr int CHUNKS = kInterior / per;
+  constexpr int WPB = trot_threads<R, DF>() / 32;  // warps per block
   extern __shared__ __align__(16) unsigned char trot_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint4* stage_w = reinterpret_cast<uint4*>(trot_smem) + (size_t)wid * 2 * 32 * CPL;  // two buffers
-  R* rot_w = reinterpret_cast<R*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)(kTrotThreads / 32) * 2 * 32 * CPL) +
-             (size_t)wid * 4 * 32;
+  LayerCoefs<W>* coef =
+      reinterpret_cast<LayerCoefs<W>*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)WPB * 2 * 32 * CPL) + wid;
   const int64_t N = 1LL << n_s;
-  const int gw = (int)blockIdx.x * (kTrotThreads / 32) + wid;
+  const int gw = (int)blockIdx.x * WPB + wid;
   if (gw >= nruns) return;  // warp-uniform
   const int v0 = run_start(gw, windows, nruns), v1 = run_start(gw + 1, windows, nruns);
   Window cur;
@@ -320,14 +444,14 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 2 : 1) k_trotte
   cur.full = (int64_t)cur.s * kInterior + kInterior <= N;
   cur.first = true;
   cur.last = v0 + 1 == v1;
-  stage_issue<T>(stage_w, cur, half, side, gw, segs, N, lane);
+  stage_issue<T, LA>(stage_w, cur, half, side, gw, segs, N, lane);
   cp_async_commit();
   int buf = 0;
-  int cached = 0, n_layers = 0, first_o = 0;  // the row pattern whose layers rot_w holds (patterns are >= 1)
+  int cached = 0, n_layers = 0, first_o = 0;  // the row pattern whose layers coef holds (patterns are >= 1)
   for (int v = v0; v < v1; ++v) {
     const bool more = v + 1 < v1;
     if (more)
-      stage_issue<T>(stage_w + (buf ^ 1) * 32 * CPL, window_next(cur, v, v1, segs, N, single_k, kb, gbits), half, side,
+      stage_issue<T, LA>(stage_w + (buf ^ 1) * 32 * CPL, window_next<LA>(cur, v, v1, segs, N, single_k, kb, gbits), half, side,
                      gw, segs, N, lane);
     cp_async_commit();
     cp_async_wait1();  // the current window's copies have landed
@@ -335,151 +459,177 @@ __global__ void __launch_bounds__(kTrotThreads, sizeof(R) == 4 ? 2 : 1) k_trotte
     {
       uint4* stage = stage_w + buf * 32 * CPL;
       // a full window followed by the next segment of its row: carry the left halo over
-      if (more && cur.s + 1 < segs) carry_copy(stage_w + (buf ^ 1) * 32 * CPL, stage, lane, CPL);
+      if (more && cur.s + 1 < segs) carry_copy<CPL, HC, CHUNKS>(stage_w + (buf ^ 1) * 32 * CPL, stage, lane);
       const LayerList* L = lists + cur.pattern;
       if (cur.pattern != cached) {  // a new row pattern (runs change rows rarely)
         cached = cur.pattern;
         n_layers = L->n;
         first_o = L->first_o;
         if (lane < n_layers) {
-          rot_w[4 * lane] = layer_c<R>(L, lane);
-          rot_w[4 * lane + 1] = layer_s<R>(L, lane);
-          rot_w[4 * lane + 2] = layer_w<R>(L, lane);
-          rot_w[4 * lane + 3] = (R)L->form[lane];
+          coef->c[lane] = A::coef(L->cf, L->cl, L->c, lane);
+          coef->s[lane] = A::coef(L->sf, L->sl, L->s, lane);
+          coef->w[lane] = A::coef(L->wf, L->wl, L->w, lane);
+          coef->form[lane] = L->form[lane];
         }
+        __syncwarp();
       }
-      const int64_t g0 = (int64_t)cur.s * kInterior;               // first interior amplitude
-      const int64_t lane0 = g0 - kHalo + (int64_t)lane * kLaneAmps;  // even
+      const int64_t g0 = (int64_t)cur.s * kInterior;        // first interior amplitude
+      const int64_t lane0 = g0 - kHalo + (int64_t)lane * LA;  // even
+      const bool interior = lane >= HL && lane < 32 - HL;
       T* row = half + cur.row * N;
-      T x[kLaneAmps];
+      V x[LA];
       if (cur.full) {
-        uint4* d = reinterpret_cast<uint4*>(x);
+        T t[LA];
+        uint4* d = reinterpret_cast<uint4*>(t);
 #pragma unroll
         for (int q = 0; q < CPL; ++q) d[q] = stage[(lane * CPL + q) ^ (lane & 7)];
-      } else {
-        if (lane > 0 && lane < 31) {
 #pragma unroll
-          for (int q = 0; q < kLaneAmps; ++q) x[q] = lane0 + q < N ? row[lane0 + q] : mk<R>((R)0, (R)0);
-        } else if (lane == 0 && cur.s > 0) {
+        for (int q = 0; q < LA; ++q) x[q] = A::load(t[q]);
+      } else {
+        if (interior) {
+#pragma unroll
+          for (int q = 0; q < LA; ++q) x[q] = lane0 + q < N ? A::load(row[lane0 + q]) : A::zero();
+        } else if (lane < HL && cur.s > 0) {
           // the left halo: from the side buffer at the start of the run, else carried
           if (cur.first) {
 #pragma unroll
-            for (int q = 0; q < kLaneAmps; ++q) x[q] = side[(int64_t)gw * 32 + 16 + q];
+            for (int q = 0; q < LA; ++q) x[q] = A::load(side[(int64_t)gw * 32 + 16 + lane * LA + q]);
           } else {
-            uint4* d = reinterpret_cast<uint4*>(x);
+            T t[LA];
+            uint4* d = reinterpret_cast<uint4*>(t);
 #pragma unroll
-            for (int q = 0; q < CPL; ++q) d[q] = stage[q];
+            for (int q = 0; q < CPL; ++q) d[q] = stage[(lane * CPL + q) ^ (lane & 7)];
+#pragma unroll
+            for (int q = 0; q < LA; ++q) x[q] = A::load(t[q]);
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < kLaneAmps; ++q) x[q] = mk<R>((R)0, (R)0);  // beyond the row ends
+          for (int q = 0; q < LA; ++q) x[q] = A::zero();  // beyond the row ends
         }
       }
       __syncwarp();
       // warp-uniform: every O pair of the interior lanes lies inside the row (no row end in
       // the window but possibly the halos', whose values do not reach the interior)
       const bool away = cur.full && g0 >= 2 && g0 + kInterior + 1 <= N;
-      if (away) {
+      int n_f1 = 0;  // double-float kernel: layers in the second form
+      if constexpr (DF) {
+        if (away) {
+          for (int l = 0; l < n_layers; ++l) {
+            const bool e_layer = ((l + first_o) & 1) == 0;
+            const int f1 = coef->form[l];
+            n_f1 += f1;
+            if (f1) layer_df<true>(x, e_layer, df_neg(coef->w[l]));
+            else layer_df<false>(x, e_layer, coef->w[l]);
+          }
+        }
+      } else if (away) {
         // layers alternate E, O: an O layer first on its own, then (E, O) pairs in one loop
         // body (the pair's second layer writes its outputs back into the registers the loop
         // carries, so no register copies are needed between layers), then a last E layer
         int l = 0;
         if (first_o && n_layers > 0) {
-          if (rot_w[3] != (R)0) layer_factored<true>(x, false, rot_w[2]);
-          else layer_factored<false>(x, false, rot_w[2]);
+          if (coef->form[0] != 0) layer_factored<true, LA>(x, false, coef->w[0]);
+          else layer_factored<false, LA>(x, false, coef->w[0]);
           l = 1;
         }
         for (; l + 1 < n_layers; l += 2) {
-          const R we = rot_w[4 * l + 2], wo = rot_w[4 * l + 6];
-          if (rot_w[4 * l + 3] != (R)0) {
-            layer_factored<true>(x, true, we);
-            if (rot_w[4 * l + 7] != (R)0) layer_factored<true>(x, false, wo);
-            else layer_factored<false>(x, false, wo);
+          const W we = coef->w[l], wo = coef->w[l + 1];
+          if (coef->form[l] != 0) {
+            layer_factored<true, LA>(x, true, we);
+            if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
+            else layer_factored<false, LA>(x, false, wo);
           } else {
-            layer_factored<false>(x, true, we);
-            if (rot_w[4 * l + 7] != (R)0) layer_factored<true>(x, false, wo);
-            else layer_factored<false>(x, false, wo);
+            layer_factored<false, LA>(x, true, we);
+            if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
+            else layer_factored<false, LA>(x, false, wo);
           }
         }
         if (l < n_layers) {
-          if (rot_w[4 * l + 3] != (R)0) layer_factored<true>(x, true, rot_w[4 * l + 2]);
-          else layer_factored<false>(x, true, rot_w[4 * l + 2]);
+          if (coef->form[l] != 0) layer_factored<true, LA>(x, true, coef->w[l]);
+          else layer_factored<false, LA>(x, true, coef->w[l]);
         }
       }
       // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
-      const bool in_ok = lane0 >= 0 && lane0 + kLaneAmps - 2 <= N - 1;
-      const bool right_ok = lane < 31 && lane0 + kLaneAmps - 1 >= 1 && lane0 + kLaneAmps <= N - 1;
+      const bool in_ok = lane0 >= 0 && lane0 + LA - 2 <= N - 1;
+      const bool right_ok = lane < 31 && lane0 + LA - 1 >= 1 && lane0 + LA <= N - 1;
       const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
       for (int l = 0; l < (away ? 0 : n_layers); ++l) {
-        const R c = rot_w[4 * l], sn = rot_w[4 * l + 1];
+        const W c = coef->c[l], sn = coef->s[l];
         if (((l + first_o) & 1) == 0) {
           // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
 #pragma unroll
-          for (int q = 0; q < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+          for (int q = 0; q < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
         } else {
-          const T right = shfl_down1(x[0]);           // next lane's first amplitude
-          const T left = shfl_up1(x[kLaneAmps - 1]);  // previous lane's last amplitude
-          if (in_ok) {
+          const V right = shfl_down1(x[0]);           // next lane's first amplitude
+          const V left = shfl_up1(x[LA - 1]);  // previous lane's last amplitude
+          if (in_ok && !DF) {  // (the double-float kernel keeps one copy of this rare path)
 #pragma unroll
-            for (int q = 1; q + 1 < kLaneAmps; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+            for (int q = 1; q + 1 < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
           } else {
 #pragma unroll
-            for (int q = 1; q + 1 < kLaneAmps; q += 2) {
+            for (int q = 1; q + 1 < LA; q += 2) {
               const int64_t j = lane0 + q;
               if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
             }
           }
-          if (right_ok) {  // (this lane's last a, next lane's first b): a <- c a + i s b
-            const T a = x[kLaneAmps - 1];
-            x[kLaneAmps - 1] = mk<R>(c * a.x - sn * right.y, c * a.y + sn * right.x);
-          }
-          if (left_ok) {  // (previous lane's last a, this lane's first b): b <- i s a + c b
-            const T b = x[0];
-            x[0] = mk<R>(c * b.x - sn * left.y, c * b.y + sn * left.x);
-          }
+          if (right_ok) x[LA - 1] = rot1(x[LA - 1], right, c, sn);  // a <- c a + i s b
+          if (left_ok) x[0] = rot1(x[0], left, c, sn);                            // b <- i s a + c b
         }
       }
       {
-        T ph;
-        if constexpr (sizeof(R) == 4) ph = away ? mk<R>(L->pc2f, L->ps2f) : mk<R>(L->pcf, L->psf);
-        else ph = away ? mk<R>(L->pc2, L->ps2) : mk<R>(L->pc, L->ps);
+        V ph;
+        if (away) {
+          ph.x = A::coef1(L->pc2f, L->pc2l, L->pc2);
+          ph.y = A::coef1(L->ps2f, L->ps2l, L->ps2);
+          if constexpr (DF) {
+            // (-i)^n_f1: the second form's factors are sin th, not i sin th
+            for (int j = 0; j < (n_f1 & 3); ++j) {
+              const auto t = ph.x;
+              ph.x = ph.y;
+              ph.y = df_neg(t);
+            }
+          }
+        } else {
+          ph.x = A::coef1(L->pcf, L->pcl, L->pc);
+          ph.y = A::coef1(L->psf, L->psl, L->ps);
+        }
 #pragma unroll
-        for (int q = 0; q < kLaneAmps; ++q) x[q] = cmul(x[q], ph);
+        for (int q = 0; q < LA; ++q) x[q] = phase_mul(A::finish(x[q]), ph);
       }
       if (cur.full) {
-        if (lane > 0 && lane < 31) {
-          const uint4* sx = reinterpret_cast<const uint4*>(x);
+        if (interior) {
+          T t[LA];
+#pragma unroll
+          for (int q = 0; q < LA; ++q) t[q] = A::store(x[q]);
+          const uint4* sx = reinterpret_cast<const uint4*>(t);
 #pragma unroll
           for (int q = 0; q < CPL; ++q) stage[(lane * CPL + q) ^ (lane & 7)] = sx[q];
         }
         __syncwarp();
         uint4* dst = reinterpret_cast<uint4*>(row + g0);
-        constexpr int chunks = kInterior / per;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
+        for (int q = 0; q < (CHUNKS + 31) / 32; ++q) {
           const int c = q * 32 + lane;
-          if (c < chunks) {
-            const int wc = c + CPL;
-            dst[c] = stage[wc ^ ((wc / CPL) & 7)];
-          }
+          if (c < CHUNKS) dst[c] = stage[swz<CPL>(c + HC)];
         }
-      } else if (lane > 0 && lane < 31) {
+      } else if (interior) {
 #pragma unroll
-        for (int q = 0; q < kLaneAmps; ++q)
-          if (lane0 + q < N) row[lane0 + q] = x[q];
+        for (int q = 0; q < LA; ++q)
+          if (lane0 + q < N) row[lane0 + q] = A::store(x[q]);
       }
     }
-    __syncwarp();  // this buffer is free for the next issue, the rotation table for a new pattern
-    if (more) cur = window_next(cur, v, v1, segs, N, single_k, kb, gbits);
+    __syncwarp();  // this buffer is free for the next issue, the coefficients for a new pattern
+    if (more) cur = window_next<LA>(cur, v, v1, segs, N, single_k, kb, gbits);
     buf ^= 1;
   }
 }
 
-template <class R>
+template <class R, bool DF>
 size_t trotter_smem() {
-  constexpr int per = 16 / sizeof(typename Cx<R>::T);
-  constexpr int CPL = kLaneAmps / per;
-  return (size_t)(kTrotThreads / 32) * (2 * 32 * CPL * 16 + 4 * 32 * sizeof(R));
+  using A = TrotArith<R, DF>;
+  constexpr int per = 16 / sizeof(typename A::T);
+  constexpr int CPL = trot_lane_amps<R, DF>() / per;
+  return (size_t)(trot_threads<R, DF>() / 32) * (2 * 32 * CPL * 16 + sizeof(LayerCoefs<typename A::W>));
 }
 
 __global__ void k_interleave(const double* __restrict__ re, const double* __restrict__ im, int64_t n,
@@ -488,19 +638,21 @@ __global__ void k_interleave(const double* __restrict__ re, const double* __rest
     out[i] = make_double2(re[i], im ? im[i] : 0.0);
 }
 
-template <class R>
+template <class R, bool DF>
 hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st) {
   using T = typename Cx<R>::T;
-  const int64_t segs = trotter_segments(p.N);
-  T* side = (T*)p.d_scratch;  // sized by the planner for R * segs * 32 amplitudes
+  constexpr int LA = trot_lane_amps<R, DF>();
+  const int64_t segs = (p.N + Geo<LA>::INTER - 1) / Geo<LA>::INTER;
+  T* side = (T*)p.d_scratch;  // sized by the planner for min(R * segs, kMaxRuns) * 32 amplitudes
   const LayerList* lists = (const LayerList*)p.d_trot_lists;
-  const size_t smem = trotter_smem<R>();
-  auto kern = k_trotter_pass<R>;
+  const size_t smem = trotter_smem<R, DF>();
+  auto kern = k_trotter_pass<R, DF>;
   HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTrotThreads, smem));
+  constexpr int TH = trot_threads<R, DF>();
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TH, smem));
   if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass does not fit an SM");
   for (const TrotPassDesc& d : p.trot_pass[adjoint ? 1 : 0]) {
     // pass rows: those with clock bit single_k set, or with a nonzero pattern of the group
@@ -508,23 +660,23 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
     const int64_t windows = rows * segs;
     if (windows < 1) continue;
     if (windows > 0x7fffffffLL) return fail(HHL_ERR_UNSUPPORTED, "Trotter pass has too many windows");
-    const int64_t max_warps = (int64_t)occ * sms * (kTrotThreads / 32);
-    int64_t runs = std::min<int64_t>(windows, max_warps);  // <= R * segs: the side buffer holds them
+    const int64_t max_warps = (int64_t)occ * sms * (TH / 32);
+    int64_t runs = std::min<int64_t>(std::min<int64_t>(windows, max_warps), kMaxRuns);  // the side buffer holds them
     if (const char* env = getenv("HHL_TROTTER_RUNS")) {    // testing override: fewer, longer runs
       const long long cap = atoll(env);
       if (cap >= 1) runs = std::min<int64_t>(runs, cap);
     }
     const int nruns = (int)runs;
-    const unsigned pgrid = (unsigned)((nruns + kTrotThreads / 32 - 1) / (kTrotThreads / 32));
+    const unsigned pgrid = (unsigned)((nruns + TH / 32 - 1) / (TH / 32));
     HHL_PROF_BEGIN(st);
-    k_trotter_bounds<R><<<(unsigned)((nruns * 32 + 255) / 256), 256, 0, st>>>((const T*)half, side, p.n_s, (int)segs,
+    k_trotter_bounds<R, LA><<<(unsigned)((nruns * 32 + 255) / 256), 256, 0, st>>>((const T*)half, side, p.n_s, (int)segs,
                                                                                 (int)windows, nruns, d.single_k, d.kb,
                                                                                 d.gbits);
     HHL_LAUNCH_CHECK("k_trotter_bounds");
     HHL_PROF_BEGIN(st);
-    kern<<<pgrid, kTrotThreads, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)windows, nruns,
+    kern<<<pgrid, TH, smem, st>>>((T*)half, side, p.n_s, (int)segs, (int)windows, nruns,
                                                          d.single_k, d.kb, d.gbits, lists + d.list_off);
-    HHL_LAUNCH_CHECK("k_trotter_pass");
+    HHL_LAUNCH_CHECK(DF ? "k_trotter_pass_df" : "k_trotter_pass");
   }
   return HHL_OK;
 }
@@ -585,25 +737,34 @@ void build_list(const Plan& p, const std::vector<int>& bits, bool adjoint, int w
   out->ps = sg * sin(e_time * dh);
   out->pc2 = out->pc * fr - out->ps * fi;
   out->ps2 = out->pc * fi + out->ps * fr;
-  out->pc2f = (float)out->pc2;
-  out->ps2f = (float)out->ps2;
-  out->pcf = (float)out->pc;
-  out->psf = (float)out->ps;
+  df_split(out->pc2, &out->pc2f, &out->pc2l);
+  df_split(out->ps2, &out->ps2f, &out->ps2l);
+  df_split(out->pc, &out->pcf, &out->pcl);
+  df_split(out->ps, &out->psf, &out->psl);
   for (int l = 0; l < out->n; ++l) {
-    out->cf[l] = (float)out->c[l];
-    out->sf[l] = (float)out->s[l];
-    out->wf[l] = (float)out->w[l];
+    df_split(out->c[l], &out->cf[l], &out->cl[l]);
+    df_split(out->s[l], &out->sf[l], &out->sl[l]);
+    df_split(out->w[l], &out->wf[l], &out->wl[l]);
   }
 }
 
 }  // namespace
 
-int64_t trotter_segments(int64_t N) { return (N + kInterior - 1) / kInterior; }
+// Side-buffer amplitudes a Trotter plan needs: 32 per warp of a pass, at most one warp per
+// window (the double-float kernel's windows have the smallest interior) and kMaxRuns warps.
+int64_t trotter_side_amps(int64_t N, int64_t R) {
+  const int64_t segs = (N + Geo<8>::INTER - 1) / Geo<8>::INTER;
+  return std::min<int64_t>(R * segs, kMaxRuns) * 32;
+}
 
 hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t st) {
   if (p.d_scratch == nullptr || p.d_trot_lists == nullptr) return fail(HHL_ERR_INVALID_ARG, "Trotter plan without tables");
-  return p.prec == HHL_PREC_C64 ? trotter_impl<float>(p, half, adjoint, st)
-                                : trotter_impl<double>(p, half, adjoint, st);
+  if (p.prec == HHL_PREC_C64) return trotter_impl<float, false>(p, half, adjoint, st);
+  // complex128: double-float on the FP32 pipe unless HHL_FP64_PIPE=1 (the FP64 form, kept for
+  // comparison and tests)
+  const char* env = getenv("HHL_FP64_PIPE");
+  if (env != nullptr && atoi(env) != 0) return trotter_impl<double, false>(p, half, adjoint, st);
+  return trotter_impl<double, true>(p, half, adjoint, st);
 }
 
 size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table) {

@@ -322,11 +322,15 @@ def test_qft_whole_register_parity(hhl, monkeypatch, prec, n, states, plain):
         assert np.abs(back[j] - psi).max() <= rel * np.abs(psi).max()
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c128-fp64pipe"])
 @pytest.mark.parametrize("dt,r_max", [(3.0, 0), (0.5, 40), (50.0, 7)])
-def test_trotter_parity(hhl, prec, dt, r_max):
+def test_trotter_parity(hhl, monkeypatch, prec, dt, r_max):
     """Controlled Strang products (several passes, odd and even pass counts) against the
-    oracle's gate-by-gate Trotter circuit."""
+    oracle's gate-by-gate Trotter circuit; complex128 in double-float arithmetic (default) and
+    on the FP64 pipe (HHL_FP64_PIPE=1)."""
+    if prec == "c128-fp64pipe":
+        monkeypatch.setenv("HHL_FP64_PIPE", "1")
+        prec = "c128"
     n_s, n_c = 5, 4
     diag, off, b, walls = problem("poiseuille", n_s)
     pl = _oracle_plan(diag, off, n_c, "range_fill")
