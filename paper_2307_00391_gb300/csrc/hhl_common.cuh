@@ -48,6 +48,7 @@ template <class R> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
 
+
 template <class R> __host__ __device__ __forceinline__ typename Cx<R>::T mk(R re, R im) {
   typename Cx<R>::T z; z.x = re; z.y = im; return z;
 }
@@ -70,6 +71,10 @@ template <class T, class S> __host__ __device__ __forceinline__ T cscale(T a, S 
 // one FP64 addition.
 struct df {
   float h, l;
+  df() = default;
+  __host__ __device__ constexpr df(float h_, float l_) : h(h_), l(l_) {}
+  __host__ __device__ explicit constexpr df(int v) : h((float)v), l(0.0f) {}
+  __host__ __device__ explicit df(double v) : h((float)v), l((float)(v - (double)(float)v)) {}  // (set-up only)
 };
 struct dfc {
   df x, y;  // real, imaginary
@@ -152,6 +157,7 @@ __device__ __forceinline__ double df_f2d(float f) {
 }
 __device__ __forceinline__ double df_to_double(df v) { return __dadd_rn(df_f2d(v.h), df_f2d(v.l)); }
 
+template <> struct Cx<df> { using T = dfc; };
 __device__ __forceinline__ dfc dfc_from(double2 z) { return {df_from_double(z.x), df_from_double(z.y)}; }
 __device__ __forceinline__ double2 dfc_to(dfc z) { return make_double2(df_to_double(z.x), df_to_double(z.y)); }
 __device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
@@ -160,6 +166,32 @@ __device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
   return {df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
 }
 __device__ __forceinline__ dfc dfc_scale(dfc a, df s) { return {df_mul(a.x, s), df_mul(a.y, s)}; }
+// Lazy forms (no final renormalisation; the tail may grow to a few units in the last place of
+// the head, which the next error-free head operation absorbs; the store's exact FP64
+// reconstruction takes any head and tail).
+__device__ __forceinline__ df df_add_lazy(df a, df b) {
+  const df s = df_two_sum(a.h, b.h);
+  return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ df df_mul_lazy(df a, df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return {p, e};
+}
+// Operators, so that the complex templates (cadd, csub, cmul, cscale, mk) serve dfc as they
+// serve float2 and double2 (Cx<df>::T = dfc); they are the lazy forms.
+__device__ __forceinline__ df operator+(df a, df b) { return df_add_lazy(a, b); }
+__device__ __forceinline__ df operator-(df a) { return df_neg(a); }
+__device__ __forceinline__ df operator-(df a, df b) { return df_add_lazy(a, df_neg(b)); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul_lazy(a, b); }
+__device__ __forceinline__ df operator*(df a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  return {p, __fmaf_rn(a.l, b, __fmaf_rn(a.h, b, -p))};
+}
+// the double-float pair of an FP64 value (FP64 operations: table set-up only)
+__device__ __forceinline__ df df_of(double v) { return df(v); }
 // host: the double-float pair of an FP64 constant
 inline void df_split(double v, float* h, float* l) {
   *h = (float)v;

@@ -108,14 +108,21 @@ __device__ void fill_twiddles(typename Cx<R>::T* t0, typename Cx<R>::T* t1, int 
   const int n1 = twiddle_entries(m) - 64;
   for (int j = threadIdx.x; j < 64 + n1; j += blockDim.x) {
     const int e = j < 64 ? j : 64 * (j - 64);
-    R s, c;
-    if constexpr (sizeof(R) == 4) {
-      sincospif(-2.0f * (float)(e & (L - 1)) / (float)L, &s, &c);
-    } else {
+    if constexpr (std::is_same<R, df>::value) {  // double-float from the FP64 values
+      double s, c;
       sincospi(-2.0 * (double)(e & (L - 1)) / (double)L, &s, &c);
+      if (j < 64) t0[j] = mk<df>(df_of(c), df_of(s));
+      else t1[j - 64] = mk<df>(df_of(c), df_of(s));
+    } else {
+      R s, c;
+      if constexpr (sizeof(R) == 4) {
+        sincospif(-2.0f * (float)(e & (L - 1)) / (float)L, &s, &c);
+      } else {
+        sincospi(-2.0 * (double)(e & (L - 1)) / (double)L, &s, &c);
+      }
+      if (j < 64) t0[j] = mk<R>(c, s);
+      else t1[j - 64] = mk<R>(c, s);
     }
-    if (j < 64) t0[j] = mk<R>(c, s);
-    else t1[j - 64] = mk<R>(c, s);
   }
 }
 
@@ -137,9 +144,25 @@ __constant__ float kRoot16f[16][2] = {
 
 // The root for the amplitude precision (FP32 kernels read FP32 constants: converting an FP64
 // constant costs a pass through GB300's narrow FP64 pipe).
+// Double-float remainders of those roots (kRoot16 - kRoot16f, evaluated in FP64 at compile time).
+#define HHL_DFL(v) ((float)((v) - (double)(float)(v)))
+#define HHL_R16(c, s) {HHL_DFL(c), HHL_DFL(s)}
+__constant__ float kRoot16l[16][2] = {
+    HHL_R16(1.0, 0.0), HHL_R16(0.92387953251128674, -0.38268343236508978),
+    HHL_R16(0.70710678118654752, -0.70710678118654752), HHL_R16(0.38268343236508978, -0.92387953251128674),
+    HHL_R16(0.0, -1.0), HHL_R16(-0.38268343236508978, -0.92387953251128674),
+    HHL_R16(-0.70710678118654752, -0.70710678118654752), HHL_R16(-0.92387953251128674, -0.38268343236508978),
+    HHL_R16(-1.0, 0.0), HHL_R16(-0.92387953251128674, 0.38268343236508978),
+    HHL_R16(-0.70710678118654752, 0.70710678118654752), HHL_R16(-0.38268343236508978, 0.92387953251128674),
+    HHL_R16(0.0, 1.0), HHL_R16(0.38268343236508978, 0.92387953251128674),
+    HHL_R16(0.70710678118654752, 0.70710678118654752), HHL_R16(0.92387953251128674, 0.38268343236508978)};
+#undef HHL_R16
+#undef HHL_DFL
+
 template <class R>
 __device__ __forceinline__ R root16(int k, int part) {
-  if constexpr (sizeof(R) == 4) return kRoot16f[k][part];
+  if constexpr (std::is_same<R, df>::value) return df{kRoot16f[k][part], kRoot16l[k][part]};
+  else if constexpr (sizeof(R) == 4) return kRoot16f[k][part];
   else return (R)kRoot16[k][part];
 }
 
@@ -718,13 +741,35 @@ struct SplitArgs {
   int log_cb;          // 2^log_cb column blocks (tiles) per row
   double scale;        // pass B: 1 / sqrt(2^m); Hadamard pass: final scale
   float scale_f;       // the same in FP32 (GB300's FP64 pipe is narrow: no per-thread conversions)
+  float scale_l;       // scale - scale_f (the double-float kernels)
   int scaled;          // scale != 1
 };
 
 template <class R>
 __device__ __forceinline__ R split_scale(const SplitArgs& a) {
-  if constexpr (sizeof(R) == 4) return a.scale_f;
+  if constexpr (std::is_same<R, df>::value) return df{a.scale_f, a.scale_l};
+  else if constexpr (sizeof(R) == 4) return a.scale_f;
   else return a.scale;
+}
+
+// The complex128 passes compute in double-float (dfc in shared memory, the same 16 bytes as the
+// double2 it replaces): a landed tile is converted in place once, and converted back as it is
+// stored; tables in FP64 (the rotation table) are converted as they are read.
+template <class T>
+constexpr bool is_dfc() { return std::is_same<T, dfc>::value; }
+template <class T>
+__device__ __forceinline__ T amp_in(const void* table, long long i) {
+  if constexpr (is_dfc<T>()) return dfc_from(static_cast<const double2*>(table)[i]);
+  else return static_cast<const T*>(table)[i];
+}
+template <class T>
+__device__ __forceinline__ uint4 unit_out(uint4 v) {
+  if constexpr (is_dfc<T>()) {
+    const double2 d = dfc_to(*reinterpret_cast<const dfc*>(&v));
+    return *reinterpret_cast<const uint4*>(&d);
+  } else {
+    return v;
+  }
 }
 
 template <class T>
@@ -785,7 +830,9 @@ __device__ __forceinline__ void group_butterflies(T (&v)[1 << RB], int lo, int l
 // (2^NB rows). Tile row j is register index lo_fixed + (j << b0) + (fixed bits above).
 // With a whole-register transform (inner_base >= 0) the tile's columns are register bits
 // too: the index below the pass's bits is inner_base + w + ((lo_fixed + (lo << b0)) << shift).
-template <class T, int NB, int TB, int RB, bool DIT, int MODE, int LW, class TW>
+// CV (double-float tiles): the tile still holds the landed FP64 amplitudes, converted as this
+// first pass loads them (each element is loaded and stored back by the same thread).
+template <class T, int NB, int TB, int RB, bool DIT, int MODE, int LW, bool CV, class TW>
 __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj, int inner_base,
                                           int shift) {
   constexpr int W = 1 << LW, G = 1 << RB;
@@ -799,7 +846,10 @@ __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, con
     T* q = X + (row0 << LW) + w;
     T v[G];
 #pragma unroll
-    for (int x = 0; x < G; ++x) v[x] = q[x << (TB + LW)];
+    for (int x = 0; x < G; ++x) {
+      if constexpr (CV) v[x] = amp_in<T>(q, (long long)x << (TB + LW));
+      else v[x] = q[x << (TB + LW)];
+    }
     if (inner_base >= 0)
       group_butterflies<T, RB, DIT, MODE>(v, inner_base + w + ((lo_fixed + (lo << b0)) << shift), shift + b0 + TB, m,
                                           tw, conj);
@@ -812,7 +862,8 @@ __device__ __forceinline__ void tile_pass(T* X, int b0, int lo_fixed, int m, con
 
 // All NB stages of a tile in passes of at most MR bits (DIF: high bits first), a barrier
 // after each pass.
-template <class T, int NB, bool DIT, int MODE, int LW = SplitGeom<T>::LW, int Q = 0, int DONE = 0, class TW>
+template <class T, int NB, bool DIT, int MODE, int LW = SplitGeom<T>::LW, int Q = 0, int DONE = 0, bool CV = false,
+          class TW>
 __device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, const TW& tw, bool conj,
                                             int inner_base = -1, int shift = 0) {
   constexpr int MR = SplitGeom<T>::MR;
@@ -820,9 +871,9 @@ __device__ __forceinline__ void tile_stages(T* X, int b0, int lo_fixed, int m, c
   if constexpr (Q < NPASS) {
     constexpr int RB = (NB - DONE) / (NPASS - Q);
     constexpr int TB = DIT ? DONE : NB - DONE - RB;
-    tile_pass<T, NB, TB, RB, DIT, MODE, LW>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
+    tile_pass<T, NB, TB, RB, DIT, MODE, LW, CV && Q == 0>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
     __syncthreads();
-    tile_stages<T, NB, DIT, MODE, LW, Q + 1, DONE + RB>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
+    tile_stages<T, NB, DIT, MODE, LW, Q + 1, DONE + RB, false>(X, b0, lo_fixed, m, tw, conj, inner_base, shift);
   }
 }
 
@@ -870,6 +921,7 @@ __device__ __forceinline__ void tile_store(T* base, const T* X, long long row_un
 #pragma unroll
       for (int q = 0; q < per; ++q) t[q] = cscale(t[q], scale);
     }
+    v = unit_out<T>(v);
     if constexpr (CS) __stcs(dst + k * step, v);  // evict-first in L2
     else dst[k * step] = v;
   }
@@ -906,6 +958,8 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
   using T = typename Cx<R>::T;
   constexpr int upr = kSplitSegBytes / 16;
   constexpr int per = 16 / sizeof(T);
+  constexpr int LWT = SplitGeom<T>::LW;
+  constexpr bool CVT = is_dfc<T>();  // the landed tile is converted by its first pass
   T* dst = static_cast<T*>(a.dst) + q.base_amp;
   if (WHOLE) {
     // whole-register QFT (DIF, + sign) or inverse QFT (DIT, - sign)
@@ -913,23 +967,22 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
     else tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, mt, tw, false, q.inner_base, a.lo);
     tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitDif) {
-    tile_stages<T, NB, false, 0>(X, a.b0, q.lo_fixed, a.m, tw, false);
+    tile_stages<T, NB, false, 0, LWT, 0, 0, CVT>(X, a.b0, q.lo_fixed, a.m, tw, false);
     tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitDit) {
-    tile_stages<T, NB, true, 0>(X, a.b0, q.lo_fixed, a.m, tw, true);
+    tile_stages<T, NB, true, 0, LWT, 0, 0, CVT>(X, a.b0, q.lo_fixed, a.m, tw, true);
     tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, (R)1, false);
   } else if (OP == kSplitHad) {
-    tile_stages<T, NB, false, 1>(X, a.b0, q.lo_fixed, a.m, tw, false);
+    tile_stages<T, NB, false, 1, LWT, 0, 0, CVT>(X, a.b0, q.lo_fixed, a.m, tw, false);
     tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
   } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
-    tile_stages<T, NB, false, 0>(X, 0, 0, a.m, tw, false);
+    tile_stages<T, NB, false, 0, LWT, 0, 0, CVT>(X, 0, 0, a.m, tw, false);
     const R s = split_scale<R>(a);
-    const T* rot = static_cast<const T*>(a.rot);
     uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + q.base_amp);
     for (int u = threadIdx.x; u < (upr << NB); u += kSplitThreads) {
       const int j = u / upr, h = u - j * upr;
       const int y = bitrev_m(j + (q.hi_fixed << NB), a.m);
-      const T r = rot[y];
+      const T r = amp_in<T>(a.rot, y);
       uint4 xv = reinterpret_cast<uint4*>(X)[u];
       uint4 keep, yv;
       T* xt = reinterpret_cast<T*>(&xv);
@@ -944,7 +997,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
       }
       reinterpret_cast<uint4*>(X)[u] = xv;
       if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
-      else cos_out[(long long)y * row_units + h] = keep;
+      else cos_out[(long long)y * row_units + h] = unit_out<T>(keep);
     }
     __syncthreads();
     tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
@@ -969,7 +1022,7 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
   T* Xb = t0 + (WHOLE ? 1024 : twiddle_entries(a.m));  // two tile buffers (double buffering), then Y
   T* Y = Xb + 2 * tile_amps;
   if (!WHOLE && OP != kSplitHad) fill_twiddles<R>(t0, t1, a.m);
-  if (WHOLE) fill_twiddle4<R>(t0, a.lo + a.m);  // first read after the barrier of the first tile
+  if constexpr (WHOLE) fill_twiddle4<R>(t0, a.lo + a.m);  // first read after the barrier of the first tile
   using TW = typename std::conditional<WHOLE, Twiddle4<T>, Twiddle<T>>::type;
   TW tw;
   if constexpr (WHOLE) {
@@ -1043,6 +1096,7 @@ hhl_status launch_split(SplitArgs a, int outer, cudaStream_t st, const char* nam
   a.log_cb = a.lo - SplitGeom<T>::LW;
   a.region = 1LL << (a.lo + a.m);
   a.scale_f = (float)a.scale;
+  a.scale_l = (float)(a.scale - (double)a.scale_f);
   a.scaled = a.scale != 1.0;
   a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
   switch (a.nb) {
@@ -1158,6 +1212,7 @@ void split_finish(SplitArgs& a, int outer) {
   a.log_cb = a.lo - SplitGeom<T>::LW;
   a.region = 1LL << (a.lo + a.m);
   a.scale_f = (float)a.scale;
+  a.scale_l = (float)(a.scale - (double)a.scale_f);
   a.scaled = a.scale != 1.0;
   a.tiles = ((long long)outer << (a.log_cb + a.m - a.nb));
 }
@@ -1734,6 +1789,12 @@ inline hhl_status hadamard_group(void* base, int lo, int m, int outer, cudaStrea
   return launch_group<float, 1, false>(g, outer, st, "k_hadamard_group");
 }
 
+// Complex128 split passes on the FP64 pipe instead of double-float (HHL_FP64_PIPE=1).
+inline bool fp64_pipe() {
+  const char* env = getenv("HHL_FP64_PIPE");
+  return env != nullptr && atoi(env) != 0;
+}
+
 }  // namespace
 
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
@@ -1747,8 +1808,10 @@ hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
     return p.full ? clock_block_impl<float, true>(p, state, st) : clock_block_impl<float, false>(p, state, st);
   }
   if (clock_cluster_applies<double>(p)) return clock_block_cluster<double>(p, state, st);
-  if (split_applies<double>(p.n_s, p.n_c, half))
-    return p.full ? clock_block_split<double, true>(p, state, st) : clock_block_split<double, false>(p, state, st);
+  if (split_applies<double>(p.n_s, p.n_c, half)) {
+    if (fp64_pipe()) return p.full ? clock_block_split<double, true>(p, state, st) : clock_block_split<double, false>(p, state, st);
+    return p.full ? clock_block_split<df, true>(p, state, st) : clock_block_split<df, false>(p, state, st);
+  }
   return p.full ? clock_block_impl<double, true>(p, state, st) : clock_block_impl<double, false>(p, state, st);
 }
 
@@ -1768,8 +1831,8 @@ hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {
   }
   if (hadamard_cluster_applies<double>(p.n_s, p.n_c, half_amps))
     return hadamard_cluster<double>(base, p.n_s, p.n_c, outer, st);
-  return split_applies<double>(p.n_s, p.n_c, half_amps) ? hadamard_split<double>(base, p.n_s, p.n_c, outer, st)
-                                                        : register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
+  if (!split_applies<double>(p.n_s, p.n_c, half_amps)) return register_transform_impl<double>(base, n, p.n_s, p.n_c, 2, st);
+  return fp64_pipe() ? hadamard_split<double>(base, p.n_s, p.n_c, outer, st) : hadamard_split<df>(base, p.n_s, p.n_c, outer, st);
 }
 
 hhl_status launch_qft_whole(void* state, int n, int outer, int direction, int prec, cudaStream_t st) {

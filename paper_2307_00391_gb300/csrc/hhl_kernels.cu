@@ -10,6 +10,8 @@
 
 #include <type_traits>
 
+#include <stdlib.h>
+
 #include "hhl_common.cuh"
 
 namespace hhl {
@@ -181,6 +183,37 @@ __device__ __forceinline__ void kahan_add(R& s, R& c, R p) {
   const R t = s + y;
   c = (t - s) - y;
   s = t;
+}
+
+// Complex128 form on the FP32 pipe: the FP64 amplitudes split into double-float with integer
+// operations, |z|^2 and the running sums in double-float (about 48 significant bits per
+// partial; the block and grid totals in FP64).
+__global__ void k_measure_sums_df(const double2* __restrict__ S, int64_t half, int64_t N, double* acc) {
+  const int64_t units = 2 * half;
+  constexpr int U = 4;  // loads in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  df s[3] = {df(0), df(0), df(0)};
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < units; i0 += U * stride) {
+    double2 z[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (i0 + k * stride < units) z[k] = S[i0 + k * stride];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i >= units) break;
+      const df re = df_from_double(z[k].x), im = df_from_double(z[k].y);
+      const df p = df_add(df_mul(re, re), df_mul(im, im));
+      if (i < half) {
+        s[0] = df_add(s[0], p);
+      } else {
+        s[1] = df_add(s[1], p);
+        if (i - half < N) s[2] = df_add(s[2], p);
+      }
+    }
+  }
+  double a[3] = {df_to_double(s[0]), df_to_double(s[1]), df_to_double(s[2])};
+  block_sum_atomic<3>(a, acc);
 }
 
 template <class R>
@@ -577,8 +610,12 @@ hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStr
     HHL_PROF_BEGIN(st);
     k_measure_finish<float><<<gf, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal, out);
   } else {
+    const char* env = getenv("HHL_FP64_PIPE");
     HHL_PROF_BEGIN(st);
-    k_measure_sums<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
+    if (env != nullptr && atoi(env) != 0)
+      k_measure_sums<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
+    else
+      k_measure_sums_df<<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
     HHL_LAUNCH_CHECK("k_measure_sums");
     HHL_PROF_BEGIN(st);
     k_measure_finish<double><<<gf, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, out);

@@ -163,9 +163,12 @@ def test_shots_match_the_oracle_sampler(hhl, prec):
     np.testing.assert_array_equal(counts.cpu().numpy(), o.sample_counts(vv_in, u))
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c128-fp64pipe"])
 @pytest.mark.parametrize("flow", ["poiseuille", "couette"])
-def test_measure_and_dissipation_parity(hhl, prec, flow):
+def test_measure_and_dissipation_parity(hhl, monkeypatch, prec, flow):
+    if prec == "c128-fp64pipe":
+        monkeypatch.setenv("HHL_FP64_PIPE", "1")
+        prec = "c128"
     n_s, n_c = 6, 7
     diag, off, b, walls = problem(flow, n_s)
     nu = 0.05
@@ -689,8 +692,8 @@ def test_cluster_clock_block_parity(hhl, monkeypatch, prec, flow, n_s, n_c):
     assert prof["k_clock_cluster"][0] == 1 and prof["k_hadamard_cluster"][0] == 1
 
 
-@pytest.mark.parametrize("prec,group", [("c128", None), ("c64", None), ("c64", "8,64"), ("c64", "2,1"),
-                                        ("c64", "16,1"), ("c64", "4,1"), ("c64", "1,1")])
+@pytest.mark.parametrize("prec,group", [("c128", None), ("c128-fp64pipe", None), ("c64", None), ("c64", "8,64"),
+                                        ("c64", "2,1"), ("c64", "16,1"), ("c64", "4,1"), ("c64", "1,1")])
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("flow,n_s,n_c", [("couette", 5, 8), ("poiseuille", 6, 9), ("couette", 7, 11),
                                           ("poiseuille", 6, 12), ("couette", 5, 13)])
@@ -699,8 +702,11 @@ def test_split_register_passes_parity(hhl, monkeypatch, prec, group, full, flow,
     take), forced on small states, stage by stage against the oracle: streaming passes
     (group None) or L2-staged group passes with G CTAs per cluster and an L2 budget in MiB
     ("G,MiB": a budget of 1 MiB leaves fewer clusters than column blocks, so each cluster
-    runs several groups)."""
+    runs several groups); complex128 in double-float arithmetic (default) and on the FP64 pipe."""
     import torch
+    if prec == "c128-fp64pipe":
+        monkeypatch.setenv("HHL_FP64_PIPE", "1")
+        prec = "c128"
     monkeypatch.setenv("HHL_FFT_SPLIT", "1")
     monkeypatch.setenv("HHL_CLOCK_CLUSTER", "0")
     monkeypatch.setenv("HHL_GROUP", "0" if group is None else "1")
