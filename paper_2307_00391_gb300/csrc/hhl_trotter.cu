@@ -127,7 +127,9 @@ template <> struct TrotArith<double, true> {
   static __device__ __forceinline__ V zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
   static __device__ __forceinline__ W coef(const float* f, const float* fl, const double*, int l) { return {f[l], fl[l]}; }
   static __device__ __forceinline__ W coef1(float f, float fl, double) { return {f, fl}; }
-  static __device__ __forceinline__ V finish(V v) { return {df_renorm(v.x), df_renorm(v.y)}; }
+  // (no renormalisation needed: the lazy phase product and the exact FP64 rebuild on the store
+  // take any head and tail)
+  static __device__ __forceinline__ V finish(V v) { return v; }
 };
 
 // p + i w q = (p.x - w q.y, p.y + w q.x): one output of the factored two-FMA rotation
@@ -148,7 +150,7 @@ __device__ __forceinline__ dfc rot1(dfc p, dfc q, df c, df s) {
 }
 __device__ __forceinline__ float2 phase_mul(float2 a, float2 b) { return cmul(a, b); }
 __device__ __forceinline__ double2 phase_mul(double2 a, double2 b) { return cmul(a, b); }
-__device__ __forceinline__ dfc phase_mul(dfc a, dfc b) { return dfc_mul(a, b); }
+__device__ __forceinline__ dfc phase_mul(dfc a, dfc b) { return cmul(a, b); }  // lazy double-float operators
 
 __device__ __forceinline__ int64_t row_with_bit_t(int64_t i, int k) {
   return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
