@@ -264,6 +264,44 @@ def algorithmic_bytes_per_solve(wl: dict, prec_bytes: int = 8) -> float:
     return 2.0 * half + trotter + 3.0 * half + 2.0 * half + 2.0 * half
 
 
+def _trotter_groups(wl: dict) -> tuple[list, list]:
+    """The planner's passes as (kb, bits) groups: forward (QPE) from bit 0 up, adjoint
+    (uncompute) from the top bit down; consecutive single-step bits share a pass while the
+    all-bits-set layer list stays within 17 layers."""
+    n_c = wl["n_c"]
+    r = _trotter_steps(wl)
+    out = []
+    for order in (list(range(n_c)), list(range(n_c - 1, -1, -1))):
+        groups, group, layers = [], [], 1
+        for k in order:
+            lk = 2 * r[k]
+            if layers + lk > 17 and group:
+                groups.append((min(group), len(group)))
+                group, layers = [], 1
+            group.append(k)
+            layers += lk
+        if group:
+            groups.append((min(group), len(group)))
+        out.append(groups)
+    return out[0], out[1]
+
+
+def postselected_bytes(wl: dict, prec_bytes: int) -> dict:
+    """Minimum HBM bytes per kernel of one postselected solve (hhl_solve_postselected): the
+    expansion passes write every clock row but row 0 once and read each source row once; the
+    clock block reads the anc = 0 half and writes both halves; the sums read both halves; the
+    reduction passes read the rows they fold and write the rows they keep."""
+    n_s, n_c = wl["n_s"], wl["n_c"]
+    N, R = 1 << n_s, 1 << n_c
+    row = N * prec_bytes
+    half = R * row
+    fwd, adj = _trotter_groups(wl)
+    expand = sum(((1 << kb) * ((1 << g) - 1) + (1 << kb)) * row for kb, g in fwd)
+    reduce = sum(((1 << kb) * (1 << g) + (1 << kb)) * row for kb, g in adj)
+    return {"k_trotter_expand": (expand, len(fwd)), "k_trotter_reduce": (reduce, len(adj)),
+            "k_clock": (3.0 * half, 3), "k_measure_sums": (2.0 * half, 1), "k_prep_row": (row, 1)}
+
+
 def _oracle_trotter_sample(wl: dict, budget_s: float) -> dict:
     """The oracle on units of the 32-qubit solve, timed one by one and extrapolated: the
     controlled Strang product U_k on one system row (for each k; the solve applies it to
@@ -488,11 +526,26 @@ def _algorithmic(plan_info: dict, wl: dict, prec_bytes: int) -> dict:
         "k_prep_fill": ("byte", 2.0 * half),
         "k_measure_sums": ("byte", 2.0 * half),
         # grouped Trotter passes change different row counts: the plan's total over its passes
+        # (the complex128 passes in double-float arithmetic are bound by FP32 issue, not HBM)
         "k_trotter_pass": ("byte", tb_launch),
+        "k_trotter_pass_df": ("byte", tb_launch),
         # the halos saved at the boundaries between warps' runs are an overhead of the
         # in-place passes, not algorithmic traffic
         "k_trotter_bounds": ("byte", 0.0),
+        **_tree_algorithmic(wl, prec_bytes),
     }
+
+
+def _tree_algorithmic(wl: dict, prec_bytes: int) -> dict:
+    if wl.get("expm") != "trotter":
+        return {}
+    pb = postselected_bytes(wl, prec_bytes)
+    out = {}
+    for base in ("k_trotter_expand", "k_trotter_reduce"):
+        total, launches = pb[base]
+        for suffix in ("", "_df"):
+            out[base + suffix] = ("byte", total / launches)
+    return out
 
 
 def _breakdown(prof: dict, steps: int) -> dict:
@@ -535,12 +588,13 @@ def _roofline(prof: dict, alg: dict, peaks: dict, workload: str, precision: str,
 
 
 def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmup: int, world: int,
-                local_rank: int, e2e_steps: int = 10) -> dict:
-    """One workload of whole solves (prepare_rhs, apply_circuit, measure, dissipation) on
-    device-resident inputs, L2 flushed between steps: a plain timed loop (CUDA events around
-    each step, no per-launch events), then a second timed loop with per-launch events (the
-    per-kernel breakdown and the dominant kernel's roofline), then the same solve end to end
-    through the public API with host b and host results."""
+                local_rank: int, e2e_steps: int = 10, postselected: bool = False) -> dict:
+    """One workload of whole solves (prepare_rhs, apply_circuit, measure, dissipation; or with
+    `postselected` the one call hhl_solve_postselected) on device-resident inputs, L2 flushed
+    between steps: a plain timed loop (CUDA events around each step, no per-launch events), then
+    a second timed loop with per-launch events (the per-kernel breakdown and the dominant
+    kernel's roofline), then the same solve end to end through the public API with host b and
+    host results."""
     import numpy as np
     import torch
     from synth_inputs import rhs, walls
@@ -563,6 +617,9 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
     torch.cuda.synchronize()
 
     def step():
+        if postselected:
+            plan.solve_postselected(b_dev, st, meas, eps, stream=stream)
+            return
         plan.prepare_rhs(b_dev, st, stream=stream)
         plan.apply_circuit(st, stream=stream)
         plan.measure_async(st, meas, stream=stream)
@@ -604,15 +661,28 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
     prof_total_s, _, prof, _ = timed_loop(True)
 
     b_pin = torch.tensor(b, dtype=torch.float64).pin_memory()
+    bz_pin = torch.tensor(b.astype(np.complex128)).pin_memory()
+    meas_pin = torch.empty(4 + 2 * N, dtype=torch.float64).pin_memory()
+    eps_pin = torch.empty(1, dtype=torch.float64).pin_memory()
     e2e_times = []
     for _ in range(max(3, e2e_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.prepare_rhs_host(b_pin, st, stream=stream)
-        plan.apply_circuit(st, stream=stream)
-        m = plan.measure(st, stream=stream)
-        e = plan.dissipation(st, stream=stream)
+        if postselected:   # host b in, host results out, through the same public call
+            with torch.cuda.stream(stream):
+                b_dev.copy_(bz_pin, non_blocking=True)
+                plan.solve_postselected(b_dev, st, meas, eps, stream=stream)
+                meas_pin.copy_(meas, non_blocking=True)
+                eps_pin.copy_(eps, non_blocking=True)
+            stream.synchronize()
+            m = {"p_success": float(meas_pin[0])}
+            e = float(eps_pin[0])
+        else:
+            plan.prepare_rhs_host(b_pin, st, stream=stream)
+            plan.apply_circuit(st, stream=stream)
+            m = plan.measure(st, stream=stream)
+            e = plan.dissipation(st, stream=stream)
         e2e_times.append(time.perf_counter() - t0)
     e2e_times = e2e_times[1:]
     e2e_total = max_over_ranks(sum(e2e_times), world)
@@ -632,7 +702,9 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
         value = replica_rate(steps, world, total_s)
         e2e_value = replica_rate(len(e2e_times), world, e2e_total)
     out = {
-        "workload": workload, "desc": wl["desc"], "precision": precision, "value": value, "unit": wl["unit"],
+        "workload": workload, "desc": wl["desc"] + ("; postselected solve (hhl_solve_postselected)" if postselected else ""),
+        "precision": precision, "value": value, "unit": wl["unit"],
+        "solves_per_s": replica_rate(steps, world, total_s),
         "ms_per_step": 1e3 * total_s / steps, "steps": steps, "warmup": warmup,
         "roofline": _roofline(prof, alg, _peaks(), workload, precision,
                               "per-launch CUDA events on the launching stream, second timed loop of the same steps"),
@@ -644,8 +716,8 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
                  "gemm_flops_per_solve": info["gemm_flops"], "trotter_passes": info["trotter_passes"],
                  "gemm_impl": ["auto", "simt", "tcgen05"][info["gemm_impl"]] if wl["expm"] == "dense" else None},
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": wl["unit"], "h2d_bytes_per_step": N * 8,
-                "d2h_bytes_per_step": (4 + 2 * N) * 8 + 8 + 8},
+        "e2e": {"value": e2e_value, "unit": wl["unit"], "h2d_bytes_per_step": N * (16 if postselected else 8),
+                "d2h_bytes_per_step": (4 + 2 * N) * 8 + 8 + (0 if postselected else 8)},
         "gpu_launches": launches,
         "result": {"p_success": m["p_success"], "eps": e},
     }
@@ -675,6 +747,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         # the rest of the metric, each timed with CUDA events and with its own roofline: the same
         # 32-qubit solve at the paper's FP64 precision, the dense tensor-core solve of the 23-qubit
         # Couette system, and the batched solves/s at 1e-6 fidelity
+        sub["poiseuille_2p18_postselected"] = solve_block(pkg, "poiseuille_2p18", "c64", "auto", args.steps,
+                                                          args.warmup, world, local_rank, postselected=True)
         sub["poiseuille_2p18_c128"] = solve_block(pkg, "poiseuille_2p18", "c128", "auto", min(args.steps, 5),
                                                   min(args.warmup, 3), world, local_rank, e2e_steps=3)
         sub["couette_1024"] = solve_block(pkg, "couette_1024", "c64", "auto", args.steps, args.warmup, world,

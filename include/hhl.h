@@ -257,6 +257,30 @@ typedef enum hhl_stage {
 } hhl_stage;
 hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void* stream);
 
+/* a1..a7 for the read-out only (Sec. II.A: the solution is read from the postselected
+ * register; App. D: the clock = 0 amplitude after the final Hadamards, U_avg): one whole solve
+ * that computes the postselected vector v, its statistics and the dissipation without the
+ * rest of the final state. The same circuit, rearranged for its prepared input, in which
+ * every clock row of the anc = 0 half holds b / (|b| 2^(n_c/2)):
+ *   QPE by doubling - clock rows that agree on bits [0, k) have had the same gates applied,
+ *     so rows [2^k, 2^(k+1)) are U_k applied to rows [0, 2^k) (groups of bits at once, with the
+ *     plan's per-pattern Strang layer lists; every row still sees its own gate sequence in
+ *     circuit order, computed once);
+ *   the clock block (inverse QFT, inversion rotation, QFT) as in hhl_apply_circuit;
+ *   uncompute, final Hadamards and postselection by halving - the clock = 0 amplitude after
+ *     the Hadamards is 2^(-n_c/2) sum_c W_c S1[c] (W_c the product of the U_k^dagger of the set
+ *     bits of c), folded from the top clock bit down: row c += U_k^dagger row c + 2^k.
+ * Outputs: out_dev (DEVICE, 4 + 2N doubles) in the layout of hhl_measure_async (p_success,
+ * p_anc1 = the weight of the anc = 1 half before the uncompute, norm, |b|, xhat); eps_dev
+ * (DEVICE, 1 double, may be NULL) as hhl_dissipation_async. b_dev: DEVICE complex128, length N.
+ * state_dev is the plan's state buffer used as workspace: afterwards only the clock = 0 row of
+ * the anc = 1 half is defined (it holds v, so hhl_dissipation, hhl_sample and
+ * hhl_qpp_dissipation may read it; hhl_measure may not). Asynchronous.
+ * Errors: HHL_ERR_UNSUPPORTED unless the plan is Strang-Trotter with full_uncompute = 0 and
+ * every clock bit's layer list fits one pass (2 r_k + 1 <= 17). */
+hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* state_dev, double* out_dev,
+                                  double* eps_dev, void* stream);
+
 /* a6 - postselection statistics (Sec. II.A: the end solution read by measurement).
  * Asynchronous form: writes to out_dev (DEVICE, 4 + 2N doubles): [p_success, p_anc1,
  * norm, b_norm, xhat_0.re, xhat_0.im, ...], xhat = v / |v|. */

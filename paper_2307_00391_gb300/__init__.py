@@ -206,6 +206,16 @@ class HHLPlan:
         out-of-range operand (synchronises the stream)."""
         check(self._lib.hhl_plan_status(self._h, ctypes.c_void_p(_stream_handle(stream))), "hhl_plan_status")
 
+    def solve_postselected(self, b_dev, state, out_dev, eps_dev=None, stream=None) -> None:
+        """One whole solve for the read-out only (hhl_solve_postselected): b_dev (torch
+        complex128, N) on the device; out_dev (torch float64, 4 + 2N) receives p_success,
+        p_anc1, norm, |b| and xhat; eps_dev (torch float64, 1) the dissipation rate. Afterwards
+        only the clock = 0 row of the anc = 1 half of ``state`` is defined (it holds v)."""
+        check(self._lib.hhl_solve_postselected(self._h, ctypes.c_void_p(b_dev.data_ptr()),
+                                               ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(out_dev.data_ptr()),
+                                               None if eps_dev is None else ctypes.c_void_p(eps_dev.data_ptr()),
+                                               ctypes.c_void_p(_stream_handle(stream))), "hhl_solve_postselected")
+
     def measure_async(self, state, out_dev, stream=None) -> None:
         check(self._lib.hhl_measure_async(self._h, ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(out_dev.data_ptr()),
                                           ctypes.c_void_p(_stream_handle(stream))), "hhl_measure_async")

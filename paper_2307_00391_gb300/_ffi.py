@@ -70,6 +70,7 @@ SIGNATURES = [
     ("hhl_apply_circuit", c_int32, [c_void_p, c_void_p, c_void_p]),
     ("hhl_apply_stage", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     ("hhl_measure_async", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("hhl_solve_postselected", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_measure", c_int32, [c_void_p, c_void_p, POINTER(Measurement), c_void_p, c_void_p]),
     ("hhl_dissipation_async", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_dissipation", c_int32, [c_void_p, c_void_p, _DP, c_void_p, c_void_p]),

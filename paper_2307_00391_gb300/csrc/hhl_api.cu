@@ -879,6 +879,28 @@ hhl_status hhl_apply_circuit(hhl_plan_t plan, void* state_dev, void* stream) {
   return HHL_OK;
 }
 
+hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* state_dev, double* out_dev,
+                                  double* eps_dev, void* stream) {
+  if (plan == nullptr || b_dev == nullptr || state_dev == nullptr || out_dev == nullptr)
+    return fail(HHL_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = plan->p;
+  std::string why;
+  if (!hhl::trotter_tree_supported(p, &why)) return fail(HHL_ERR_UNSUPPORTED, why);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* s0 = (char*)state_dev;
+  char* s1 = s0 + (size_t)(p.R * p.N) * p.amp_bytes();
+  HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal, 0, sizeof(double), st));
+  hhl_status s = hhl::launch_bnorm(b_dev, p.N, p.d_scal, st);
+  if (s == HHL_OK) s = hhl::launch_prep_row(p, b_dev, s0, st);
+  if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s0, false, st);     // QPE by doubling
+  if (s == HHL_OK) s = hhl::launch_clock_block(p, state_dev, st);      // writes the whole anc = 1 half
+  if (s == HHL_OK) s = hhl::launch_measure_sums(p, state_dev, st);     // |S0|^2, |S1|^2 (= P(anc = 1))
+  if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s1, true, st);      // uncompute + H + clock = 0
+  if (s == HHL_OK) s = hhl::launch_measure_row(p, state_dev, out_dev, st);
+  if (s == HHL_OK && eps_dev != nullptr) s = hhl::launch_dissipation(p, state_dev, eps_dev, nullptr, st);
+  return s;
+}
+
 hhl_status hhl_measure_async(hhl_plan_t plan, const void* state_dev, double* out_dev, void* stream) {
   if (plan == nullptr || state_dev == nullptr || out_dev == nullptr) return fail(HHL_ERR_INVALID_ARG, "NULL argument");
   return hhl::launch_measure(plan->p, state_dev, out_dev, (cudaStream_t)stream);

@@ -257,6 +257,13 @@ hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, c
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st);
+// The read-outs of the postselected solve: launch_measure_sums before the reduction tree
+// (|S0|^2 and |S1|^2 into the plan scalars), launch_measure_row after it (|v|^2 of the
+// clock = 0 row of the anc = 1 half, then the measurement block as hhl_measure_async writes it).
+hhl_status launch_measure_sums(const Plan& p, const void* state, cudaStream_t st);
+hhl_status launch_measure_row(const Plan& p, const void* state, double* out, cudaStream_t st);
+// a1 for the postselected solve: b / (|b| 2^(n_c/2)) into the clock = 0 row of the anc = 0 half only.
+hhl_status launch_prep_row(const Plan& p, const double* b, void* state, cudaStream_t st);
 hhl_status launch_dissipation(const Plan& p, const void* state, double* eps, double* u_dev, cudaStream_t st);
 hhl_status launch_sample(const Plan& p, const void* state, const double* uniforms, int64_t shots, uint64_t* counts,
                          double* cdf, cudaStream_t st);
@@ -274,6 +281,11 @@ hhl_status launch_expm_eigen(int N, int J, const double* d_vr, const double* d_v
 hhl_status launch_store_operands(const Plan& p, const double2* d_u, int k, cudaStream_t st);
 // All controlled products of QPE (adjoint: of the uncompute) on one half, in grouped passes.
 hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t st);
+// The tree passes of the postselected solve: QPE by doubling from the clock = 0 row of the
+// anc = 0 half (reduce = false), or the uncompute, final Hadamards and postselection folded
+// into the clock = 0 row of the anc = 1 half (reduce = true).
+bool trotter_tree_supported(const Plan& p, std::string* why);
+hhl_status launch_trotter_tree(const Plan& p, void* half, bool reduce, cudaStream_t st);
 // U = exp(i Ahat t) (N x N complex128) for a Toeplitz tridiagonal A from the analytic sine
 // basis: d_c / d_s = cos / sin(lambdahat_j t), d_ctab[q] = cos(q pi/(N+1)), q < 2N+2.
 hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, const double* d_ctab, double2* d_g,

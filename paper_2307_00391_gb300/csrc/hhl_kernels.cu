@@ -256,6 +256,17 @@ __global__ void k_measure_sums(const typename Cx<R>::T* __restrict__ S, int64_t 
   block_sum_atomic<3>(a, acc);
 }
 
+// |v|^2 of one row of N amplitudes (the postselected row), FP64.
+template <class R>
+__global__ void k_row_norm(const typename Cx<R>::T* __restrict__ v, int64_t N, double* acc) {
+  double s[1] = {0.0};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const double re = (double)v[j].x, im = (double)v[j].y;
+    s[0] += re * re + im * im;
+  }
+  block_sum_atomic<1>(s, acc);
+}
+
 // out = [p_success, p_anc1, norm, |b|, xhat (2N doubles)]
 template <class R>
 __global__ void k_measure_finish(const typename Cx<R>::T* __restrict__ S, int64_t half, int64_t N,
@@ -595,6 +606,53 @@ hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, c
     k_rows_scatter<double><<<sg, kThreads, 0, st>>>((double2*)half, (const double2*)p.d_scratch, p.n_s, k, m_sub);
   }
   HHL_LAUNCH_CHECK("k_rows_scatter");
+  return HHL_OK;
+}
+
+hhl_status launch_measure_sums(const Plan& p, const void* state, cudaStream_t st) {
+  const int64_t half = p.R * p.N;
+  HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal + 1, 0, 3 * sizeof(double), st));
+  const int g = grid_for(2 * half, kThreads, 152 * 8);
+  const char* env = getenv("HHL_FP64_PIPE");
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64)
+    k_measure_sums<float><<<g, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal + 1);
+  else if (env != nullptr && atoi(env) != 0)
+    k_measure_sums<double><<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
+  else
+    k_measure_sums_df<<<g, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal + 1);
+  HHL_LAUNCH_CHECK("k_measure_sums");
+  return HHL_OK;
+}
+
+hhl_status launch_measure_row(const Plan& p, const void* state, double* out, cudaStream_t st) {
+  const int64_t half = p.R * p.N;
+  HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal + 3, 0, sizeof(double), st));
+  const int gf = grid_for(p.N, kThreads, 152 * 4);
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64)
+    k_row_norm<float><<<gf, kThreads, 0, st>>>((const float2*)state + half, p.N, p.d_scal + 3);
+  else
+    k_row_norm<double><<<gf, kThreads, 0, st>>>((const double2*)state + half, p.N, p.d_scal + 3);
+  HHL_LAUNCH_CHECK("k_row_norm");
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64)
+    k_measure_finish<float><<<gf, kThreads, 0, st>>>((const float2*)state, half, p.N, p.d_scal, out);
+  else
+    k_measure_finish<double><<<gf, kThreads, 0, st>>>((const double2*)state, half, p.N, p.d_scal, out);
+  HHL_LAUNCH_CHECK("k_measure_finish");
+  return HHL_OK;
+}
+
+hhl_status launch_prep_row(const Plan& p, const double* b, void* state, cudaStream_t st) {
+  const int gs = grid_for(p.N, kThreads, 152);
+  HHL_PROF_BEGIN(st);
+  if (p.prec == HHL_PREC_C64)
+    k_prep_scale<float><<<gs, kThreads, 0, st>>>((const double2*)b, p.d_scal, (float2*)p.d_bs, p.N, p.n_c);
+  else
+    k_prep_scale<double><<<gs, kThreads, 0, st>>>((const double2*)b, p.d_scal, (double2*)p.d_bs, p.N, p.n_c);
+  HHL_LAUNCH_CHECK("k_prep_scale");
+  HHL_CUDA_TRY(cudaMemcpyAsync(state, p.d_bs, (size_t)p.N * p.amp_bytes(), cudaMemcpyDeviceToDevice, st));
   return HHL_OK;
 }
 

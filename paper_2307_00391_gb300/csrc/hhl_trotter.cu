@@ -400,6 +400,105 @@ __device__ __forceinline__ Window window_next(Window d, int v, int v1, int segs,
 // window is formed again after the current one is done, so that it holds no registers
 // during the layers.) 16 warps per SM with up to 128 registers each: the paired layers need
 // them (with 24 warps and 80 registers the pass spilled and ran 10% slower).
+// The layers of one row pattern and its end-of-pass phase on a window held in registers:
+// the factored forms on windows away from the row ends (`away`, warp-uniform), the plain
+// rotations with per-pair validity near them. lane0: the row index of this lane's first
+// amplitude; coef: the pattern's coefficients (per warp, in shared memory); L: its list.
+template <class R, bool DF, int LA>
+__device__ __forceinline__ void apply_pattern(typename TrotArith<R, DF>::V (&x)[LA],
+                                              const LayerCoefs<typename TrotArith<R, DF>::W>* coef,
+                                              const LayerList* L, int n_layers, int first_o, bool away, int64_t lane0,
+                                              int64_t N, int lane) {
+  using A = TrotArith<R, DF>;
+  using V = typename A::V;
+  using W = typename A::W;
+  int n_f1 = 0;  // double-float kernel: layers in the second form
+  if constexpr (DF) {
+    if (away) {
+      for (int l = 0; l < n_layers; ++l) {
+        const bool e_layer = ((l + first_o) & 1) == 0;
+        const int f1 = coef->form[l];
+        n_f1 += f1;
+        if (f1) layer_df<true>(x, e_layer, df_neg(coef->w[l]));
+        else layer_df<false>(x, e_layer, coef->w[l]);
+      }
+    }
+  } else if (away) {
+    // layers alternate E, O: an O layer first on its own, then (E, O) pairs in one loop
+    // body (the pair's second layer writes its outputs back into the registers the loop
+    // carries, so no register copies are needed between layers), then a last E layer
+    int l = 0;
+    if (first_o && n_layers > 0) {
+      if (coef->form[0] != 0) layer_factored<true, LA>(x, false, coef->w[0]);
+      else layer_factored<false, LA>(x, false, coef->w[0]);
+      l = 1;
+    }
+    for (; l + 1 < n_layers; l += 2) {
+      const W we = coef->w[l], wo = coef->w[l + 1];
+      if (coef->form[l] != 0) {
+        layer_factored<true, LA>(x, true, we);
+        if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
+        else layer_factored<false, LA>(x, false, wo);
+      } else {
+        layer_factored<false, LA>(x, true, we);
+        if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
+        else layer_factored<false, LA>(x, false, wo);
+      }
+    }
+    if (l < n_layers) {
+      if (coef->form[l] != 0) layer_factored<true, LA>(x, true, coef->w[l]);
+      else layer_factored<false, LA>(x, true, coef->w[l]);
+    }
+  }
+  // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
+  const bool in_ok = lane0 >= 0 && lane0 + LA - 2 <= N - 1;
+  const bool right_ok = lane < 31 && lane0 + LA - 1 >= 1 && lane0 + LA <= N - 1;
+  const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
+  for (int l = 0; l < (away ? 0 : n_layers); ++l) {
+    const W c = coef->c[l], sn = coef->s[l];
+    if (((l + first_o) & 1) == 0) {
+      // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
+#pragma unroll
+      for (int q = 0; q < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+    } else {
+      const V right = shfl_down1(x[0]);           // next lane's first amplitude
+      const V left = shfl_up1(x[LA - 1]);  // previous lane's last amplitude
+      if (in_ok && !DF) {  // (the double-float kernel keeps one copy of this rare path)
+#pragma unroll
+        for (int q = 1; q + 1 < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
+      } else {
+#pragma unroll
+        for (int q = 1; q + 1 < LA; q += 2) {
+          const int64_t j = lane0 + q;
+          if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
+        }
+      }
+      if (right_ok) x[LA - 1] = rot1(x[LA - 1], right, c, sn);  // a <- c a + i s b
+      if (left_ok) x[0] = rot1(x[0], left, c, sn);                            // b <- i s a + c b
+    }
+  }
+  {
+    V ph;
+    if (away) {
+      ph.x = A::coef1(L->pc2f, L->pc2l, L->pc2);
+      ph.y = A::coef1(L->ps2f, L->ps2l, L->ps2);
+      if constexpr (DF) {
+        // (-i)^n_f1: the second form's factors are sin th, not i sin th
+        for (int j = 0; j < (n_f1 & 3); ++j) {
+          const auto t = ph.x;
+          ph.x = ph.y;
+          ph.y = df_neg(t);
+        }
+      }
+    } else {
+      ph.x = A::coef1(L->pcf, L->pcl, L->pc);
+      ph.y = A::coef1(L->psf, L->psl, L->ps);
+    }
+#pragma unroll
+    for (int q = 0; q < LA; ++q) x[q] = phase_mul(A::finish(x[q]), ph);
+  }
+}
+
 // Threads per block: 256. Blocks per SM: 2 for complex64 (128 registers), 1 for the FP64 form
 // of complex128, 3 for the double-float form (8 amplitudes per lane: two 4 KiB staging buffers
 // per warp, 80 registers, 24 warps per SM to hide its latencies).
@@ -513,91 +612,7 @@ __global__ void __launch_bounds__(trot_threads<R, DF>(), trot_min_blocks<R, DF>(
       // warp-uniform: every O pair of the interior lanes lies inside the row (no row end in
       // the window but possibly the halos', whose values do not reach the interior)
       const bool away = cur.full && g0 >= 2 && g0 + kInterior + 1 <= N;
-      int n_f1 = 0;  // double-float kernel: layers in the second form
-      if constexpr (DF) {
-        if (away) {
-          for (int l = 0; l < n_layers; ++l) {
-            const bool e_layer = ((l + first_o) & 1) == 0;
-            const int f1 = coef->form[l];
-            n_f1 += f1;
-            if (f1) layer_df<true>(x, e_layer, df_neg(coef->w[l]));
-            else layer_df<false>(x, e_layer, coef->w[l]);
-          }
-        }
-      } else if (away) {
-        // layers alternate E, O: an O layer first on its own, then (E, O) pairs in one loop
-        // body (the pair's second layer writes its outputs back into the registers the loop
-        // carries, so no register copies are needed between layers), then a last E layer
-        int l = 0;
-        if (first_o && n_layers > 0) {
-          if (coef->form[0] != 0) layer_factored<true, LA>(x, false, coef->w[0]);
-          else layer_factored<false, LA>(x, false, coef->w[0]);
-          l = 1;
-        }
-        for (; l + 1 < n_layers; l += 2) {
-          const W we = coef->w[l], wo = coef->w[l + 1];
-          if (coef->form[l] != 0) {
-            layer_factored<true, LA>(x, true, we);
-            if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
-            else layer_factored<false, LA>(x, false, wo);
-          } else {
-            layer_factored<false, LA>(x, true, we);
-            if (coef->form[l + 1] != 0) layer_factored<true, LA>(x, false, wo);
-            else layer_factored<false, LA>(x, false, wo);
-          }
-        }
-        if (l < n_layers) {
-          if (coef->form[l] != 0) layer_factored<true, LA>(x, true, coef->w[l]);
-          else layer_factored<false, LA>(x, true, coef->w[l]);
-        }
-      }
-      // per-lane validity of the O pairs (j, j+1), j odd, 1 <= j and j + 1 <= N - 1
-      const bool in_ok = lane0 >= 0 && lane0 + LA - 2 <= N - 1;
-      const bool right_ok = lane < 31 && lane0 + LA - 1 >= 1 && lane0 + LA <= N - 1;
-      const bool left_ok = lane > 0 && lane0 - 1 >= 1 && lane0 <= N - 1;
-      for (int l = 0; l < (away ? 0 : n_layers); ++l) {
-        const W c = coef->c[l], sn = coef->s[l];
-        if (((l + first_o) & 1) == 0) {
-          // E layer: pairs (2p, 2p+1) inside each lane; pairs beyond the row are zero.
-#pragma unroll
-          for (int q = 0; q < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
-        } else {
-          const V right = shfl_down1(x[0]);           // next lane's first amplitude
-          const V left = shfl_up1(x[LA - 1]);  // previous lane's last amplitude
-          if (in_ok && !DF) {  // (the double-float kernel keeps one copy of this rare path)
-#pragma unroll
-            for (int q = 1; q + 1 < LA; q += 2) rot_apply(x[q], x[q + 1], c, sn);
-          } else {
-#pragma unroll
-            for (int q = 1; q + 1 < LA; q += 2) {
-              const int64_t j = lane0 + q;
-              if (j >= 1 && j + 1 <= N - 1) rot_apply(x[q], x[q + 1], c, sn);
-            }
-          }
-          if (right_ok) x[LA - 1] = rot1(x[LA - 1], right, c, sn);  // a <- c a + i s b
-          if (left_ok) x[0] = rot1(x[0], left, c, sn);                            // b <- i s a + c b
-        }
-      }
-      {
-        V ph;
-        if (away) {
-          ph.x = A::coef1(L->pc2f, L->pc2l, L->pc2);
-          ph.y = A::coef1(L->ps2f, L->ps2l, L->ps2);
-          if constexpr (DF) {
-            // (-i)^n_f1: the second form's factors are sin th, not i sin th
-            for (int j = 0; j < (n_f1 & 3); ++j) {
-              const auto t = ph.x;
-              ph.x = ph.y;
-              ph.y = df_neg(t);
-            }
-          }
-        } else {
-          ph.x = A::coef1(L->pcf, L->pcl, L->pc);
-          ph.y = A::coef1(L->psf, L->psl, L->ps);
-        }
-#pragma unroll
-        for (int q = 0; q < LA; ++q) x[q] = phase_mul(A::finish(x[q]), ph);
-      }
+      apply_pattern<R, DF, LA>(x, coef, L, n_layers, first_o, away, lane0, N, lane);
       if (cur.full) {
         if (interior) {
           T t[LA];
@@ -632,6 +647,208 @@ size_t trotter_smem() {
   constexpr int per = 16 / sizeof(typename A::T);
   constexpr int CPL = trot_lane_amps<R, DF>() / per;
   return (size_t)(trot_threads<R, DF>() / 32) * (2 * 32 * CPL * 16 + sizeof(LayerCoefs<typename A::W>));
+}
+
+// ------------------------------------------------------------------------ the tree passes
+// The postselected solve (hhl_solve_postselected) replaces the controlled products of QPE and
+// of the uncompute by two trees, exact rearrangements of the same circuit for its prepared
+// input, in which every clock row of the anc = 0 half holds the same vector.
+//
+// QPE by doubling (expansion): clock rows that agree on bits [0, kb) have had the same gates
+// applied so far, and a row c + p 2^kb (p a pattern of the next group of clock bits) is row c
+// with the pattern's products applied next. So, group by group, rows [2^kb, 2^(kb+G)) are
+// computed from rows [0, 2^kb) with the groups' per-pattern layer lists: every row still sees
+// its own gate sequence in circuit order (the same arithmetic as the in-place passes), each
+// computed once; only the clock = 0 row has to be prepared.
+//
+// Uncompute, final Hadamards and postselection by halving (reduction): after the final
+// Hadamard layer the clock = 0 amplitude is 2^(-n_c/2) sum_c W_c S1[c], W_c the product of the
+// U_k^dagger of the set bits of c (U_{n_c-1}^dagger first). By linearity the sum folds group by
+// group from the top clock bits down: row c (c < 2^kb) accumulates its own value and, for
+// every nonzero pattern p of the group, the pattern's adjoint list applied to row c + p 2^kb.
+// After the last group row 0 holds the postselected vector (scaled by 2^(-n_c/2) on the store).
+//
+// A warp takes a window (interior and both halos) of a source row into staging with
+// asynchronous copies, double-buffered over its sequence of windows; the halos come straight
+// from the source rows, which a tree pass never writes.
+template <class R, bool DF, bool RED>
+__global__ void __launch_bounds__(kTrotThreads, RED ? (sizeof(R) == 4 || DF ? 2 : 1) : trot_min_blocks<R, DF>())
+    k_trotter_tree(typename Cx<R>::T* __restrict__ half, int n_s, int segs, int64_t items, int nwarps, int kb,
+                   int gbits, const LayerList* __restrict__ lists, float scale_f, float scale_l, double scale_d) {
+  using A = TrotArith<R, DF>;
+  using T = typename A::T;
+  using V = typename A::V;
+  using W = typename A::W;
+  constexpr int LA = trot_lane_amps<R, DF>();
+  constexpr int HL = Geo<LA>::HL;
+  constexpr int kInterior = Geo<LA>::INTER;
+  constexpr int per = 16 / sizeof(T);
+  constexpr int CPL = LA / per;
+  constexpr int HC = kHalo / per;
+  constexpr int WCH = 32 * CPL;             // chunks of a window
+  constexpr int CHUNKS = kInterior / per;   // of its interior
+  constexpr int WPB = kTrotThreads / 32;
+  extern __shared__ __align__(16) unsigned char trot_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint4* stage_w = reinterpret_cast<uint4*>(trot_smem) + (size_t)wid * 2 * WCH;
+  LayerCoefs<W>* coef =
+      reinterpret_cast<LayerCoefs<W>*>(reinterpret_cast<uint4*>(trot_smem) + (size_t)WPB * 2 * WCH) + wid;
+  const int64_t N = 1LL << n_s;
+  const int gw = (int)blockIdx.x * WPB + wid;
+  if (gw >= nwarps) return;  // warp-uniform
+  const int P = RED ? 1 << gbits : 1;  // windows per item
+  const int64_t j0 = (int64_t)gw * items / nwarps * P, j1 = (int64_t)(gw + 1) * items / nwarps * P;
+  const int64_t kmask = (1LL << kb) - 1;
+  // window j of the sequence: source row, destination row, pattern (0: the accumulator's own
+  // row in a reduction), segment
+  auto decode = [&](int64_t j, int64_t* src, int64_t* dst, int* pat, int* seg) {
+    const int64_t item = RED ? j >> gbits : j;
+    const int64_t i = item / segs;
+    *seg = (int)(item - i * segs);
+    if (RED) {
+      *pat = (int)(j & (P - 1));
+      *dst = i;
+      *src = i + ((int64_t)*pat << kb);
+    } else {
+      *pat = (int)(1 + (i >> kb));
+      *src = i & kmask;
+      *dst = *src + ((int64_t)*pat << kb);
+    }
+  };
+  auto issue = [&](uint4* stage, int64_t src, int seg) {
+    const T* row = half + src * N;
+    const int64_t w0 = (int64_t)seg * kInterior - kHalo;  // first amplitude of the window
+#pragma unroll
+    for (int q = 0; q < WCH / 32; ++q) {
+      const int c = q * 32 + lane;
+      const int64_t a0 = w0 + (int64_t)c * per;
+      if (a0 >= 0 && a0 + per <= N) cp_async16(&stage[swz<CPL>(c)], reinterpret_cast<const uint4*>(row + a0));
+      else stage[swz<CPL>(c)] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  {
+    int64_t src, dst;
+    int pat, seg;
+    decode(j0, &src, &dst, &pat, &seg);
+    if (j0 < j1) issue(stage_w, src, seg);
+  }
+  cp_async_commit();
+  int buf = 0, cached = -1, n_layers = 0, first_o = 0;
+  const bool interior = lane >= HL && lane < 32 - HL;
+  V acc[LA];
+  for (int64_t j = j0; j < j1; ++j) {
+    if (j + 1 < j1) {
+      int64_t src, dst;
+      int pat, seg;
+      decode(j + 1, &src, &dst, &pat, &seg);
+      issue(stage_w + (buf ^ 1) * WCH, src, seg);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    int64_t src, dst;
+    int pat, seg;
+    decode(j, &src, &dst, &pat, &seg);
+    uint4* stage = stage_w + buf * WCH;
+    const int64_t g0 = (int64_t)seg * kInterior;
+    const int64_t lane0 = g0 - kHalo + (int64_t)lane * LA;
+    const bool full = g0 + kInterior <= N;
+    V x[LA];
+    {
+      T t[LA];
+      uint4* d = reinterpret_cast<uint4*>(t);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) d[q] = stage[(lane * CPL + q) ^ (lane & 7)];
+#pragma unroll
+      for (int q = 0; q < LA; ++q) x[q] = A::load(t[q]);
+    }
+    if (RED && pat == 0) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) acc[q] = x[q];
+    } else {
+      const LayerList* L = lists + pat;
+      if (pat != cached) {
+        cached = pat;
+        n_layers = L->n;
+        first_o = L->first_o;
+        if (lane < n_layers) {
+          coef->c[lane] = A::coef(L->cf, L->cl, L->c, lane);
+          coef->s[lane] = A::coef(L->sf, L->sl, L->s, lane);
+          coef->w[lane] = A::coef(L->wf, L->wl, L->w, lane);
+          coef->form[lane] = L->form[lane];
+        }
+      }
+      __syncwarp();
+      const bool away = full && g0 >= 2 && g0 + kInterior + 1 <= N;
+      apply_pattern<R, DF, LA>(x, coef, L, n_layers, first_o, away, lane0, N, lane);
+      if (RED) {
+#pragma unroll
+        for (int q = 0; q < LA; ++q) acc[q] = cadd(acc[q], x[q]);
+      }
+    }
+    if (!RED || pat == P - 1) {
+      V* out = RED ? acc : x;
+      if (RED && kb == 0) {  // the postselected vector: 2^(-n_c/2) of the folded sum
+        const W sc = A::coef1(scale_f, scale_l, scale_d);
+#pragma unroll
+        for (int q = 0; q < LA; ++q) out[q] = cscale(out[q], sc);
+      }
+      T* drow = half + dst * N;
+      __syncwarp();  // every lane has read its window out of the staging buffer
+      if (full) {
+        if (interior) {
+          T t[LA];
+#pragma unroll
+          for (int q = 0; q < LA; ++q) t[q] = A::store(out[q]);
+          const uint4* sx = reinterpret_cast<const uint4*>(t);
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) stage[(lane * CPL + q) ^ (lane & 7)] = sx[q];
+        }
+        __syncwarp();
+        uint4* dptr = reinterpret_cast<uint4*>(drow + g0);
+#pragma unroll
+        for (int q = 0; q < (CHUNKS + 31) / 32; ++q) {
+          const int c = q * 32 + lane;
+          if (c < CHUNKS) dptr[c] = stage[swz<CPL>(c + HC)];
+        }
+      } else if (interior) {
+#pragma unroll
+        for (int q = 0; q < LA; ++q)
+          if (lane0 + q < N) drow[lane0 + q] = A::store(out[q]);
+      }
+    }
+    __syncwarp();  // the buffer is free for the next issue, the coefficients for a new pattern
+    buf ^= 1;
+  }
+}
+
+template <class R, bool DF, bool RED>
+hhl_status tree_impl(const Plan& p, void* half, const TrotPassDesc& d, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  constexpr int LA = trot_lane_amps<R, DF>();
+  const int64_t segs = (p.N + Geo<LA>::INTER - 1) / Geo<LA>::INTER;
+  const size_t smem = trotter_smem<R, DF>();
+  auto kern = k_trotter_tree<R, DF, RED>;
+  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  HHL_CUDA_TRY(cudaGetDevice(&dev));
+  HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HHL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTrotThreads, smem));
+  if (occ < 1) return fail(HHL_ERR_UNSUPPORTED, "Trotter tree pass does not fit an SM");
+  // items: expansion (rows written) x segments; reduction (rows kept) x segments
+  const int64_t rows = RED ? (1LL << d.kb) : (1LL << d.kb) * ((1LL << d.gbits) - 1);
+  const int64_t items = rows * segs;
+  const int64_t max_warps = (int64_t)occ * sms * (kTrotThreads / 32);
+  const int nwarps = (int)std::min<int64_t>(items, max_warps);
+  const unsigned grid = (unsigned)((nwarps + kTrotThreads / 32 - 1) / (kTrotThreads / 32));
+  const double scale = 1.0 / sqrt((double)p.R);
+  float sf, sl;
+  df_split(scale, &sf, &sl);
+  HHL_PROF_BEGIN(st);
+  kern<<<grid, kTrotThreads, smem, st>>>((T*)half, p.n_s, (int)segs, items, nwarps, d.kb, d.gbits,
+                                        (const LayerList*)p.d_trot_lists + d.list_off, sf, sl, scale);
+  HHL_LAUNCH_CHECK(RED ? (DF ? "k_trotter_reduce_df" : "k_trotter_reduce") : (DF ? "k_trotter_expand_df" : "k_trotter_expand"));
+  return HHL_OK;
 }
 
 __global__ void k_interleave(const double* __restrict__ re, const double* __restrict__ im, int64_t n,
@@ -767,6 +984,42 @@ hhl_status launch_trotter(const Plan& p, void* half, bool adjoint, cudaStream_t 
   const char* env = getenv("HHL_FP64_PIPE");
   if (env != nullptr && atoi(env) != 0) return trotter_impl<double, false>(p, half, adjoint, st);
   return trotter_impl<double, true>(p, half, adjoint, st);
+}
+
+bool trotter_tree_supported(const Plan& p, std::string* why) {
+  if (p.expm_mode != HHL_EXPM_TROTTER || p.d_trot_lists == nullptr) {
+    *why = "the postselected solve needs a Strang-Trotter plan";
+    return false;
+  }
+  if (p.full) {
+    *why = "the postselected solve needs the postselect-early uncompute (full_uncompute = 0)";
+    return false;
+  }
+  for (int dir = 0; dir < 2; ++dir) {
+    int next = dir == 0 ? 0 : p.n_c;  // expansion: groups from bit 0 up; reduction: from the top down
+    for (const TrotPassDesc& d : p.trot_pass[dir]) {
+      const bool ok = dir == 0 ? d.kb == next : d.kb + d.gbits == next;
+      if (!ok) {
+        *why = "a clock bit needs more than 17 Strang layers (one bit over several passes)";
+        return false;
+      }
+      next = dir == 0 ? d.kb + d.gbits : d.kb;
+    }
+  }
+  return true;
+}
+
+hhl_status launch_trotter_tree(const Plan& p, void* half, bool reduce, cudaStream_t st) {
+  const char* env = getenv("HHL_FP64_PIPE");
+  const bool fp64 = env != nullptr && atoi(env) != 0;
+  for (const TrotPassDesc& d : p.trot_pass[reduce ? 1 : 0]) {
+    hhl_status s;
+    if (p.prec == HHL_PREC_C64) s = reduce ? tree_impl<float, false, true>(p, half, d, st) : tree_impl<float, false, false>(p, half, d, st);
+    else if (fp64) s = reduce ? tree_impl<double, false, true>(p, half, d, st) : tree_impl<double, false, false>(p, half, d, st);
+    else s = reduce ? tree_impl<double, true, true>(p, half, d, st) : tree_impl<double, true, false>(p, half, d, st);
+    if (s != HHL_OK) return s;
+  }
+  return HHL_OK;
 }
 
 size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table) {
