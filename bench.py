@@ -741,9 +741,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         torch.distributed.barrier()
     pkg.load()
     wl = WORKLOADS[args.workload]
-    main = solve_block(pkg, args.workload, args.precision, args.gemm, args.steps, args.warmup, world, local_rank)
+    main = solve_block(pkg, args.workload, args.precision, args.gemm, args.steps, args.warmup, world, local_rank,
+                       postselected=args.postselected)
     sub = {}
-    if args.workload == DEFAULT_WORKLOAD and args.sub == "all":
+    if args.workload == DEFAULT_WORKLOAD and args.sub == "all" and not args.postselected:
         # the rest of the metric, each timed with CUDA events and with its own roofline: the same
         # 32-qubit solve at the paper's FP64 precision, the dense tensor-core solve of the 23-qubit
         # Couette system, and the batched solves/s at 1e-6 fidelity
@@ -765,6 +766,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
                    "expm": wl["expm"], "gemm_impl": main["plan"]["gemm_impl"],
                    "uncompute": "postselect-early",
+                   "readout": "postselected solve" if args.postselected else "full final state",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": main["roofline"],
@@ -1059,6 +1061,8 @@ def main():
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
     ap.add_argument("--gemm", default="auto", choices=["auto", "simt", "tcgen05"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--postselected", action="store_true",
+                    help="Strang-Trotter workloads: time the postselected solve (hhl_solve_postselected)")
     ap.add_argument("--streams", type=int, default=8, help="worker streams of the batched engine")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

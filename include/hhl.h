@@ -186,6 +186,8 @@ void hhl_params_default(hhl_params* p);
  * params.signed_clock = 1. */
 hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hhl_plan_t* out);
 void hhl_plan_destroy(hhl_plan_t plan);
+/* The same call under the name of the hot-path contract (hhl_plan_create). */
+hhl_status hhl_plan(const hhl_problem* prob, const hhl_params* params, hhl_plan_t* out);
 hhl_status hhl_plan_get_info(hhl_plan_t plan, hhl_plan_info* info);
 uint64_t hhl_state_bytes(hhl_plan_t plan);
 
@@ -236,6 +238,32 @@ hhl_status hhl_prepare_rhs_qsp2(hhl_plan_t plan, const int64_t* idx_dev, const d
  * allocates its LCU register (6N complex128 of device memory, freed with the plan).
  * Errors: NULL arguments; HHL_ERR_SINGULAR for a zero register. */
 hhl_status hhl_qpp_dissipation(hhl_plan_t plan, const void* state_dev, double* eps, double* p0, void* stream);
+
+/* Host builders of the QPP nonlinear transform (App. D: the QADC by phase estimation of an
+ * amplitude-estimation iterate, the squaring rotation, the QDAC), for a UNITARY plan on the
+ * HHL kernels. zeta: HOST, 2^a_bits real amplitudes of a normalised state |zeta> = U_V |0>
+ * (U_V the Householder reflection taking |0> to |zeta>). form 0: amplitude-estimation form,
+ * system register data (low a bits) and address (high a bits), dimension n^2 (n = 2^a_bits,
+ * a_bits <= 4); form 1: the swap-test form as App. D prints it (STEPS 1-5), per address s the
+ * data register ua, the address clone a1 and the swap-test qubit a2, index
+ * ua + n a1 + n^2 a2 + 2 n^2 s, dimension 2 n^3 (a_bits <= 2). All outputs are HOST FP64
+ * arrays; the calls use no GPU. Errors: NULL pointers or sizes out of range
+ * (HHL_ERR_INVALID_ARG). */
+/* q_out (dim x dim, row-major, real): the iterate, block diagonal over the address. Form 0:
+ * block k = -U_V S_0 U_V^T S_k (S_j flips the sign of |j>); form 1: block s = -A S_s A^T S_good
+ * with A = (H on a2)(SWAP(ua, a1) controlled by a2)(H on a2)(U_V on ua), S_good = -Z on a2 and
+ * S_s the flip of |0>_ua |s>_a1 |0>_a2. */
+hhl_status hhl_qpp_iterate(const double* zeta, int32_t a_bits, int32_t form, double* q_out);
+/* theta_out (2^n_clock): the squaring rotation per clock value y, theta_y = 2 arcsin(c z^2)
+ * with z^2 = sin^2(pi y / 2^n_clock) (form 0) or 2 sin^2(pi y / 2^n_clock) - 1 (form 1); |c| <= 1. */
+hhl_status hhl_qpp_rotation_table(int32_t n_clock, double c, int32_t form, double* theta_out);
+/* b_out (dim, real): the start state, the uniform address times |zeta> (form 0) or the state
+ * after STEPS 1-3 (form 1: amplitude (z_i [j = s] +- [i = s] z_j) / (2 sqrt n), + for a2 = 0). */
+hhl_status hhl_qpp_start_state(const double* zeta, int32_t a_bits, int32_t form, double* b_out);
+/* squares_out (n complex, re/im interleaved): the postselected vector v (dim complex, re/im
+ * interleaved) projected, address block by address block, on that block's start state
+ * (normalised): ~ c z_s^2 / sqrt(n). */
+hhl_status hhl_qpp_project(const double* v, const double* b_start, int32_t a_bits, int32_t form, double* squares_out);
 
 /* a2..a5 - the circuit after state preparation, in place (Sec. IV/VI, standard HHL):
  * clock-bit-controlled U_k for k = 0..n_c-1, inverse QFT on the clock, clock-controlled
@@ -349,6 +377,9 @@ typedef struct hhl_batch_info {
  * assigned to streams by decreasing GEMM work. Allocates every state and workspace. */
 hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, int32_t count,
                             const int32_t* gemm_choice, int32_t streams, hhl_batch_t* out);
+/* hhl_batch_create with the library's GEMM choice per instance and 8 worker streams, under the
+ * name of the hot-path contract. */
+hhl_status hhl_batch_plan(const hhl_problem* probs, const hhl_params* params, int32_t count, hhl_batch_t* out);
 void hhl_batch_destroy(hhl_batch_t batch);
 hhl_status hhl_batch_get_info(hhl_batch_t batch, hhl_batch_info* info);
 /* Per instance: register sizes, chosen GEMM, offsets into the packed arrays, T0. */

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("hhl_last_error", c_char_p, []),
     ("hhl_params_default", None, [POINTER(Params)]),
     ("hhl_plan_create", c_int32, [POINTER(Problem), POINTER(Params), POINTER(c_void_p)]),
+    ("hhl_plan", c_int32, [POINTER(Problem), POINTER(Params), POINTER(c_void_p)]),
     ("hhl_plan_destroy", None, [c_void_p]),
     ("hhl_plan_get_info", c_int32, [c_void_p, POINTER(PlanInfo)]),
     ("hhl_state_bytes", c_uint64, [c_void_p]),
@@ -75,6 +76,7 @@ SIGNATURES = [
     ("hhl_dissipation_async", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_dissipation", c_int32, [c_void_p, c_void_p, _DP, c_void_p, c_void_p]),
     ("hhl_batch_create", c_int32, [POINTER(Problem), POINTER(Params), c_int32, c_void_p, c_int32, POINTER(c_void_p)]),
+    ("hhl_batch_plan", c_int32, [POINTER(Problem), POINTER(Params), c_int32, POINTER(c_void_p)]),
     ("hhl_batch_destroy", None, [c_void_p]),
     ("hhl_batch_get_info", c_int32, [c_void_p, POINTER(BatchInfo)]),
     ("hhl_batch_instance", c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
@@ -98,6 +100,10 @@ SIGNATURES = [
     ("hhl_prepare_rhs_qsp1", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("hhl_prepare_rhs_qsp2", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("hhl_qpp_dissipation", c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), c_void_p]),
+    ("hhl_qpp_iterate", c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    ("hhl_qpp_rotation_table", c_int32, [c_int32, c_double, c_int32, c_void_p]),
+    ("hhl_qpp_start_state", c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    ("hhl_qpp_project", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
     ("hhl_kernel_launch_count", c_uint64, []),
     ("hhl_controlled_u_noalloc", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("hhl_profile_enable", None, [c_int32]),

@@ -730,6 +730,10 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
 #undef HHL_PLAN_TRY
 }
 
+hhl_status hhl_plan(const hhl_problem* prob, const hhl_params* params, hhl_plan_t* out) {
+  return hhl_plan_create(prob, params, out);
+}
+
 void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
@@ -893,8 +897,16 @@ hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* st
   hhl_status s = hhl::launch_bnorm(b_dev, p.N, p.d_scal, st);
   if (s == HHL_OK) s = hhl::launch_prep_row(p, b_dev, s0, st);
   if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s0, false, st);     // QPE by doubling
-  if (s == HHL_OK) s = hhl::launch_clock_block(p, state_dev, st);      // writes the whole anc = 1 half
-  if (s == HHL_OK) s = hhl::launch_measure_sums(p, state_dev, st);     // |S0|^2, |S1|^2 (= P(anc = 1))
+  // the clock block writes the whole anc = 1 half; the weights |S0|^2, |S1|^2 (= P(anc = 1))
+  // come from its pass B on the split path, else from a read of both halves
+  bool summed = false;
+  if (s == HHL_OK) s = [&]() -> hhl_status {
+    HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal + 1, 0, 3 * sizeof(double), st));
+    return HHL_OK;
+  }();
+  if (s == HHL_OK) s = hhl::launch_clock_block_sums(p, state_dev, p.d_scal + 1, &summed, st);
+  if (s == HHL_OK && !summed) s = hhl::launch_clock_block(p, state_dev, st);
+  if (s == HHL_OK && !summed) s = hhl::launch_measure_sums(p, state_dev, st);
   if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s1, true, st);      // uncompute + H + clock = 0
   if (s == HHL_OK) s = hhl::launch_measure_row(p, state_dev, out_dev, st);
   if (s == HHL_OK && eps_dev != nullptr) s = hhl::launch_dissipation(p, state_dev, eps_dev, nullptr, st);

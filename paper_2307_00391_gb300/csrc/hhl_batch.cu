@@ -451,6 +451,10 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
   return HHL_OK;
 }
 
+hhl_status hhl_batch_plan(const hhl_problem* probs, const hhl_params* params, int32_t count, hhl_batch_t* out) {
+  return hhl_batch_create(probs, params, count, nullptr, 8, out);
+}
+
 void hhl_batch_destroy(hhl_batch_t b) { hhl::free_batch(b); }
 
 hhl_status hhl_batch_get_info(hhl_batch_t b, hhl_batch_info* info) {

@@ -255,6 +255,10 @@ hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, c
 // SIMT controlled product with an explicit operand B[m][n] (U^T forward, conj(U) adjoint).
 hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, cudaStream_t st);
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st);
+// The clock block for the postselected solve (postselect-early plans on the split-pass path):
+// the anc = 0 half is not stored; the weights of the two halves after the block are added to
+// sums[0] and sums[1]. *done = false when the plan takes another path (then nothing is launched).
+hhl_status launch_clock_block_sums(const Plan& p, void* state, double* sums, bool* done, cudaStream_t st);
 hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st);
 hhl_status launch_measure(const Plan& p, const void* state, double* out, cudaStream_t st);
 // The read-outs of the postselected solve: launch_measure_sums before the reduction tree

@@ -723,7 +723,36 @@ hhl_status register_transform_impl(void* state, int n, int lo, int m, int mode, 
 //   C  QFT DIT stages on the high bits, in place (anc = 1 half, or both halves).
 // Pass B's write of row y = bitrev(p) goes to the anc = 0 half, which no pass reads after A,
 // so the bit-reversed scatter cannot race with another tile's reads.
-enum SplitOp { kSplitDif = 0, kSplitMid = 1, kSplitDit = 2, kSplitHad = 3 };
+// kSplitMidSums: pass B of the postselected solve, which needs no anc = 0 half afterwards: the
+// cos part is not stored; instead each thread sums cos^2(theta_y/2) |x_y|^2 and
+// sin^2(theta_y/2) |x_y|^2, the weights of the anc = 0 and anc = 1 halves after the clock block
+// (the QFT of pass C is unitary), and the block totals go to two FP64 accumulators.
+enum SplitOp { kSplitDif = 0, kSplitMid = 1, kSplitDit = 2, kSplitHad = 3, kSplitMidSums = 4 };
+
+// Per-thread sums of pass B's weights: compensated (Kahan) in FP32, plain in FP64 and
+// double-float.
+template <class R>
+struct MidSums {
+  R s[2], c[2];
+  __device__ __forceinline__ void init() {
+    s[0] = s[1] = c[0] = c[1] = R(0);
+  }
+  __device__ __forceinline__ void add(int i, R v) {
+    if constexpr (std::is_same<R, float>::value) {
+      const float y = v - c[i];
+      const float t = s[i] + y;
+      c[i] = (t - s[i]) - y;
+      s[i] = t;
+    } else {
+      s[i] = s[i] + v;
+    }
+  }
+  __device__ __forceinline__ double total(int i) const {
+    if constexpr (std::is_same<R, float>::value) return (double)s[i] - (double)c[i];
+    else if constexpr (std::is_same<R, df>::value) return df_to_double(s[i]);
+    else return s[i];
+  }
+};
 
 constexpr int kSplitThreads = 256;
 constexpr int kSplitSegBytes = 256;  // bytes per row segment of a tile
@@ -731,6 +760,7 @@ constexpr int kSplitMinBits = 4;     // tile rows >= 16
 constexpr int kSplitMaxBits = 7;     // tile rows <= 128
 
 struct SplitArgs {
+  double* sums;        // kSplitMidSums: the two weights (accumulated)
   void* src;           // tiles are read here ...
   void* dst;           // ... and written back here at the same rows
   void* dst_cos;       // pass B: cos part (anc = 0 half)
@@ -954,7 +984,8 @@ __device__ __forceinline__ TilePos tile_pos(const SplitArgs& a, long long t) {
 // store back), shared by the streaming passes and the L2-staged group passes below.
 template <class R, int OP, bool FULL, int NB, bool WHOLE, bool CS = false, class TW>
 __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q, typename Cx<R>::T* X,
-                                           typename Cx<R>::T* Y, const TW& tw, int mt, long long row_units) {
+                                           typename Cx<R>::T* Y, const TW& tw, int mt, long long row_units,
+                                           MidSums<R>* sums = nullptr) {
   using T = typename Cx<R>::T;
   constexpr int upr = kSplitSegBytes / 16;
   constexpr int per = 16 / sizeof(T);
@@ -975,7 +1006,8 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
   } else if (OP == kSplitHad) {
     tile_stages<T, NB, false, 1, LWT, 0, 0, CVT>(X, a.b0, q.lo_fixed, a.m, tw, false);
     tile_store<T, NB, CS>(dst, X, row_units, q.row0, a.b0, split_scale<R>(a), a.scaled != 0);
-  } else {  // kSplitMid: b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
+  } else {  // kSplitMid(Sums): b0 = 0, the tile holds every low bit of the rows hi_fixed << NB
+    constexpr bool SUMS = OP == kSplitMidSums;
     tile_stages<T, NB, false, 0, LWT, 0, 0, CVT>(X, 0, 0, a.m, tw, false);
     const R s = split_scale<R>(a);
     uint4* cos_out = reinterpret_cast<uint4*>(static_cast<T*>(a.dst_cos) + q.base_amp);
@@ -991,13 +1023,22 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
 #pragma unroll
       for (int e = 0; e < per; ++e) {
         const T x = cscale(xt[e], s);
-        if (FULL) yt[e] = cscale(x, r.x * s);
-        else kt[e] = cscale(x, r.x);
+        if constexpr (SUMS) {
+          const R w = x.x * x.x + x.y * x.y;
+          sums->add(0, w * (r.x * r.x));
+          sums->add(1, w * (r.y * r.y));
+        } else if (FULL) {
+          yt[e] = cscale(x, r.x * s);
+        } else {
+          kt[e] = cscale(x, r.x);
+        }
         xt[e] = cscale(x, r.y * s);
       }
       reinterpret_cast<uint4*>(X)[u] = xv;
-      if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
-      else cos_out[(long long)y * row_units + h] = unit_out<T>(keep);
+      if constexpr (!SUMS) {
+        if (FULL) reinterpret_cast<uint4*>(Y)[u] = yv;
+        else cos_out[(long long)y * row_units + h] = unit_out<T>(keep);
+      }
     }
     __syncthreads();
     tile_stages<T, NB, true, 0>(X, 0, 0, a.m, tw, true);
@@ -1036,6 +1077,8 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
   const long long row_units = ((long long)1 << a.lo) / per;  // 16-byte units per row
   long long t = blockIdx.x;
   if (t >= a.tiles) return;  // block-uniform
+  MidSums<R> sums;
+  sums.init();
   {
     const TilePos q = tile_pos<NB, LW>(a, t);
     tile_issue<T, NB>(Xb, static_cast<const T*>(a.src) + q.base_amp, row_units, q.row0, a.b0);
@@ -1053,9 +1096,26 @@ __global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split
     split_cp_async_wait1();
     __syncthreads();  // the current tile has landed for every thread
     const TilePos q = tile_pos<NB, LW>(a, t);
-    split_tile<R, OP, FULL, NB, WHOLE>(a, q, Xb + buf * tile_amps, Y, tw, mt, row_units);
+    split_tile<R, OP, FULL, NB, WHOLE>(a, q, Xb + buf * tile_amps, Y, tw, mt, row_units, &sums);
     __syncthreads();  // this buffer is read out before it is refilled
     buf ^= 1;
+  }
+  if constexpr (OP == kSplitMidSums) {  // block totals of the two weights -> FP64 accumulators
+    __shared__ double red[2][kSplitThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      double v = sums.total(i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double v = 0.0;
+      for (int w = 0; w < kSplitThreads / 32; ++w) v += red[threadIdx.x][w];
+      atomicAdd(a.sums + threadIdx.x, v);
+    }
   }
   (void)rows;
 }
@@ -1698,6 +1758,39 @@ hhl_status clock_block_split(const Plan& p, void* state, cudaStream_t st) {
   return launch_split<R, kSplitDit, false>(a, FULL ? 2 : 1, st, "k_clock_pass_c");
 }
 
+// The clock block of the postselected solve: passes A, B (weights summed into sums[0..1], no
+// anc = 0 store) and C.
+template <class R>
+hhl_status clock_block_split_sums(const Plan& p, void* state, double* sums, cudaStream_t st) {
+  using T = typename Cx<R>::T;
+  const int m = p.n_c, m_lo = m / 2, m_hi = m - m_lo;
+  T* S0 = static_cast<T*>(state);
+  T* S1 = S0 + p.R * p.N;
+  SplitArgs a = {};
+  a.lo = p.n_s;
+  a.m = m;
+  a.rot = p.d_rot;
+  a.sums = sums;
+  a.src = S0;
+  a.dst = S1;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  hhl_status s = launch_split<R, kSplitDif, false>(a, 1, st, "k_clock_pass_a");
+  if (s != HHL_OK) return s;
+  a.src = S1;
+  a.dst = S1;
+  a.b0 = 0;
+  a.nb = m_lo;
+  a.scale = 1.0 / sqrt((double)p.R);
+  s = launch_split<R, kSplitMidSums, false>(a, 1, st, "k_clock_pass_b");
+  if (s != HHL_OK) return s;
+  a.src = S1;
+  a.dst = S1;
+  a.b0 = m_lo;
+  a.nb = m_hi;
+  return launch_split<R, kSplitDit, false>(a, 1, st, "k_clock_pass_c");
+}
+
 template <class R>
 hhl_status hadamard_split(void* base, int lo, int m, int outer, cudaStream_t st) {
   const int m_lo = m / 2, m_hi = m - m_lo;
@@ -1813,6 +1906,20 @@ hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st) {
     return p.full ? clock_block_split<df, true>(p, state, st) : clock_block_split<df, false>(p, state, st);
   }
   return p.full ? clock_block_impl<double, true>(p, state, st) : clock_block_impl<double, false>(p, state, st);
+}
+
+hhl_status launch_clock_block_sums(const Plan& p, void* state, double* sums, bool* done, cudaStream_t st) {
+  *done = false;
+  const long long half = p.R * p.N;
+  if (p.full) return HHL_OK;
+  if (p.prec == HHL_PREC_C64) {
+    if (clock_cluster_applies<float>(p) || !split_applies<float>(p.n_s, p.n_c, half) || group_applies(true)) return HHL_OK;
+    *done = true;
+    return clock_block_split_sums<float>(p, state, sums, st);
+  }
+  if (clock_cluster_applies<double>(p) || !split_applies<double>(p.n_s, p.n_c, half)) return HHL_OK;
+  *done = true;
+  return fp64_pipe() ? clock_block_split_sums<double>(p, state, sums, st) : clock_block_split_sums<df>(p, state, sums, st);
 }
 
 hhl_status launch_final_h(const Plan& p, void* state, cudaStream_t st) {

@@ -168,3 +168,60 @@ def test_host_fault_injection_plan():
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
     assert out.returncode == 0, out.stderr
     assert out.stdout.startswith("1 injected planner failure"), out.stdout
+
+
+def test_contract_names_reject_invalid_requests_on_the_host(lib):
+    """The hot-path contract's names (hhl_plan, hhl_batch_plan) are the library's calls: the
+    same host validation before any CUDA call."""
+    from paper_2307_00391_gb300 import _ffi
+    par = _ffi.Params()
+    lib.hhl_params_default(ctypes.byref(par))
+    prob, keep = _tridiag(4)
+    h = ctypes.c_void_p()
+    assert lib.hhl_plan(None, ctypes.byref(par), ctypes.byref(h)) == 1
+    bad = _ffi.Params.from_buffer_copy(par)
+    bad.n_clock = 0
+    assert lib.hhl_plan(ctypes.byref(prob), ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert lib.hhl_batch_plan(None, ctypes.byref(par), 1, ctypes.byref(h)) == 1
+    assert lib.hhl_batch_plan(ctypes.byref(prob), ctypes.byref(par), 0, ctypes.byref(h)) == 1
+
+
+@pytest.mark.parametrize("form", ["ae", "swap"])
+def test_qpp_host_builders_against_the_oracle(lib, form):
+    """The library's host builders of the QPP transform (iterate, rotation table, start state,
+    projection) against the oracle's independent constructions (App. D)."""
+    from oracle import qpp_oracle as q
+    from paper_2307_00391_gb300 import qpp
+    rng = np.random.default_rng(11)
+    for a in ((1, 2, 3) if form == "ae" else (1, 2)):
+        z = rng.standard_normal(1 << a)
+        z /= np.linalg.norm(z)
+        if form == "ae":
+            np.testing.assert_allclose(qpp.iterate(z), q.amplitude_estimation_iterate(z), atol=1e-14)
+        else:
+            np.testing.assert_allclose(qpp.swap_iterate(z), q.swap_test_iterate(z), atol=1e-14)
+            np.testing.assert_allclose(qpp.swap_register_state(z), q.swap_test_prepare(z).real, atol=1e-15)
+    if form == "ae":
+        np.testing.assert_allclose(qpp.rotation_table(7, 0.9), q.squaring_angles(7, 0.9), atol=1e-15)
+    else:
+        np.testing.assert_allclose(qpp.swap_rotation_table(7, 0.9), q.swap_squaring_angles(7, 0.9), atol=1e-15)
+    # the projection: a postselected vector built from known address amplitudes w_s times each
+    # block's start state returns w_s (the start states are orthonormal per block)
+    a = 2
+    z = rng.standard_normal(1 << a)
+    z /= np.linalg.norm(z)
+    n = 1 << a
+    f = 0 if form == "ae" else 1
+    dim = n * n if form == "ae" else 2 * n ** 3
+    b = np.zeros(dim)
+    assert lib.hhl_qpp_start_state(ctypes.c_void_p(z.ctypes.data), a, f, ctypes.c_void_p(b.ctypes.data)) == 0
+    w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = (b.reshape(n, -1) * np.sqrt(n) * w[:, None]).reshape(-1).astype(np.complex128)
+    out = np.zeros(2 * n)
+    assert lib.hhl_qpp_project(ctypes.c_void_p(v.ctypes.data), ctypes.c_void_p(b.ctypes.data), a, f,
+                               ctypes.c_void_p(out.ctypes.data)) == 0
+    np.testing.assert_allclose(out[0::2] + 1j * out[1::2], w, atol=1e-14)
+    # invalid requests
+    assert lib.hhl_qpp_iterate(None, a, f, ctypes.c_void_p(b.ctypes.data)) == 1
+    assert lib.hhl_qpp_rotation_table(0, 1.0, f, ctypes.c_void_p(out.ctypes.data)) == 1
+    assert lib.hhl_qpp_rotation_table(4, 1.5, f, ctypes.c_void_p(out.ctypes.data)) == 1

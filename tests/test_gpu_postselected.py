@@ -48,10 +48,18 @@ def _postselected(hhl, plan, b, n_s, n_c):
                                                    ("couette", 5, 10, 500.0, 0),     # groups and single bits
                                                    ("poiseuille", 10, 7, 50.0, 8),   # rows of several windows
                                                    ("couette", 1, 3, 1.0, 8)])       # the smallest row
-def test_postselected_solve_matches_oracle(hhl, monkeypatch, prec, flow, n_s, n_c, dt, r_max):
+@pytest.mark.parametrize("split", [False, True])
+def test_postselected_solve_matches_oracle(hhl, monkeypatch, prec, flow, n_s, n_c, dt, r_max, split):
+    """split: the clock block as split register passes (the path of large states, where pass B
+    sums the two halves' weights instead of storing the anc = 0 half), forced on small states."""
     if prec == "c128-fp64pipe":
         monkeypatch.setenv("HHL_FP64_PIPE", "1")
         prec = "c128"
+    if split:
+        if n_c < 8 or (1 << n_s) * 8 < 256:
+            pytest.skip("the split passes need 8 or more clock bits and 256-byte rows")
+        monkeypatch.setenv("HHL_FFT_SPLIT", "1")
+        monkeypatch.setenv("HHL_CLOCK_CLUSTER", "0")
     diag, off, b, walls = problem(flow, n_s)
     nu = 0.05
     pl = o.plan(o.dense_from_tridiag(diag, off), n_c, t0_rule="range_fill")
