@@ -956,8 +956,11 @@ def batch_block(pkg, args, world: int, local_rank: int) -> dict:
         batch.run_host(b_pin, stream=stream)
         e2e.append(time.perf_counter() - t0)
     e2e = e2e[1:]
-    flops = [2.0 * it["n_c"] * 8.0 * (1 << (it["n_c"] - 1)) * (1 << it["n_s"]) ** 2 for it in inst]
-    tc_flops = sum(f for f, bi in zip(flops, batch.instances) if bi["gemm"])
+    # GEMM flops of the two trees per instance (2^k rows at step k, both trees); on tcgen05 the
+    # steps with 2^k >= 128 of the instances with tiles
+    flops = [2.0 * 8.0 * ((1 << it["n_c"]) - 1) * (1 << it["n_s"]) ** 2 for it in inst]
+    tc_flops = sum(2.0 * 8.0 * sum(1 << k for k in range(7, it["n_c"])) * (1 << it["n_s"]) ** 2
+                   for it, bi in zip(inst, batch.instances) if bi["gemm"])
     batch.close()
     del out, eps, b_dev
     torch.cuda.empty_cache()

@@ -304,8 +304,10 @@ hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void
  * state_dev is the plan's state buffer used as workspace: afterwards only the clock = 0 row of
  * the anc = 1 half is defined (it holds v, so hhl_dissipation, hhl_sample and
  * hhl_qpp_dissipation may read it; hhl_measure may not). Asynchronous.
- * Errors: HHL_ERR_UNSUPPORTED unless the plan is Strang-Trotter with full_uncompute = 0 and
- * every clock bit's layer list fits one pass (2 r_k + 1 <= 17). */
+ * Dense plans run the two trees as controlled-U GEMMs on 2^k rows (tcgen05 where 2^k >= 128,
+ * CUDA cores below); Strang-Trotter plans as grouped Strang passes.
+ * Errors: HHL_ERR_UNSUPPORTED unless full_uncompute = 0 and, for Strang-Trotter plans, every
+ * clock bit's layer list fits one pass (2 r_k + 1 <= 17). */
 hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* state_dev, double* out_dev,
                                   double* eps_dev, void* stream);
 
@@ -353,8 +355,10 @@ hhl_status hhl_dissipation(hhl_plan_t plan, const void* state_dev, double* eps_o
 /* ---------------------------------------------------------------------------------- batch
  * Many HHL instances of uneven size in one CUDA graph (growth direction of the path: the
  * paper's sweeps over T0, clock count and system size, Sec. VI, run as one batch). Every
- * instance is the circuit of hhl_apply_circuit (complex64, postselect-early uncompute)
- * followed by the readouts of hhl_measure_async and hhl_dissipation_async; A must be a
+ * instance is the postselected solve of hhl_solve_postselected in its dense form (complex64:
+ * QPE by doubling and the uncompute by halving as controlled-U GEMMs on 2^k rows, tcgen05 where
+ * 2^k >= 128, the clock block), with the outputs of hhl_measure_async and
+ * hhl_dissipation_async; A must be a
  * Toeplitz tridiagonal matrix, because U_k is generated just in time from its analytic
  * eigenbasis (U_k[n][m] = g_k(|n-m|) - g_k(n+m), an O(N^2) FP64 kernel per k) instead of
  * being stored. */

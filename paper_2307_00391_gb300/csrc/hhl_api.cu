@@ -107,6 +107,18 @@ bool fault(const char* what) {
   return f != nullptr && strcmp(f, what) == 0;
 }
 
+// Tree steps of the postselected solve on fewer rows than one tcgen05 tile (2^k < 128) run on
+// CUDA cores, so tcgen05 plans also keep CUDA-core operands for k < kTreeSimtBits.
+constexpr int kTreeSimtBits = 7;
+
+// The GEMM operands of U_k (d_u: N x N complex128 on the device).
+hhl_status store_operands_k(Plan& p, const double2* d_u, int k, cudaStream_t st) {
+  if (p.gemm_impl == HHL_GEMM_SIMT) return launch_store_operands(p, d_u, k, st);
+  hhl_status s = tc_prepare_operands(p, d_u, k, st);
+  if (s == HHL_OK && k < kTreeSimtBits) s = launch_store_operands(p, d_u, k, st);
+  return s;
+}
+
 hhl_status dev_alloc(void** p, size_t bytes, uint64_t* counter) {
   if (fault("alloc")) return fail(HHL_ERR_OOM, "injected allocation failure (HHL_FAULT=alloc)");
   cudaError_t e = cudaMalloc(p, bytes);
@@ -568,10 +580,11 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       return fail(HHL_ERR_UNSUPPORTED, "tcgen05 GEMM not available for this size/precision");
     }
     const size_t mat = (size_t)N * N;
-    if (p.gemm_impl == HHL_GEMM_SIMT) {
-      HHL_ALLOC(p.d_bfwd, (size_t)p.n_c * mat * ab, &p.table_bytes);
-      HHL_ALLOC(p.d_badj, (size_t)p.n_c * mat * ab, &p.table_bytes);
-    }
+    // CUDA-core operands: every k (SIMT plans), or the k whose tree steps of the postselected
+    // solve have fewer rows than one tcgen05 tile (2^k < 128) (tcgen05 plans)
+    const int n_simt = p.gemm_impl == HHL_GEMM_SIMT ? p.n_c : std::min(p.n_c, kTreeSimtBits);
+    HHL_ALLOC(p.d_bfwd, (size_t)n_simt * mat * ab, &p.table_bytes);
+    HHL_ALLOC(p.d_badj, (size_t)n_simt * mat * ab, &p.table_bytes);
     // Toeplitz A (the channel-flow operators): U_k[n][m] = g_k(n-m) - g_k(n+m+2) from the
     // analytic sine basis, O(N^2) per k. Otherwise the eigenvectors go to the device once and
     // every U_k is one FP64 eigen-product (O(N^3)).
@@ -626,9 +639,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
           up[2 * e + 1] = qi[e];
         }
         ue = cudaMemcpyAsync(d_u, up.data(), 2 * mat * sizeof(double), cudaMemcpyHostToDevice, st);
-        hhl_status ks = ue == cudaSuccess ? (p.gemm_impl == HHL_GEMM_SIMT ? launch_store_operands(p, d_u, k, st)
-                                                                         : tc_prepare_operands(p, d_u, k, st))
-                                          : HHL_OK;
+        hhl_status ks = ue == cudaSuccess ? store_operands_k(p, d_u, k, st) : HHL_OK;
         if (ks != HHL_OK) { cudaStreamSynchronize(st); cudaFree(d_u); cudaStreamDestroy(st); hhl_plan_destroy(h); return ks; }
         if (ue == cudaSuccess) ue = cudaStreamSynchronize(st);  // the host buffer is reused next k
       }
@@ -668,8 +679,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       if (ce != cudaSuccess) break;
       hhl_status ks = eg.toeplitz ? launch_toeplitz_expm((int)N, d_c, d_s, d_ctab, d_g, d_u, st)
                                   : launch_expm_eigen((int)N, J, d_vr, d_vi, d_c, d_s, eg.wgt, d_u, st);
-      if (ks == HHL_OK) ks = p.gemm_impl == HHL_GEMM_SIMT ? launch_store_operands(p, d_u, k, st)
-                                                          : tc_prepare_operands(p, d_u, k, st);
+      if (ks == HHL_OK) ks = store_operands_k(p, d_u, k, st);
       if (ks != HHL_OK) { cudaStreamSynchronize(st); free_tmp(); cudaStreamDestroy(st); hhl_plan_destroy(h); return ks; }
       ce = cudaStreamSynchronize(st);  // host phase buffers are reused next iteration
     }
@@ -888,15 +898,27 @@ hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* st
   if (plan == nullptr || b_dev == nullptr || state_dev == nullptr || out_dev == nullptr)
     return fail(HHL_ERR_INVALID_ARG, "NULL argument");
   const Plan& p = plan->p;
+  const bool dense = p.expm_mode == HHL_EXPM_DENSE;
   std::string why;
-  if (!hhl::trotter_tree_supported(p, &why)) return fail(HHL_ERR_UNSUPPORTED, why);
+  if (dense && p.full) return fail(HHL_ERR_UNSUPPORTED, "the postselected solve needs full_uncompute = 0");
+  if (!dense && !hhl::trotter_tree_supported(p, &why)) return fail(HHL_ERR_UNSUPPORTED, why);
   cudaStream_t st = (cudaStream_t)stream;
   char* s0 = (char*)state_dev;
   char* s1 = s0 + (size_t)(p.R * p.N) * p.amp_bytes();
+  // the trees as controlled-product GEMMs (dense plans) or Strang passes (Trotter plans)
+  auto tree = [&](void* half, bool reduce) -> hhl_status {
+    if (!dense) return hhl::launch_trotter_tree(p, half, reduce, st);
+    for (int j = 0; j < p.n_c; ++j) {
+      hhl_status ts = hhl::launch_ctrl_u_tree(p, half, reduce ? p.n_c - 1 - j : j, reduce, st);
+      if (ts != HHL_OK) return ts;
+    }
+    return HHL_OK;
+  };
   HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal, 0, sizeof(double), st));
-  hhl_status s = hhl::launch_bnorm(b_dev, p.N, p.d_scal, st);
+  hhl_status s = hhl::tc_reset_error(p, st);
+  if (s == HHL_OK) s = hhl::launch_bnorm(b_dev, p.N, p.d_scal, st);
   if (s == HHL_OK) s = hhl::launch_prep_row(p, b_dev, s0, st);
-  if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s0, false, st);     // QPE by doubling
+  if (s == HHL_OK) s = tree(s0, false);                                // QPE by doubling
   // the clock block writes the whole anc = 1 half; the weights |S0|^2, |S1|^2 (= P(anc = 1))
   // come from its pass B on the split path, else from a read of both halves
   bool summed = false;
@@ -907,7 +929,7 @@ hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* st
   if (s == HHL_OK) s = hhl::launch_clock_block_sums(p, state_dev, p.d_scal + 1, &summed, st);
   if (s == HHL_OK && !summed) s = hhl::launch_clock_block(p, state_dev, st);
   if (s == HHL_OK && !summed) s = hhl::launch_measure_sums(p, state_dev, st);
-  if (s == HHL_OK) s = hhl::launch_trotter_tree(p, s1, true, st);      // uncompute + H + clock = 0
+  if (s == HHL_OK) s = tree(s1, true);                                 // uncompute + H + clock = 0
   if (s == HHL_OK) s = hhl::launch_measure_row(p, state_dev, out_dev, st);
   if (s == HHL_OK && eps_dev != nullptr) s = hhl::launch_dissipation(p, state_dev, eps_dev, nullptr, st);
   return s;

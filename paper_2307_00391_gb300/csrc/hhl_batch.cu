@@ -119,6 +119,99 @@ __global__ void k_ugen_embed_simt(int n_s, const float4* __restrict__ g, int adj
   }
 }
 
+// A controlled product on few rows (the small steps of the postselected solve's trees, 2^k < 128
+// rows): y[i][n] = sum_m U'[n][m] x[i][m] with U' = U_k or U_k^dagger = conj(U_k) generated on
+// the fly from the double-float g table (u_elem), so no N x N operand is written or read. A
+// block owns 32 output columns of MT rows (MT = min(16, rows of the step)); its 256 threads
+// split the sum over m in eight parts (32 columns x 8), the x rows staged in shared memory in
+// chunks of 128 columns, the parts added in shared memory at the end. Output rows are mapped as
+// the GEMMs' (write, or add to the row and scale).
+constexpr int kToepCols = 32, kToepSplit = 8, kToepChunk = 128;
+
+template <int MT>
+__global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half, int n_s, const float4* __restrict__ g,
+                                                       int adjoint, RowMap rows, int64_t m_rows) {
+  __shared__ float2 xs[MT][kToepChunk];
+  __shared__ float2 part[kToepSplit - 1][MT][kToepCols];
+  const int N = 1 << n_s;
+  const int tx = threadIdx.x % kToepCols, ty = threadIdx.x / kToepCols;
+  const int n = blockIdx.x * kToepCols + tx;
+  const int64_t i0 = (int64_t)blockIdx.y * MT;
+  const int64_t left = m_rows - i0;
+  const int nr = left < MT ? (int)left : MT;
+  float2 acc[MT];
+#pragma unroll
+  for (int r = 0; r < MT; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int c0 = 0; c0 < N; c0 += kToepChunk) {
+    const int cw = min(kToepChunk, N - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < MT * kToepChunk; e += 256) {
+      const int r = e / kToepChunk, c = e - r * kToepChunk;
+      xs[r][c] = (r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (n < N) {
+      constexpr int per = kToepChunk / kToepSplit;
+      const int q0 = ty * per, q1 = min(q0 + per, cw);
+      for (int c = q0; c < q1; ++c) {
+        float2 u = u_elem(g, n, c0 + c);
+        if (adjoint) u.y = -u.y;
+#pragma unroll
+        for (int r = 0; r < MT; ++r) {
+          const float2 x = xs[r][c];
+          acc[r].x = fmaf(u.x, x.x, fmaf(-u.y, x.y, acc[r].x));
+          acc[r].y = fmaf(u.x, x.y, fmaf(u.y, x.x, acc[r].y));
+        }
+      }
+    }
+  }
+  if (ty > 0) {
+#pragma unroll
+    for (int r = 0; r < MT; ++r) part[ty - 1][r][tx] = acc[r];
+  }
+  __syncthreads();
+  if (ty == 0 && n < N) {
+    const float sc = (float)rows.scale;
+#pragma unroll
+    for (int r = 0; r < MT; ++r) {
+      if (r >= nr) break;
+      float2 y = acc[r];
+#pragma unroll
+      for (int t = 0; t < kToepSplit - 1; ++t) {
+        y.x += part[t][r][tx].x;
+        y.y += part[t][r][tx].y;
+      }
+      float2* d = half + rowmap_out(rows, i0 + r) * N + n;
+      if (rows.accumulate) {
+        y.x += d->x;
+        y.y += d->y;
+        if (rows.scale != 1.0) {
+          y.x *= sc;
+          y.y *= sc;
+        }
+      }
+      *d = y;
+    }
+  }
+}
+
+hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
+                                cudaStream_t st) {
+  const int N = 1 << n_s;
+  const int mt = m >= 16 ? 16 : (int)m;  // m is a power of two here
+  dim3 grid((unsigned)((N + kToepCols - 1) / kToepCols), (unsigned)((m + mt - 1) / mt));
+  HHL_PROF_BEGIN(st);
+  switch (mt) {
+    case 1: k_toeplitz_rows<1><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+    case 2: k_toeplitz_rows<2><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+    case 4: k_toeplitz_rows<4><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+    case 8: k_toeplitz_rows<8><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+    default: k_toeplitz_rows<16><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+  }
+  HHL_LAUNCH_CHECK("k_toeplitz_rows");
+  return HHL_OK;
+}
+
 struct Work {
   cudaStream_t s = nullptr;
   cudaEvent_t done = nullptr;
@@ -199,7 +292,9 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
   const double* b = B->d_b + B->b_off[i];
   HHL_CUDA_TRY(cudaMemsetAsync(p.d_scal, 0, 16 * sizeof(double), st));
   hhl_status s = launch_bnorm(b, p.N, p.d_scal, st);
-  if (s == HHL_OK) s = launch_prep_fill(p, b, state, st);
+  // the postselected solve (the same circuit rearranged for its prepared input; see
+  // hhl_solve_postselected): only the clock = 0 row of the anc = 0 half is prepared
+  if (s == HHL_OK) s = launch_prep_row(p, b, state, st);
   if (s != HHL_OK) return s;
   // g_k for every k of this instance
   {
@@ -211,31 +306,42 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
     HHL_LAUNCH_CHECK("k_ugen_g");
   }
   const int M = (int)(2 * p.N + 2);
-  auto product = [&](int k, bool adjoint) -> hhl_status {
+  // tree step k: expansion (rows [2^k, 2^(k+1)) = U_k rows [0, 2^k), anc = 0 half) or
+  // reduction (rows [0, 2^k) += U_k^dagger rows [2^k, 2^(k+1)), anc = 1 half, the last step
+  // scaled by 2^(-n_c/2)), on tcgen05 where the instance has tiles and 2^k >= 128 rows
+  auto step = [&](int k, bool reduce) -> hhl_status {
     const float4* gk = B->d_g + B->g_off[i] + (size_t)k * M;
     const int64_t N2 = 2 * p.N;
-    if (B->gemm[i] == 0) {
-      int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
+    const int64_t m = 1LL << k;
+    RowMap rows;
+    rows.in_off = reduce ? m : 0;
+    rows.out_off = reduce ? 0 : m;
+    rows.accumulate = reduce ? 1 : 0;
+    if (reduce && k == 0) rows.scale = 1.0 / sqrt((double)p.R);
+    void* half = reduce ? (void*)s1 : (void*)s0;
+    const int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
+    if (m < 128)  // few rows: U_k generated on the fly, no N x N operand
+      return launch_toeplitz_rows((float2*)half, p.n_s, gk, reduce ? 1 : 0, rows, m, st);
+    if (B->gemm[i] == 0 || rows.scale != 1.0) {
       HHL_PROF_BEGIN(st);
-      k_ugen_embed_simt<<<g, 256, 0, st>>>(p.n_s, gk, adjoint ? 1 : 0, (float2*)w.ubuf);
+      k_ugen_embed_simt<<<g, 256, 0, st>>>(p.n_s, gk, reduce ? 1 : 0, (float2*)w.ubuf);
       HHL_LAUNCH_CHECK("k_ugen_embed_simt");
-      return launch_ctrl_u_simt(p, adjoint ? (void*)s1 : (void*)s0, k, w.ubuf, st);
+      return launch_ctrl_u_simt_map(p, half, rows, m, w.ubuf, st);
     }
     __half* hi = (__half*)w.ubuf;
     __half* lo = hi + N2 * N2;
-    int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
     HHL_PROF_BEGIN(st);
-    k_ugen_embed_tc<<<g, 256, 0, st>>>(p.n_s, gk, adjoint ? 1 : 0, hi, lo);
+    k_ugen_embed_tc<<<g, 256, 0, st>>>(p.n_s, gk, reduce ? 1 : 0, hi, lo);
     HHL_LAUNCH_CHECK("k_ugen_embed_tc");
     const CUtensorMap* mp = &B->maps[(size_t)i * 4];
-    return launch_tc_gemm(p.n_s, p.R / 2, k, adjoint ? (void*)s1 : (void*)s0, w.a_hi, w.a_lo, mp[0], mp[1], mp[2],
-                          mp[3], B->gemm[i], B->d_err, st);
+    return launch_tc_gemm_map(p.n_s, m, rows, half, w.a_hi, w.a_lo, mp[0], mp[1], mp[2], mp[3], B->gemm[i], B->d_err,
+                              st);
   };
-  for (int k = 0; k < p.n_c && s == HHL_OK; ++k) s = product(k, false);
+  for (int k = 0; k < p.n_c && s == HHL_OK; ++k) s = step(k, false);
   if (s == HHL_OK) s = launch_clock_block(p, state, st);
-  for (int k = p.n_c - 1; k >= 0 && s == HHL_OK; --k) s = product(k, true);
-  if (s == HHL_OK) s = launch_final_h(p, state, st);
-  if (s == HHL_OK) s = launch_measure(p, state, B->d_out + B->out_off[i], st);
+  if (s == HHL_OK) s = launch_measure_sums(p, state, st);  // |S0|^2, |S1|^2 before the reduction
+  for (int k = p.n_c - 1; k >= 0 && s == HHL_OK; --k) s = step(k, true);
+  if (s == HHL_OK) s = launch_measure_row(p, state, B->d_out + B->out_off[i], st);
   if (s == HHL_OK) s = launch_dissipation(p, state, B->d_eps + i, nullptr, st);
   return s;
 }
@@ -325,13 +431,19 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
     if (gsel != 0 && (p.R / 2 < 128 || 2 * p.N < gsel)) gsel = 0;  // tile does not fit
     B->gemm[i] = gsel;
     p.gemm_impl = gsel ? HHL_GEMM_TCGEN05 : HHL_GEMM_SIMT;
-    B->gemm_flops += 2.0 * p.n_c * 8.0 * (double)(p.R / 2) * (double)p.N * (double)p.N;
+    // the two trees: sum over k of 2^k rows each (expansion and reduction)
+    B->gemm_flops += 2.0 * 8.0 * (double)(p.R - 1) * (double)p.N * (double)p.N;
   }
   // LPT assignment of instances to worker streams by GEMM work
   streams = std::min(streams, count);
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
-  auto cost = [&](int i) { return (double)(B->plans[i].R / 2) * B->plans[i].N * B->plans[i].N * B->plans[i].n_c + 1.0; };
+  // work of an instance: the GEMM rows of its two trees (2^n_c) and its 2 n_c operand
+  // generations, each over N^2 entries
+  auto cost = [&](int i) {
+    const Plan& q = B->plans[i];
+    return (double)(q.R + 2 * q.n_c) * (double)q.N * (double)q.N + 1.0;
+  };
   std::sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
   std::vector<double> load(streams, 0.0);
   B->work.resize(streams);

@@ -198,6 +198,32 @@ inline void df_split(double v, float* h, float* l) {
   *l = (float)(v - (double)*h);
 }
 
+// ------------------------------------------------------------------ row maps of the controlled products
+// Which state rows a controlled-U GEMM reads and writes. The circuit's controlled U_k (k >= 0):
+// the rows with clock bit k set, in place. The trees of the postselected solve (k = -1):
+// contiguous input rows i + in_off, output rows i + out_off, overwritten (expansion) or added
+// to (reduction), the stored value multiplied by `scale`.
+struct RowMap {
+  int k = -1;
+  int accumulate = 0;
+  int64_t in_off = 0, out_off = 0;
+  double scale = 1.0;
+};
+__host__ __device__ __forceinline__ int64_t rowmap_bit(int64_t i, int k) {
+  return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
+}
+__host__ __device__ __forceinline__ int64_t rowmap_in(const RowMap& m, int64_t i) {
+  return m.k >= 0 ? rowmap_bit(i, m.k) : i + m.in_off;
+}
+__host__ __device__ __forceinline__ int64_t rowmap_out(const RowMap& m, int64_t i) {
+  return m.k >= 0 ? rowmap_bit(i, m.k) : i + m.out_off;
+}
+inline RowMap circuit_rows(int k) {
+  RowMap m;
+  m.k = k;
+  return m;
+}
+
 // ------------------------------------------------------------------ the plan
 // One Trotter pass: clock bits [kb, kb + gbits) (single_k >= 0: the one bit single_k, rows
 // with that bit set) and the offset of its per-row-pattern layer lists in the plan's table.
@@ -254,6 +280,13 @@ hhl_status launch_prep_fill(const Plan& p, const double* b, void* state, cudaStr
 hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st);
 // SIMT controlled product with an explicit operand B[m][n] (U^T forward, conj(U) adjoint).
 hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, cudaStream_t st);
+// The same on m_sub rows mapped by `rows` (the trees of the postselected solve).
+hhl_status launch_ctrl_u_simt_map(const Plan& p, void* half, const RowMap& rows, int64_t m_sub, const void* B,
+                                  cudaStream_t st);
+// One tree step of the dense postselected solve: expansion (rows [2^k, 2^(k+1)) = U_k rows
+// [0, 2^k)) or reduction (rows [0, 2^k) += U_k^dagger rows [2^k, 2^(k+1)), the last one, k = 0,
+// scaled by 2^(-n_c/2)), on the plan's operands (tcgen05 where 2^k >= 128, else CUDA cores).
+hhl_status launch_ctrl_u_tree(const Plan& p, void* half, int k, bool reduce, cudaStream_t st);
 hhl_status launch_clock_block(const Plan& p, void* state, cudaStream_t st);
 // The clock block for the postselected solve (postselect-early plans on the split-pass path):
 // the anc = 0 half is not stored; the weights of the two halves after the block are added to
@@ -321,6 +354,13 @@ namespace hhl {
 hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo,
                           const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
                           const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
+// The same on m_sub (a multiple of 128) rows mapped by `rows`.
+hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& rows, void* half, void* a_hi, void* a_lo,
+                              const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
+                              const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
+// The plan's tcgen05 product on mapped rows (m_sub a multiple of 128).
+hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, int64_t m_sub, int k, bool adjoint,
+                                cudaStream_t st);
 hhl_status tc_make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows);
 hhl_status tc_init_kernels();
 

@@ -162,15 +162,12 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
   lo = __float2half_rn(v - __half2float(hi));
 }
 
-__device__ __forceinline__ int64_t row_with_bit_tc(int64_t i, int k) {
-  return ((i >> k) << (k + 1)) | (1LL << k) | (i & ((1LL << k) - 1));
-}
 
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                    const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-                   float* __restrict__ state_half, int n_s, int k, int k_iters, int* err, long long wait_cycles,
+                   float* __restrict__ state_half, int n_s, RowMap rows, int k_iters, int* err, long long wait_cycles,
                    int fault) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -266,7 +263,7 @@ __global__ void __launch_bounds__(128, 1)
   if (abort_flag == 0) {  // uniform across the CTA: tcgen05.ld is warp-collective
     const int64_t N2 = 2LL << n_s;  // floats per state row
     const int64_t i = m0 + warp * 32 + lane;
-    float* dst = state_half + row_with_bit_tc(i, k) * N2 + n0;
+    float* dst = state_half + rowmap_out(rows, i) * N2 + n0;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
@@ -274,9 +271,15 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld_32cols(lane_addr + c, v);
       float4* d4 = reinterpret_cast<float4*>(dst + c);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        d4[q] = make_float4(v[4 * q] * kUnscale, v[4 * q + 1] * kUnscale, v[4 * q + 2] * kUnscale,
-                            v[4 * q + 3] * kUnscale);
+      for (int q = 0; q < 8; ++q) {
+        float4 o = make_float4(v[4 * q] * kUnscale, v[4 * q + 1] * kUnscale, v[4 * q + 2] * kUnscale,
+                               v[4 * q + 3] * kUnscale);
+        if (rows.accumulate) {  // a reduction step of the postselected solve: the row keeps its value
+          const float4 prev = d4[q];
+          o = make_float4(prev.x + o.x, prev.y + o.y, prev.z + o.z, prev.w + o.w);
+        }
+        d4[q] = o;
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -286,10 +289,11 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-// Rows with clock bit k set -> compact FP16 hi / lo arrays (M_sub x 2N), scaled by 2^15.
+// The mapped rows (those with clock bit k set, or a tree step's source rows) -> compact FP16
+// hi / lo arrays (M_sub x 2N), scaled by 2^15.
 // An amplitude component of magnitude >= 2 cannot be represented: error flag 4.
 __global__ void k_tc_split_rows(const float4* __restrict__ half, uint2* __restrict__ a_hi, uint2* __restrict__ a_lo,
-                                int n_s, int k, int64_t m_sub, int* err) {
+                                int n_s, RowMap rows, int64_t m_sub, int* err) {
   const int row4_bits = n_s - 1;  // float4 per row = 2N/4 = 2^(n_s-1)
   const int64_t total = m_sub << row4_bits;
   constexpr int U = 4;  // loads in flight per thread
@@ -302,7 +306,7 @@ __global__ void k_tc_split_rows(const float4* __restrict__ half, uint2* __restri
       const int64_t e = e0 + q * stride;
       if (e < total) {
         const int64_t i = e >> row4_bits, c = e & ((1LL << row4_bits) - 1);
-        v[q] = half[(row_with_bit_tc(i, k) << row4_bits) + c];
+        v[q] = half[(rowmap_in(rows, i) << row4_bits) + c];
       }
     }
 #pragma unroll
@@ -425,16 +429,30 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
 }
 
 hhl_status launch_ctrl_u_tc(const Plan& p, void* half, int k, bool adjoint, cudaStream_t st) {
+  return launch_ctrl_u_tc_map(p, half, circuit_rows(k), p.R / 2, k, adjoint, st);
+}
+
+hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, int64_t m_sub, int k, bool adjoint,
+                                cudaStream_t st) {
   const TcState* t = static_cast<const TcState*>(p.d_tc);
   if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
   const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
-  return launch_tc_gemm(p.n_s, p.R / 2, k, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn, t->err, st);
+  return launch_tc_gemm_map(p.n_s, m_sub, rows, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn,
+                            t->err, st);
 }
 
 hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo, const CUtensorMap& map_ahi,
                           const CUtensorMap& map_alo, const CUtensorMap& map_bhi, const CUtensorMap& map_blo, int bn,
                           int* err, cudaStream_t st) {
+  return launch_tc_gemm_map(n_s, m_sub, circuit_rows(k), half, a_hi, a_lo, map_ahi, map_alo, map_bhi, map_blo, bn, err,
+                            st);
+}
+
+hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* half, void* a_hi, void* a_lo,
+                              const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
+                              const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st) {
   const int64_t N2 = 2LL << n_s;
+  if (m_sub < kBM || m_sub % kBM != 0) return fail(HHL_ERR_INVALID_ARG, "tcgen05 GEMM rows must be a multiple of 128");
   // HHL_FAULT=tc_wait (testing the timeout path): no operand copy is issued and every wait is
   // bounded by about a millisecond, so the MMA lane's first wait runs out with nothing in flight
   const char* fenv = getenv("HHL_FAULT");

@@ -99,7 +99,7 @@ template <class R, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_ctrl_gemm_simt(const typename Cx<R>::T* __restrict__ S,
                                                         typename Cx<R>::T* __restrict__ out,
                                                         const typename Cx<R>::T* __restrict__ B,
-                                                        int n_s, int k, int64_t m_sub) {
+                                                        int n_s, RowMap rows, int64_t m_sub) {
   using T = typename Cx<R>::T;
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ T As[BK][BM + 1];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_ctrl_gemm_simt(const typename Cx<R>::T*
       const int r = e / BK, kk = e % BK;
       const int64_t i = i0 + r, m = m0 + kk;
       T v = mk<R>((R)0, (R)0);
-      if (i < m_sub && m < N) v = S[row_with_bit(i, k) * N + m];
+      if (i < m_sub && m < N) v = S[rowmap_in(rows, i) * N + m];
       As[kk][r] = v;
     }
     for (int e = threadIdx.x; e < BK * BN; e += 256) {
@@ -160,15 +160,23 @@ __global__ void __launch_bounds__(256) k_ctrl_gemm_simt(const typename Cx<R>::T*
   }
 }
 
-// S[row(i)][:] = out[i][:] for the rows with clock bit k set.
+// S[row(i)][:] = out[i][:] (the rows with clock bit k set, or a tree's mapped rows, where the
+// reduction adds out[i][:] to the row and its last step scales the sum).
 template <class R>
 __global__ void k_rows_scatter(typename Cx<R>::T* __restrict__ S, const typename Cx<R>::T* __restrict__ out,
-                               int n_s, int k, int64_t m_sub) {
+                               int n_s, RowMap rows, int64_t m_sub) {
   const int64_t N = 1LL << n_s;
   const int64_t total = m_sub * N;
+  const R sc = (R)rows.scale;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e >> n_s, m = e & (N - 1);
-    S[row_with_bit(i, k) * N + m] = out[e];
+    typename Cx<R>::T* d = S + rowmap_out(rows, i) * N + m;
+    if (rows.accumulate) {
+      const typename Cx<R>::T v = cadd(*d, out[e]);
+      *d = rows.scale != 1.0 ? cscale(v, sc) : v;
+    } else {
+      *d = out[e];
+    }
   }
 }
 
@@ -585,8 +593,34 @@ hhl_status launch_ctrl_u_dense(const Plan& p, void* half, int k, bool adjoint, c
   return launch_ctrl_u_simt(p, half, k, B, st);
 }
 
+hhl_status launch_ctrl_u_tree(const Plan& p, void* half, int k, bool reduce, cudaStream_t st) {
+  RowMap rows;
+  const int64_t m = 1LL << k;
+  if (reduce) {
+    rows.in_off = m;
+    rows.out_off = 0;
+    rows.accumulate = 1;
+    if (k == 0) rows.scale = 1.0 / sqrt((double)p.R);
+  } else {
+    rows.in_off = 0;
+    rows.out_off = m;
+  }
+  if (p.gemm_impl == HHL_GEMM_TCGEN05 && m >= 128 && rows.scale == 1.0)
+    return launch_ctrl_u_tc_map(p, half, rows, m, k, reduce, st);
+  if (p.d_bfwd == nullptr) {  // a tcgen05 plan keeps no CUDA-core operands
+    return fail(HHL_ERR_UNSUPPORTED, "tree step below 128 rows on a tcgen05-only plan");
+  }
+  const size_t mat = (size_t)p.N * p.N;
+  const void* B = (const char*)(reduce ? p.d_badj : p.d_bfwd) + (size_t)k * mat * p.amp_bytes();
+  return launch_ctrl_u_simt_map(p, half, rows, m, B, st);
+}
+
 hhl_status launch_ctrl_u_simt(const Plan& p, void* half, int k, const void* B, cudaStream_t st) {
-  const int64_t m_sub = p.R / 2;
+  return launch_ctrl_u_simt_map(p, half, circuit_rows(k), p.R / 2, B, st);
+}
+
+hhl_status launch_ctrl_u_simt_map(const Plan& p, void* half, const RowMap& k, int64_t m_sub, const void* B,
+                                  cudaStream_t st) {
   const int64_t N = p.N;
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((m_sub + 63) / 64));
   const int sg = grid_for(m_sub * N, kThreads, 152 * 32);

@@ -118,7 +118,7 @@ def test_postselected_solve_refuses_other_plans(hhl):
     import torch
     diag, off, b, walls = problem("poiseuille", 4)
     out = torch.empty(4 + 32, dtype=torch.float64, device="cuda")
-    for kw in (dict(expm="dense"), dict(expm="trotter", full_uncompute=True),
+    for kw in (dict(expm="trotter", full_uncompute=True),
                dict(expm="trotter", trotter_dt=1e-3, trotter_steps_max=40)):   # a bit over several passes
         plan = hhl.HHLPlan(4, 5, diag=diag, off=off, precision="c64", **kw)
         st = plan.new_state()
@@ -152,3 +152,40 @@ def test_postselected_32_qubits_against_full_state(hhl):
     assert got["p_anc1"] == pytest.approx(m["p_anc1"], rel=1e-4)
     assert got["norm"] == pytest.approx(1.0, abs=1e-5)
     assert abs(np.vdot(got["xhat"], m["xhat"])) >= 1 - 1e-6
+
+
+@pytest.mark.parametrize("prec,gemm,flow,n_s,n_c", [("c64", "tcgen05", "couette", 7, 8),      # k = 7 on tcgen05
+                                                    ("c64", "tcgen05", "poiseuille", 8, 10),  # k = 7..9 on tcgen05
+                                                    ("c64", "simt", "poiseuille", 4, 6),
+                                                    ("c128", "simt", "couette", 5, 7),
+                                                    ("c128", "simt", "poiseuille", 1, 3)])
+def test_postselected_dense_matches_oracle(hhl, prec, gemm, flow, n_s, n_c):
+    """The dense form of the postselected solve (the trees as controlled-U GEMMs on 2^k rows:
+    tcgen05 where 2^k >= 128, CUDA cores below) against the oracle's whole circuit."""
+    diag, off, b, walls = problem(flow, n_s)
+    nu = 0.05
+    pl = o.plan(o.dense_from_tridiag(diag, off), n_c, t0_rule="range_fill")
+    psi = run_stages(b, n_s, pl)["final_h"]
+    post = o.postselect(psi, n_s, n_c)
+    plan = hhl.HHLPlan(n_s, n_c, diag=diag, off=off, precision=prec, gemm=gemm, nu=nu, walls=walls)
+    got = _postselected(hhl, plan, b, n_s, n_c)
+    N = 1 << n_s
+    tol = TOL[prec]
+    v_ref = psi.reshape(2, 1 << n_c, N)[1, 0]
+    dv = np.abs(got["v"] - v_ref).max()
+    assert dv <= tol, dv
+    assert got["p_anc1"] == pytest.approx(post["p_anc1"], rel=1e-9 if prec == "c128" else 1e-4)
+    assert got["p_success"] == pytest.approx(post["p_success"], rel=1e-9 if prec == "c128" else 1e-4)
+    bound = (1.0 + math.sqrt(N)) * dv / (np.linalg.norm(got["v"]) - math.sqrt(N) * dv) + 1e-13
+    np.testing.assert_allclose(got["xhat"], post["xhat"], atol=bound)
+    u_ref = o.velocity(post["v"], np.linalg.norm(b), pl["C"], pl["lam_ub"])
+    assert got["eps"] == pytest.approx(o.dissipation(u_ref, walls[0], walls[1], nu), rel=1e-9 if prec == "c128" else 1e-3)
+
+
+def test_postselected_dense_refuses_full_uncompute(hhl):
+    import torch
+    diag, off, b, walls = problem("poiseuille", 4)
+    plan = hhl.HHLPlan(4, 5, diag=diag, off=off, precision="c64", full_uncompute=True)
+    with pytest.raises(hhl.HHLError) as e:
+        plan.solve_postselected(_b_dev(b), plan.new_state(), torch.empty(40, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 8
