@@ -694,6 +694,10 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
         half = (1 << (wl["n_s"] + wl["n_c"])) * prec_bytes
         for x in "abc":
             alg[f"k_clock_pass_{x}"] = ("byte", 2.0 * half / 3)
+        if wl["expm"] == "dense":  # tensor-core tree steps: 2^k rows for k >= 7, both trees
+            n_c, N = wl["n_c"], 1 << wl["n_s"]
+            tc_steps = max(1, n_c - 7)
+            alg["k_ctrl_gemm_tc"] = ("flop", 2.0 * 8.0 * sum(1 << k for k in range(7, n_c)) * N * N / (2 * tc_steps))
     hbm_bytes_step, hbm_ms_step = 0.0, 0.0
     for name, (n, ms) in prof.items():
         kind, per = alg.get(name, (None, 0.0))
@@ -759,6 +763,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                                                   min(args.warmup, 3), world, local_rank, e2e_steps=3)
         sub["couette_1024"] = solve_block(pkg, "couette_1024", "c64", "auto", args.steps, args.warmup, world,
                                           local_rank)
+        sub["couette_1024_postselected"] = solve_block(pkg, "couette_1024", "c64", "auto", args.steps, args.warmup,
+                                                       world, local_rank, postselected=True)
         sub["batch_256"] = batch_block(pkg, args, world, local_rank)
     if rank != 0:
         return

@@ -115,7 +115,7 @@ constexpr int kTreeSimtBits = 7;
 hhl_status store_operands_k(Plan& p, const double2* d_u, int k, cudaStream_t st) {
   if (p.gemm_impl == HHL_GEMM_SIMT) return launch_store_operands(p, d_u, k, st);
   hhl_status s = tc_prepare_operands(p, d_u, k, st);
-  if (s == HHL_OK && k < kTreeSimtBits) s = launch_store_operands(p, d_u, k, st);
+  if (s == HHL_OK && k < kTreeSimtBits && p.d_bfwd != nullptr) s = launch_store_operands(p, d_u, k, st);
   return s;
 }
 
@@ -582,9 +582,15 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
     const size_t mat = (size_t)N * N;
     // CUDA-core operands: every k (SIMT plans), or the k whose tree steps of the postselected
     // solve have fewer rows than one tcgen05 tile (2^k < 128) (tcgen05 plans)
-    const int n_simt = p.gemm_impl == HHL_GEMM_SIMT ? p.n_c : std::min(p.n_c, kTreeSimtBits);
-    HHL_ALLOC(p.d_bfwd, (size_t)n_simt * mat * ab, &p.table_bytes);
-    HHL_ALLOC(p.d_badj, (size_t)n_simt * mat * ab, &p.table_bytes);
+    // (complex64 plans of a Toeplitz A keep the g_k tables instead: their small steps generate
+    // U_k on the fly)
+    if (eg.toeplitz && p.prec == HHL_PREC_C64)
+      HHL_ALLOC(p.d_gdf, (size_t)p.n_c * (2 * N + 2) * sizeof(float4), &p.table_bytes);
+    const int n_simt = p.gemm_impl == HHL_GEMM_SIMT ? p.n_c : (p.d_gdf != nullptr ? 0 : std::min(p.n_c, kTreeSimtBits));
+    if (n_simt > 0) {
+      HHL_ALLOC(p.d_bfwd, (size_t)n_simt * mat * ab, &p.table_bytes);
+      HHL_ALLOC(p.d_badj, (size_t)n_simt * mat * ab, &p.table_bytes);
+    }
     // Toeplitz A (the channel-flow operators): U_k[n][m] = g_k(n-m) - g_k(n+m+2) from the
     // analytic sine basis, O(N^2) per k. Otherwise the eigenvectors go to the device once and
     // every U_k is one FP64 eigen-product (O(N^3)).
@@ -679,6 +685,7 @@ hhl_status hhl_plan_create(const hhl_problem* prob, const hhl_params* params, hh
       if (ce != cudaSuccess) break;
       hhl_status ks = eg.toeplitz ? launch_toeplitz_expm((int)N, d_c, d_s, d_ctab, d_g, d_u, st)
                                   : launch_expm_eigen((int)N, J, d_vr, d_vi, d_c, d_s, eg.wgt, d_u, st);
+      if (ks == HHL_OK && p.d_gdf != nullptr) ks = launch_g_to_df((int)N, d_g, p.d_gdf + (size_t)k * (2 * N + 2), st);
       if (ks == HHL_OK) ks = store_operands_k(p, d_u, k, st);
       if (ks != HHL_OK) { cudaStreamSynchronize(st); free_tmp(); cudaStreamDestroy(st); hhl_plan_destroy(h); return ks; }
       ce = cudaStreamSynchronize(st);  // host phase buffers are reused next iteration
@@ -747,7 +754,7 @@ hhl_status hhl_plan(const hhl_problem* prob, const hhl_params* params, hhl_plan_
 void hhl_plan_destroy(hhl_plan_t plan) {
   if (plan == nullptr) return;
   Plan& p = plan->p;
-  void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
+  void* ptrs[] = {p.d_bfwd, p.d_badj, p.d_gdf, p.d_rot, p.d_scal, p.d_b, p.d_bs, p.d_scratch, p.d_trot,
                   p.d_trot_lists, plan->d_meas, plan->d_u, plan->d_cdf, plan->d_bsplit, plan->d_qpp};
   for (void* q : ptrs)
     if (q) cudaFree(q);

@@ -75,12 +75,7 @@ __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-// U_k[n][m] = g(|n-m|) - g(n+m+2) (0-based n, m) from the double-float table, in FP32: the
-// difference of the high parts is exact for close values and the low parts restore the rest.
-__device__ __forceinline__ float2 u_elem(const float4* __restrict__ g, int n, int m) {
-  const float4 a = g[n > m ? n - m : m - n], b = g[n + m + 2];
-  return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
-}
+__device__ __forceinline__ float2 u_elem(const float4* __restrict__ g, int n, int m) { return toeplitz_u(g, n, m); }
 
 // Split-FP16 real embedding of U_k (adjoint: U_k^dagger = conj(U_k), A real symmetric),
 // scaled by 2^15: hi / lo (2N x 2N), rows = output real column, columns = input real index.
@@ -117,99 +112,6 @@ __global__ void k_ugen_embed_simt(int n_s, const float4* __restrict__ g, int adj
     if (adjoint) u.y = -u.y;
     B[e] = u;
   }
-}
-
-// A controlled product on few rows (the small steps of the postselected solve's trees, 2^k < 128
-// rows): y[i][n] = sum_m U'[n][m] x[i][m] with U' = U_k or U_k^dagger = conj(U_k) generated on
-// the fly from the double-float g table (u_elem), so no N x N operand is written or read. A
-// block owns 32 output columns of MT rows (MT = min(16, rows of the step)); its 256 threads
-// split the sum over m in eight parts (32 columns x 8), the x rows staged in shared memory in
-// chunks of 128 columns, the parts added in shared memory at the end. Output rows are mapped as
-// the GEMMs' (write, or add to the row and scale).
-constexpr int kToepCols = 32, kToepSplit = 8, kToepChunk = 128;
-
-template <int MT>
-__global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half, int n_s, const float4* __restrict__ g,
-                                                       int adjoint, RowMap rows, int64_t m_rows) {
-  __shared__ float2 xs[MT][kToepChunk];
-  __shared__ float2 part[kToepSplit - 1][MT][kToepCols];
-  const int N = 1 << n_s;
-  const int tx = threadIdx.x % kToepCols, ty = threadIdx.x / kToepCols;
-  const int n = blockIdx.x * kToepCols + tx;
-  const int64_t i0 = (int64_t)blockIdx.y * MT;
-  const int64_t left = m_rows - i0;
-  const int nr = left < MT ? (int)left : MT;
-  float2 acc[MT];
-#pragma unroll
-  for (int r = 0; r < MT; ++r) acc[r] = make_float2(0.f, 0.f);
-  for (int c0 = 0; c0 < N; c0 += kToepChunk) {
-    const int cw = min(kToepChunk, N - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < MT * kToepChunk; e += 256) {
-      const int r = e / kToepChunk, c = e - r * kToepChunk;
-      xs[r][c] = (r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    if (n < N) {
-      constexpr int per = kToepChunk / kToepSplit;
-      const int q0 = ty * per, q1 = min(q0 + per, cw);
-      for (int c = q0; c < q1; ++c) {
-        float2 u = u_elem(g, n, c0 + c);
-        if (adjoint) u.y = -u.y;
-#pragma unroll
-        for (int r = 0; r < MT; ++r) {
-          const float2 x = xs[r][c];
-          acc[r].x = fmaf(u.x, x.x, fmaf(-u.y, x.y, acc[r].x));
-          acc[r].y = fmaf(u.x, x.y, fmaf(u.y, x.x, acc[r].y));
-        }
-      }
-    }
-  }
-  if (ty > 0) {
-#pragma unroll
-    for (int r = 0; r < MT; ++r) part[ty - 1][r][tx] = acc[r];
-  }
-  __syncthreads();
-  if (ty == 0 && n < N) {
-    const float sc = (float)rows.scale;
-#pragma unroll
-    for (int r = 0; r < MT; ++r) {
-      if (r >= nr) break;
-      float2 y = acc[r];
-#pragma unroll
-      for (int t = 0; t < kToepSplit - 1; ++t) {
-        y.x += part[t][r][tx].x;
-        y.y += part[t][r][tx].y;
-      }
-      float2* d = half + rowmap_out(rows, i0 + r) * N + n;
-      if (rows.accumulate) {
-        y.x += d->x;
-        y.y += d->y;
-        if (rows.scale != 1.0) {
-          y.x *= sc;
-          y.y *= sc;
-        }
-      }
-      *d = y;
-    }
-  }
-}
-
-hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
-                                cudaStream_t st) {
-  const int N = 1 << n_s;
-  const int mt = m >= 16 ? 16 : (int)m;  // m is a power of two here
-  dim3 grid((unsigned)((N + kToepCols - 1) / kToepCols), (unsigned)((m + mt - 1) / mt));
-  HHL_PROF_BEGIN(st);
-  switch (mt) {
-    case 1: k_toeplitz_rows<1><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 2: k_toeplitz_rows<2><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 4: k_toeplitz_rows<4><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 8: k_toeplitz_rows<8><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    default: k_toeplitz_rows<16><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-  }
-  HHL_LAUNCH_CHECK("k_toeplitz_rows");
-  return HHL_OK;
 }
 
 struct Work {

@@ -224,6 +224,15 @@ inline RowMap circuit_rows(int k) {
   return m;
 }
 
+// U_k[n][m] = g(|n-m|) - g(n+m+2) (0-based n, m; a Toeplitz tridiagonal A's exp(i Ahat t_k)
+// from its analytic sine basis) from the double-float table g (hi re, lo re, hi im, lo im), in
+// FP32: the difference of the high parts is exact for close values and the low parts restore
+// the rest.
+__device__ __forceinline__ float2 toeplitz_u(const float4* __restrict__ g, int n, int m) {
+  const float4 a = g[n > m ? n - m : m - n], b = g[n + m + 2];
+  return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
+}
+
 // ------------------------------------------------------------------ the plan
 // One Trotter pass: clock bits [kb, kb + gbits) (single_k >= 0: the one bit single_k, rows
 // with that bit set) and the offset of its per-row-pattern layer lists in the plan's table.
@@ -252,6 +261,7 @@ struct Plan {
   double* d_b = nullptr;      // N complex128: host-prepared b
   void* d_bs = nullptr;       // N amplitudes: b / (|b| 2^(n_c/2)), one anc = 0 row
   void* d_scratch = nullptr;  // GEMM output rows: 2^(n_c-1) * N amplitudes
+  float4* d_gdf = nullptr;    // Toeplitz A, complex64: per k the 2N+2 double-float g_k values
   // Trotter (Toeplitz tridiagonal): per k the step count and the 2x2 blocks
   std::vector<int> trot_r;
   std::vector<double> trot_blocks;  // per k: E(tau/2), E(tau), O(tau): 3 x 8 doubles
@@ -327,6 +337,12 @@ hhl_status launch_trotter_tree(const Plan& p, void* half, bool reduce, cudaStrea
 // basis: d_c / d_s = cos / sin(lambdahat_j t), d_ctab[q] = cos(q pi/(N+1)), q < 2N+2.
 hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, const double* d_ctab, double2* d_g,
                                 double2* d_u, cudaStream_t st);
+// g (FP64, 2N+2) -> its double-float copy gdf.
+hhl_status launch_g_to_df(int N, const double2* d_g, float4* gdf, cudaStream_t st);
+// The controlled product on m rows mapped by `rows` with U_k (or U_k^dagger, adjoint) generated
+// on the fly from its double-float g table (complex64; the small steps of the trees).
+hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
+                                cudaStream_t st);
 // Plan time: group the clock bits into passes, fill p.trot_pass and the layer-list table
 // (bytes, to be uploaded to p.d_trot_lists); returns the number of lists.
 size_t trotter_build_passes(Plan& p, std::vector<unsigned char>* table);

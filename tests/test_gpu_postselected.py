@@ -182,6 +182,27 @@ def test_postselected_dense_matches_oracle(hhl, prec, gemm, flow, n_s, n_c):
     assert got["eps"] == pytest.approx(o.dissipation(u_ref, walls[0], walls[1], nu), rel=1e-9 if prec == "c128" else 1e-3)
 
 
+@pytest.mark.parametrize("gemm", ["tcgen05", "simt"])
+def test_postselected_dense_general_matrix(hhl, gemm):
+    """A dense symmetric A that is not Toeplitz (U_k from its Jacobi eigenvectors; the small
+    tree steps then multiply stored CUDA-core operands) against the oracle's whole circuit."""
+    n_s, n_c = 7, 8
+    N = 1 << n_s
+    rng = np.random.default_rng(29)
+    q = np.linalg.qr(rng.standard_normal((N, N)))[0]
+    a = q @ np.diag(rng.uniform(1.0, 9.0, N)) @ q.T
+    a = 0.5 * (a + a.T)
+    b = rng.random(N)
+    pl = o.plan(a, n_c, t0_rule="range_fill")
+    psi = run_stages(b, n_s, pl)["final_h"]
+    post = o.postselect(psi, n_s, n_c)
+    plan = hhl.HHLPlan(n_s, n_c, dense=a, precision="c64", gemm=gemm)
+    got = _postselected(hhl, plan, b, n_s, n_c)
+    dv = np.abs(got["v"] - psi.reshape(2, 1 << n_c, N)[1, 0]).max()
+    assert dv <= TOL["c64"], dv
+    assert got["p_success"] == pytest.approx(post["p_success"], rel=1e-4)
+
+
 def test_postselected_dense_refuses_full_uncompute(hhl):
     import torch
     diag, off, b, walls = problem("poiseuille", 4)
