@@ -122,6 +122,7 @@ struct Work {
   __half* a_hi = nullptr;  // tc split rows (M_sub x 2N FP16)
   __half* a_lo = nullptr;
   void* scratch = nullptr; // simt GEMM output rows (M_sub x N complex64)
+  TcWork tcw;              // none: the batch's GEMMs run one CTA per tile (no split tiles)
 };
 
 int gemm_rule(int n_s, int n_c) {
@@ -222,7 +223,7 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
     if (reduce && k == 0) rows.scale = 1.0 / sqrt((double)p.R);
     void* half = reduce ? (void*)s1 : (void*)s0;
     const int g = (int)std::min<int64_t>((p.N * p.N + 255) / 256, 152 * 16);
-    if (m < 128)  // few rows: U_k generated on the fly, no N x N operand
+    if (m < toeplitz_rows_limit())  // few rows: U_k generated on the fly, no N x N operand
       return launch_toeplitz_rows((float2*)half, p.n_s, gk, reduce ? 1 : 0, rows, m, st);
     if (B->gemm[i] == 0 || rows.scale != 1.0) {
       HHL_PROF_BEGIN(st);
@@ -236,7 +237,7 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
     k_ugen_embed_tc<<<g, 256, 0, st>>>(p.n_s, gk, reduce ? 1 : 0, hi, lo);
     HHL_LAUNCH_CHECK("k_ugen_embed_tc");
     const CUtensorMap* mp = &B->maps[(size_t)i * 4];
-    return launch_tc_gemm_map(p.n_s, m, rows, half, w.a_hi, w.a_lo, mp[0], mp[1], mp[2], mp[3], B->gemm[i], B->d_err,
+    return launch_tc_gemm_map(p.n_s, m, rows, half, w.a_hi, w.a_lo, mp[0], mp[1], mp[2], mp[3], B->gemm[i], B->d_err, w.tcw, 0,
                               st);
   };
   for (int k = 0; k < p.n_c && s == HHL_OK; ++k) s = step(k, false);

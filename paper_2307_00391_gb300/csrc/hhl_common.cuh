@@ -341,6 +341,7 @@ hhl_status launch_toeplitz_expm(int N, const double* d_c, const double* d_s, con
 hhl_status launch_g_to_df(int N, const double2* d_g, float4* gdf, cudaStream_t st);
 // The controlled product on m rows mapped by `rows` with U_k (or U_k^dagger, adjoint) generated
 // on the fly from its double-float g table (complex64; the small steps of the trees).
+int64_t toeplitz_rows_limit();
 hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
                                 cudaStream_t st);
 // Plan time: group the clock bits into passes, fill p.trot_pass and the layer-list table
@@ -363,17 +364,24 @@ hhl_status tc_flag_status(int flag);
 }  // namespace hhl
 #include <cuda.h>
 namespace hhl {
-// The split-FP16 tcgen05 GEMM with explicit operands (row gather + GEMM of one controlled
-// product): bn = 128 or 256 output real columns per CTA; the maps describe the FP16 a_hi /
-// a_lo (M_sub x 2N) and the embedded operand hi / lo (2N x 2N, both scaled by 2^15) with
-// boxes (64 x 128) and (64 x bn).
-hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo,
-                          const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
-                          const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
-// The same on m_sub (a multiple of 128) rows mapped by `rows`.
+// Workspace of the stream-K tcgen05 GEMM: two partial 128 x 256 FP32 tiles per CTA of the
+// largest grid (one CTA per SM). One per stream that runs GEMMs: a launch and its fixup use it.
+struct TcWork {
+  float* ws = nullptr;
+  int grid_cap = 0;        // CTAs of the largest grid
+};
+int tc_num_sms();
+hhl_status tc_work_alloc(TcWork& w, size_t* bytes);
+void tc_work_free(TcWork& w);
+// The split-FP16 tcgen05 GEMM with explicit operands (row gather + stream-K GEMM of one
+// controlled product) on m_sub (a multiple of 128) rows mapped by `rows`: bn = 128 or 256
+// output real columns per tile; the maps describe the FP16 a_hi / a_lo (M_sub x 2N) and the
+// embedded operand hi / lo (2N x 2N, both scaled by 2^15) with boxes (64 x 128) and (64 x bn).
+// streamk = 0: one CTA per output tile; 1: stream-K over the SMs when the tiles are few.
 hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& rows, void* half, void* a_hi, void* a_lo,
                               const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
-                              const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st);
+                              const CUtensorMap& map_blo, int bn, int* err, const TcWork& w, int streamk,
+                              cudaStream_t st);
 // The plan's tcgen05 product on mapped rows (m_sub a multiple of 128).
 hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, int64_t m_sub, int k, bool adjoint,
                                 cudaStream_t st);

@@ -21,15 +21,30 @@
 // the rows with bit k set into compact X_hi / X_lo arrays, so the GEMM may write its result
 // straight back into those state rows.
 //
-// Kernel: one CTA of 128 threads per 128 x BN output tile. Warp 0 (one lane) issues TMA
-// loads (128-byte swizzle) into a 2-stage shared-memory ring, warp 1 (one lane) issues the
-// MMAs (M = 128, N = BN, K = 16) into a BN-column TMEM accumulator, and all four warps
-// drain TMEM with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. output rows) and
-// store the rows. Every mbarrier wait is bounded (wait_cycles, a kernel argument); on expiry
-// the CTA records an error flag (read back as HHL_ERR_TIMEOUT) and skips the remaining work,
-// but before it frees its TMEM and exits it drains what it started: the producer waits
-// (bounded) for every bulk copy it issued to land, and the MMA lane always commits its issued
-// MMAs to the final barrier, which the whole CTA waits on (bounded) before the dealloc.
+// Kernel (persistent, stream-K): the work is the list of (output tile, K step) units, tile-major,
+// 128 x BN tiles of K / 64 steps each; the grid has one CTA per SM (fewer when there are few
+// units, every CTA keeping at least a quarter of a tile's steps) and CTA b takes the contiguous
+// units [b U / G, (b + 1) U / G), so every SM does the same number of MMAs whatever the number
+// of rows (a 128-row product no longer runs on 8 SMs only). When the tiles alone fill most of
+// the SMs the grid is one CTA per tile instead (each range is one whole tile): the large
+// products are bound by the operand stream from L2, which a finer split does not shorten, and
+// the split tiles' partials would cost a second pass. Its range is a sequence of tile
+// segments. Roles: warp 0 (one lane) issues the TMA loads (128-byte swizzle) into a ring of
+// shared-memory stages, across segment boundaries; warp 1 (one lane) issues the MMAs
+// (M = 128, N = BN, K = 16) into one of two BN-column TMEM accumulators, alternating per
+// segment, so that the epilogue of one segment overlaps the MMAs of the next; warps 2-5 drain
+// TMEM with tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. output rows). A
+// segment that covers its whole tile is written straight to the state rows. A tile split over
+// several CTAs needs no wait between CTAs: each contributor stores its FP32 partial in a
+// workspace slot of its own (two per CTA: its range's first and last segment), and a second
+// launch on the same stream, k_tc_fixup, adds each split tile's partials in the order of the
+// CTAs (the same sum on every run) and writes the rows. Every mbarrier wait is
+// bounded (wait_cycles, a kernel argument) and gives up early once another role has given up;
+// on expiry the CTA records an error flag (read back as HHL_ERR_TIMEOUT) and skips the
+// remaining work, but before it frees its TMEM and exits it drains what it started: the
+// producer waits (bounded) for every bulk copy it issued to land, and the MMA lane always
+// commits its issued MMAs to the final barrier, which the whole CTA waits on (bounded) before
+// the dealloc (and k_tc_fixup does nothing once the flag is set).
 // Fault injection for the error path (fault = 1): the producer issues no copy at all, so the
 // MMA lane's first wait runs out with nothing in flight.
 #include <cuda.h>
@@ -47,15 +62,16 @@ namespace {
 constexpr int kBM = 128;           // output rows per CTA (MMA M)
 constexpr int kBN = 256;           // output real columns per CTA (MMA N), plan path
 constexpr int kBK = 64;            // fp16 K elements per stage (128 bytes: one swizzle row)
-constexpr int kStages = 2;
 constexpr int kTileA = kBM * kBK * 2;   // 16 KiB
+constexpr int kThreadsTc = 192;    // producer warp, MMA warp, four epilogue warps
 constexpr float kOpScale = 32768.0f;    // 2^15 on each operand
 constexpr float kUnscale = 1.0f / (32768.0f * 32768.0f);  // 2^-30 on the product
 template <int BN> struct TcShape {
   static constexpr int kTileB = BN * kBK * 2;                     // 32 KiB at BN = 256
   static constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;     // A_hi, A_lo, B_hi, B_lo
+  static constexpr int kStages = BN == 256 ? 2 : 3;               // 192 KiB of stages either way
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
-  static constexpr int kTmemCols = BN;                            // fp32 accumulator columns
+  static constexpr int kTmemCols = 2 * BN;                        // two fp32 accumulators
 };
 constexpr long long kWaitCycles = 4000000000LL;      // default bound of a wait: ~2 s at 2 GHz
 constexpr long long kFaultWaitCycles = 2000000LL;    // injected timeout: ~1 ms
@@ -65,6 +81,7 @@ struct TcState {
   __half* a_lo = nullptr;
   __half* b = nullptr;     // n_c x {fwd_hi, fwd_lo, adj_hi, adj_lo} x (2N x 2N)
   int* err = nullptr;      // device error flag
+  TcWork work;             // stream-K partials and tile counters
   int bn = kBN;           // output tile width (128 or 256)
   std::vector<CUtensorMap> maps;  // [0] A_hi, [1] A_lo, then per k: fwd_hi, fwd_lo, adj_hi, adj_lo
 };
@@ -102,6 +119,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
   }
   return true;
+}
+
+// The same, also giving up (without a flag of its own) once another role of the CTA has set
+// *abort; on its own expiry it sets *abort.
+__device__ __forceinline__ bool mbar_wait_role(uint64_t* bar, uint32_t parity, int* err, int code, long long limit,
+                                               volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > limit) {
+      atomicExch(err, code);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier 1 over the four epilogue warps (128 threads).
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Stream-K partition: CTA b of G takes units [b U / G, (b + 1) U / G); the CTA holding unit x.
+__device__ __forceinline__ int64_t sk_start(int64_t b, int64_t units, int64_t G) { return b * units / G; }
+__device__ __forceinline__ int64_t sk_owner(int64_t x, int64_t units, int64_t G) { return ((x + 1) * G - 1) / units; }
+// End (exclusive K step) of the segment that starts at step kb of a tile with `left` units left.
+__device__ __forceinline__ int seg_end(int kb, int k_iters, int64_t left) {
+  return left < (int64_t)(k_iters - kb) ? kb + (int)left : k_iters;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -164,29 +212,38 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
 
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreadsTc, 1)
     k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                    const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-                   float* __restrict__ state_half, int n_s, RowMap rows, int k_iters, int* err, long long wait_cycles,
-                   int fault) {
+                   float* __restrict__ state_half, int n_s, RowMap rows, int k_iters, int tiles_n, int64_t units,
+                   float* __restrict__ ws, int* err, long long wait_cycles, int fault) {
+  constexpr int S = TcShape<BN>::kStages;
+  constexpr int kTileB = TcShape<BN>::kTileB, kStageBytes = TcShape<BN>::kStageBytes;
+  constexpr int kTmemCols = TcShape<BN>::kTmemCols;
+  constexpr int kPart = kBM * BN;  // floats of one partial tile
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages];
-  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ volatile int abort_flag;
+  __shared__ int s_go[2];  // by segment parity: rewritten only two barriers later
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  constexpr int kTileB = TcShape<BN>::kTileB, kStageBytes = TcShape<BN>::kStageBytes;
-  constexpr int kTmemCols = TcShape<BN>::kTmemCols;
-  const int n0 = blockIdx.x * BN;   // real output column
-  const int m0 = blockIdx.y * kBM;   // subset row
+  const int64_t G = gridDim.x, cta = blockIdx.x;
+  const int64_t u_begin = sk_start(cta, units, G), u_end = sk_start(cta + 1, units, G);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&tfull_bar[s], 1);
+      mbar_init(&tempty_bar[s], 128);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -203,90 +260,177 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // producer: TMA loads of the four operand tiles of each K step
-    int issued = 0;
-    for (int it = 0; it < (fault ? 0 : k_iters); ++it) {
-      const int s = it % kStages;
-      if (!mbar_wait_bounded(&empty_bar[s], ((it / kStages) & 1) ^ 1, err, 1, wait_cycles)) {
-        abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA loads of the four operand tiles of each K step, segment after segment
+      int64_t gi = 0, issued = 0;
+      for (int64_t u = u_begin; u < u_end && !fault && !abort_flag;) {
+        const int64_t t = u / k_iters;
+        const int kb = (int)(u - t * k_iters);
+        const int ke = seg_end(kb, k_iters, u_end - u);
+        const int m0 = (int)(t / tiles_n) * kBM, n0 = (int)(t % tiles_n) * BN;
+        for (int it = kb; it < ke; ++it, ++gi) {
+          const int s = (int)(gi % S);
+          if (!mbar_wait_role(&empty_bar[s], (uint32_t)((gi / S) & 1) ^ 1u, err, 1, wait_cycles, &abort_flag)) break;
+          const uint32_t st = base + s * kStageBytes;
+          mbar_expect_tx(&full_bar[s], kStageBytes);
+          const int kx = it * kBK;
+          tma_load_2d(st, &map_ahi, &full_bar[s], kx, m0);
+          tma_load_2d(st + kTileA, &map_alo, &full_bar[s], kx, m0);
+          tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
+          tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
+          issued = gi + 1;
+        }
+        u += ke - kb;
       }
-      const uint32_t st = base + s * kStageBytes;
-      mbar_expect_tx(&full_bar[s], kStageBytes);
-      const int kx = it * kBK;
-      tma_load_2d(st, &map_ahi, &full_bar[s], kx, m0);
-      tma_load_2d(st + kTileA, &map_alo, &full_bar[s], kx, m0);
-      tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
-      tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
-      issued = it + 1;
+      // drain: the last copy issued into each stage has landed before shared memory is released
+      // (on the normal path the MMA lane has already consumed them, so these return at once)
+      for (int64_t g2 = issued > S ? issued - S : 0; g2 < issued; ++g2)
+        mbar_wait_bounded(&full_bar[g2 % S], (uint32_t)((g2 / S) & 1), err, 5, wait_cycles);
     }
-    // drain: the last copy issued into each stage has landed before shared memory is released
-    // (on the normal path the MMA lane has already consumed them, so these return at once)
-    for (int it = issued > kStages ? issued - kStages : 0; it < issued; ++it)
-      mbar_wait_bounded(&full_bar[it % kStages], (it / kStages) & 1, err, 5, wait_cycles);
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = idesc_f16(kBM, BN);
-    bool ok = true;
-    for (int it = 0; it < k_iters; ++it) {
-      const int s = it % kStages;
-      if (!mbar_wait_bounded(&full_bar[s], (it / kStages) & 1, err, 2, wait_cycles)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = base + s * kStageBytes;
-      const uint32_t a_hi = st, a_lo = st + kTileA, b_hi = st + 2 * kTileA, b_lo = st + 2 * kTileA + kTileB;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: one accumulator per segment, alternating between the two
+      constexpr uint32_t idesc = idesc_f16(kBM, BN);
+      int64_t gi = 0;
+      int j = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++j) {
+        const int64_t t = u / k_iters;
+        const int kb = (int)(u - t * k_iters);
+        const int ke = seg_end(kb, k_iters, u_end - u);
+        const int buf = j & 1;
+        // the epilogue has read this accumulator's previous segment (free at first use)
+        if (!mbar_wait_role(&tempty_bar[buf], (uint32_t)((j >> 1) & 1) ^ 1u, err, 3, wait_cycles, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        for (int it = kb; it < ke; ++it, ++gi) {
+          const int s = (int)(gi % S);
+          if (!mbar_wait_role(&full_bar[s], (uint32_t)((gi / S) & 1), err, 2, wait_cycles, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * kStageBytes;
+          const uint32_t a_hi = st, a_lo = st + kTileA, b_hi = st + 2 * kTileA, b_lo = st + 2 * kTileA + kTileB;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint32_t off = kk * 32;  // 16 fp16 = 32 bytes along K inside the swizzled row
-        const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
-        mma_f16(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
-        mma_f16(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
-        mma_f16(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t off = kk * 32;  // 16 fp16 = 32 bytes along K inside the swizzled row
+            const uint32_t acc0 = (it > kb || kk > 0) ? 1u : 0u;
+            mma_f16(d, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
+            mma_f16(d, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+            mma_f16(d, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+          }
+          mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+        }
+        if (!ok) break;
+        mma_commit(&tfull_bar[buf]);  // the segment's accumulator is complete
+        u += ke - kb;
       }
-      mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+      // always commit: done_bar completes once every MMA this lane issued has finished (at once
+      // when none was), so the wait below also drains an aborted accumulation before the dealloc
+      mma_commit(&done_bar);
     }
-    // always commit: done_bar completes once every MMA this lane issued has finished (at once
-    // when none was), so the wait below also drains an aborted accumulation before the dealloc
-    mma_commit(&done_bar);
-    if (!ok) abort_flag = 1;
+  } else {
+    // epilogue: warps 2-5, thread row = its TMEM lane
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const bool leader = threadIdx.x == 64;
+    const int64_t N2 = 2LL << n_s;  // floats per state row
+    int j = 0;
+    for (int64_t u = u_begin; u < u_end; ++j) {
+      const int64_t t = u / k_iters;
+      const int kb = (int)(u - t * k_iters);
+      const int ke = seg_end(kb, k_iters, u_end - u);
+      const int buf = j & 1;
+      if (leader) s_go[j & 1] = mbar_wait_role(&tfull_bar[buf], (uint32_t)((j >> 1) & 1), err, 3, wait_cycles, &abort_flag);
+      epilogue_sync();
+      if (!s_go[j & 1]) break;  // uniform: read after the barrier
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+      const int m0 = (int)(t / tiles_n) * kBM, n0 = (int)(t % tiles_n) * BN;
+      float* dst = state_half + rowmap_out(rows, m0 + row) * N2 + n0;
+      if (kb == 0 && ke == k_iters) {
+        // the whole tile is this CTA's: straight to the state row
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          float v[32];
+          tmem_ld_32cols(taddr + c, v);
+          float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float4 o = make_float4(v[4 * e] * kUnscale, v[4 * e + 1] * kUnscale, v[4 * e + 2] * kUnscale,
+                                   v[4 * e + 3] * kUnscale);
+            if (rows.accumulate) {  // a reduction step of the postselected solve: the row keeps its value
+              const float4 prev = d4[e];
+              o = make_float4(prev.x + o.x, prev.y + o.y, prev.z + o.z, prev.w + o.w);
+            }
+            d4[e] = o;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&tempty_bar[buf]);
+      } else {
+        // a split tile: this CTA's FP32 partial goes to its slot (row-major 128 x BN; slot 0 when
+        // the segment starts the CTA's range inside the tile, else slot 1), added up by
+        // k_tc_fixup after the launch
+        float* wp = ws + (size_t)(2 * cta + (u_begin > t * k_iters ? 0 : 1)) * kPart + (size_t)row * BN;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          float v[32];
+          tmem_ld_32cols(taddr + c, v);
+          float4* w4 = reinterpret_cast<float4*>(wp + c);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) __stcg(w4 + e, make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&tempty_bar[buf]);  // the accumulator is free for the segment after next
+      }
+      u += ke - kb;
+    }
   }
   __syncwarp();
-  __syncthreads();  // the producer and MMA lanes have left their (bounded) loops
+  __syncthreads();  // every role has left its (bounded) loop
 
-  // epilogue: all four warps drain their 32 TMEM lanes (= output rows)
   if (!mbar_wait_bounded(&done_bar, 0, err, 3, wait_cycles)) abort_flag = 1;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (abort_flag == 0) {  // uniform across the CTA: tcgen05.ld is warp-collective
-    const int64_t N2 = 2LL << n_s;  // floats per state row
-    const int64_t i = m0 + warp * 32 + lane;
-    float* dst = state_half + rowmap_out(rows, i) * N2 + n0;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-      float v[32];
-      tmem_ld_32cols(lane_addr + c, v);
-      float4* d4 = reinterpret_cast<float4*>(dst + c);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 o = make_float4(v[4 * q] * kUnscale, v[4 * q + 1] * kUnscale, v[4 * q + 2] * kUnscale,
-                               v[4 * q + 3] * kUnscale);
-        if (rows.accumulate) {  // a reduction step of the postselected solve: the row keeps its value
-          const float4 prev = d4[q];
-          o = make_float4(prev.x + o.x, prev.y + o.y, prev.z + o.z, prev.w + o.w);
-        }
-        d4[q] = o;
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+}
+
+// The tiles the stream-K GEMM split over several CTAs: one thread per 4 output columns adds
+// the contributors' partials in CTA order (the same sum on every run), scales by 2^-30 and
+// writes (or adds to) the state row. Tiles held whole by one CTA were written by the GEMM.
+template <int BN>
+__global__ void __launch_bounds__(256) k_tc_fixup(const float4* __restrict__ ws, float* __restrict__ state_half,
+                                                  int n_s, RowMap rows, int k_iters, int tiles_n, int64_t units,
+                                                  int64_t G, int* err) {
+  constexpr int kQ = BN / 4;  // float4 per tile row
+  const int64_t t = blockIdx.y;
+  const int64_t t0u = t * k_iters;
+  const int64_t first = ((t0u + 1) * G - 1) / units, last = ((t0u + k_iters) * G - 1) / units;
+  if (first == last || *err != 0) return;  // whole tile, or the GEMM gave up
+  const int e = blockIdx.x * 256 + threadIdx.x;  // < 128 * kQ by the grid
+  const int row = e / kQ, q = e % kQ;
+  float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t b = first; b <= last; ++b) {
+    const int64_t slot = 2 * b + (b * units / G > t0u ? 0 : 1);
+    const float4 v = __ldcg(ws + slot * (kBM * kQ) + (int64_t)row * kQ + q);
+    o = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+  }
+  const int m0 = (int)(t / tiles_n) * kBM, n0 = (int)(t % tiles_n) * BN;
+  float4* d4 = reinterpret_cast<float4*>(state_half + rowmap_out(rows, m0 + row) * (2LL << n_s) + n0) + q;
+  o = make_float4(o.x * kUnscale, o.y * kUnscale, o.z * kUnscale, o.w * kUnscale);
+  if (rows.accumulate) {
+    const float4 prev = *d4;
+    o = make_float4(prev.x + o.x, prev.y + o.y, prev.z + o.z, prev.w + o.w);
+  }
+  *d4 = o;
 }
 
 // The mapped rows (those with clock bit k set, or a tree step's source rows) -> compact FP16
@@ -404,6 +548,8 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
       cudaGetLastError();
       return fail(HHL_ERR_OOM, "tcgen05 operand allocation failed");
     }
+    hhl_status ws = tc_work_alloc(t->work, &p.workspace_bytes);
+    if (ws != HHL_OK) return ws;
     p.workspace_bytes += 2 * abytes;
     p.table_bytes += (size_t)p.n_c * 4 * mat * sizeof(__half);
     HHL_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), st));
@@ -438,21 +584,44 @@ hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, i
   if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
   const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
   return launch_tc_gemm_map(p.n_s, m_sub, rows, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn,
-                            t->err, st);
+                            t->err, t->work, 1, st);
 }
 
-hhl_status launch_tc_gemm(int n_s, int64_t m_sub, int k, void* half, void* a_hi, void* a_lo, const CUtensorMap& map_ahi,
-                          const CUtensorMap& map_alo, const CUtensorMap& map_bhi, const CUtensorMap& map_blo, int bn,
-                          int* err, cudaStream_t st) {
-  return launch_tc_gemm_map(n_s, m_sub, circuit_rows(k), half, a_hi, a_lo, map_ahi, map_alo, map_bhi, map_blo, bn, err,
-                            st);
+int tc_num_sms() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 152;
+    return v > 0 ? v : 152;
+  }();
+  return n;
+}
+
+hhl_status tc_work_alloc(TcWork& w, size_t* bytes) {
+  w.grid_cap = tc_num_sms();
+  const size_t wsb = (size_t)2 * w.grid_cap * kBM * kBN * sizeof(float);  // two partial tiles per CTA
+  if (cudaMalloc(&w.ws, wsb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HHL_ERR_OOM, "tcgen05 stream-K workspace allocation failed");
+  }
+  if (bytes) *bytes += wsb;
+  return HHL_OK;
+}
+
+void tc_work_free(TcWork& w) {
+  if (w.ws) cudaFree(w.ws);
+  w.ws = nullptr;
 }
 
 hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* half, void* a_hi, void* a_lo,
                               const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
-                              const CUtensorMap& map_blo, int bn, int* err, cudaStream_t st) {
+                              const CUtensorMap& map_blo, int bn, int* err, const TcWork& w, int streamk,
+                              cudaStream_t st) {
   const int64_t N2 = 2LL << n_s;
   if (m_sub < kBM || m_sub % kBM != 0) return fail(HHL_ERR_INVALID_ARG, "tcgen05 GEMM rows must be a multiple of 128");
+  if (bn != 128 && bn != 256) return fail(HHL_ERR_INVALID_ARG, "tcgen05 tile width must be 128 or 256");
+  const int64_t tiles_n = N2 / bn, tiles = (m_sub / kBM) * tiles_n;
+  if (streamk && w.ws == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 stream-K workspace missing");
   // HHL_FAULT=tc_wait (testing the timeout path): no operand copy is issued and every wait is
   // bounded by about a millisecond, so the MMA lane's first wait runs out with nothing in flight
   const char* fenv = getenv("HHL_FAULT");
@@ -464,20 +633,41 @@ hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* hal
   HHL_PROF_BEGIN(st);
   k_tc_split_rows<<<g, 256, 0, st>>>((const float4*)half, (uint2*)a_hi, (uint2*)a_lo, n_s, k, m_sub, err);
   HHL_LAUNCH_CHECK("k_tc_split_rows");
-  if (bn == 256) {
-    dim3 grid((unsigned)(N2 / 256), (unsigned)(m_sub / kBM));
-    HHL_PROF_BEGIN(st);
-    k_ctrl_gemm_tc<256><<<grid, 128, TcShape<256>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
-                                                                     n_s, k, (int)(N2 / kBK), err, wait_cycles,
-                                                                     fault);
-  } else {
-    dim3 grid((unsigned)(N2 / 128), (unsigned)(m_sub / kBM));
-    HHL_PROF_BEGIN(st);
-    k_ctrl_gemm_tc<128><<<grid, 128, TcShape<128>::kSmemBytes, st>>>(map_ahi, map_alo, map_bhi, map_blo, (float*)half,
-                                                                     n_s, k, (int)(N2 / kBK), err, wait_cycles,
-                                                                     fault);
+  // grid: one CTA per tile when the tiles fill at least three quarters of the SMs (or the
+  // caller asks for it: the batch, whose streams fill the GPU together); otherwise stream-K,
+  // one CTA per SM, fewer when a CTA would get under a quarter of a tile
+  const int k_iters = (int)(N2 / kBK);
+  const int64_t units = tiles * k_iters;
+  int64_t G = tiles;
+  if (streamk && 4 * tiles < 3 * (int64_t)w.grid_cap) {
+    const int64_t min_units = k_iters >= 4 ? k_iters / 4 : 1;
+    G = units / min_units;
+    if (G < 1) G = 1;
+    if (G > w.grid_cap) G = w.grid_cap;
   }
+  HHL_PROF_BEGIN(st);
+  if (bn == 256)
+    k_ctrl_gemm_tc<256><<<(unsigned)G, kThreadsTc, TcShape<256>::kSmemBytes, st>>>(
+        map_ahi, map_alo, map_bhi, map_blo, (float*)half, n_s, k, k_iters, (int)tiles_n, units, w.ws, err,
+        wait_cycles, fault);
+  else
+    k_ctrl_gemm_tc<128><<<(unsigned)G, kThreadsTc, TcShape<128>::kSmemBytes, st>>>(
+        map_ahi, map_alo, map_bhi, map_blo, (float*)half, n_s, k, k_iters, (int)tiles_n, units, w.ws, err,
+        wait_cycles, fault);
   HHL_LAUNCH_CHECK("k_ctrl_gemm_tc");
+  // the split tiles, if any (a range boundary inside a tile): partials added in CTA order
+  bool split = false;
+  for (int64_t b = 1; b < G && !split; ++b) split = (b * units / G) % k_iters != 0;
+  if (!split) return HHL_OK;
+  const dim3 fgrid((unsigned)(kBM * (bn / 4) / 256), (unsigned)tiles);
+  HHL_PROF_BEGIN(st);
+  if (bn == 256)
+    k_tc_fixup<256><<<fgrid, 256, 0, st>>>((const float4*)w.ws, (float*)half, n_s, k, k_iters, (int)tiles_n, units, G,
+                                           err);
+  else
+    k_tc_fixup<128><<<fgrid, 256, 0, st>>>((const float4*)w.ws, (float*)half, n_s, k, k_iters, (int)tiles_n, units, G,
+                                           err);
+  HHL_LAUNCH_CHECK("k_tc_fixup");
   return HHL_OK;
 }
 
@@ -521,6 +711,7 @@ void tc_free(Plan& p) {
   if (t->a_lo) cudaFree(t->a_lo);
   if (t->b) cudaFree(t->b);
   if (t->err) cudaFree(t->err);
+  tc_work_free(t->work);
   delete t;
   p.d_tc = nullptr;
 }

@@ -605,9 +605,11 @@ hhl_status launch_ctrl_u_tree(const Plan& p, void* half, int k, bool reduce, cud
     rows.in_off = 0;
     rows.out_off = m;
   }
+  if (p.d_gdf != nullptr && m < toeplitz_rows_limit())  // few rows: U_k generated on the fly from its g table
+    return launch_toeplitz_rows((float2*)half, p.n_s, p.d_gdf + (size_t)k * (2 * p.N + 2), reduce ? 1 : 0, rows, m, st);
   if (p.gemm_impl == HHL_GEMM_TCGEN05 && m >= 128 && rows.scale == 1.0)
     return launch_ctrl_u_tc_map(p, half, rows, m, k, reduce, st);
-  if (p.d_gdf != nullptr && m < 128)  // few rows: U_k generated on the fly from its g table
+  if (p.d_gdf != nullptr && m < 128)
     return launch_toeplitz_rows((float2*)half, p.n_s, p.d_gdf + (size_t)k * (2 * p.N + 2), reduce ? 1 : 0, rows, m, st);
   if (p.d_bfwd == nullptr) {  // a tcgen05 plan keeps no CUDA-core operands
     return fail(HHL_ERR_UNSUPPORTED, "tree step below 128 rows on a tcgen05-only plan");
@@ -919,71 +921,120 @@ hhl_status launch_g_to_df(int N, const double2* d_g, float4* gdf, cudaStream_t s
 
 // A controlled product on few rows (the small steps of the postselected solve's trees, 2^k < 128
 // rows): y[i][n] = sum_m U'[n][m] x[i][m] with U' = U_k or U_k^dagger = conj(U_k) generated on
-// the fly from the double-float g table (u_elem), so no N x N operand is written or read. A
-// block owns 32 output columns of MT rows (MT = min(16, rows of the step)); its 256 threads
-// split the sum over m in eight parts (32 columns x 8), the x rows staged in shared memory in
-// chunks of 128 columns, the parts added in shared memory at the end. Output rows are mapped as
-// the GEMMs' (write, or add to the row and scale).
-constexpr int kToepCols = 32, kToepSplit = 8, kToepChunk = 128;
+// the fly from the double-float g table (U[n][m] = g(|n - m|) - g(n + m + 2)), so no N x N
+// operand is written or read. A block owns TN output columns n of MT rows (MT = min(16, rows
+// of the step); TN = 8, 16 or 32, the largest that still gives two blocks per SM) and splits
+// the sum over m in 256 / TN parts: thread t takes n = n0 + t % TN and every (256 / TN)-th
+// column of each chunk of 256 columns. Per chunk the block stages the x rows and the g entries
+// the chunk needs (its TN + 255 differences n - m and sums n + m + 2) in shared memory, the
+// loads of a thread issued together; the parts of each output are added by shuffles inside the
+// warp, then across the 8 warps in shared memory (reusing the x buffer). Output rows are mapped
+// as the GEMMs' (write, or add to the row and scale).
+constexpr int kToepChunk = 256;
 
-template <int MT>
+// Tree steps on fewer rows than this take the on-the-fly Toeplitz product instead of a GEMM
+// (128 by default: the tensor-core tiles start at 128 rows); HHL_TOEP_ROWS=<power of two>
+// moves the threshold.
+int64_t toeplitz_rows_limit() {
+  static const int64_t lim = [] {
+    const char* e = getenv("HHL_TOEP_ROWS");
+    const long long v = e != nullptr ? atoll(e) : 0;
+    return v >= 1 ? (int64_t)v : (int64_t)128;
+  }();
+  return lim;
+}
+
+template <int MT, int TN>
 __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half, int n_s, const float4* __restrict__ g,
                                                        int adjoint, RowMap rows, int64_t m_rows) {
-  __shared__ float2 xs[MT][kToepChunk];
-  __shared__ float2 part[kToepSplit - 1][MT][kToepCols];
+  constexpr int P = 256 / TN;                      // parts of each output
+  constexpr int kXs = MT * kToepChunk;             // staged x values per chunk
+  constexpr int kLd = (kXs + 255) / 256;           // x loads per thread per chunk
+  static_assert(8 * MT * TN <= kXs, "partials reuse the x buffer");
+  __shared__ float2 xs[kXs];
+  __shared__ float4 gd[TN + kToepChunk], gs[TN + kToepChunk];
   const int N = 1 << n_s;
-  const int tx = threadIdx.x % kToepCols, ty = threadIdx.x / kToepCols;
-  const int n = blockIdx.x * kToepCols + tx;
+  const int gmax = 2 * N + 1;  // last entry of the g table
+  const int nl = threadIdx.x % TN, cs = threadIdx.x / TN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * TN, n = n0 + nl;
   const int64_t i0 = (int64_t)blockIdx.y * MT;
   const int64_t left = m_rows - i0;
   const int nr = left < MT ? (int)left : MT;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float2 acc[MT];
 #pragma unroll
   for (int r = 0; r < MT; ++r) acc[r] = make_float2(0.f, 0.f);
   for (int c0 = 0; c0 < N; c0 += kToepChunk) {
     const int cw = min(kToepChunk, N - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < MT * kToepChunk; e += 256) {
-      const int r = e / kToepChunk, c = e - r * kToepChunk;
-      xs[r][c] = (r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
+    float2 v[kLd];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int e = threadIdx.x + j * 256;
+      const int r = e / kToepChunk, c = e % kToepChunk;
+      v[j] = (e < kXs && r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();  // the previous chunk's readers are done
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int e = threadIdx.x + j * 256;
+      if (e < kXs) xs[e] = v[j];
+    }
+    // differences n - m = (n0 - c0 - cw + 1) + j and sums n + m + 2 = (n0 + c0 + 2) + j
+    const int dlo = n0 - c0 - cw + 1, slo = n0 + c0 + 2;
+    for (int j = threadIdx.x; j < TN + cw - 1; j += 256) {
+      const int ia = abs(dlo + j), is = slo + j;
+      gd[j] = ia <= gmax ? g[ia] : z4;
+      gs[j] = is <= gmax ? g[is] : z4;
     }
     __syncthreads();
     if (n < N) {
-      constexpr int per = kToepChunk / kToepSplit;
-      const int q0 = ty * per, q1 = min(q0 + per, cw);
-      for (int c = q0; c < q1; ++c) {
-        float2 u = toeplitz_u(g, n, c0 + c);
+#pragma unroll 4
+      for (int c = cs; c < cw; c += P) {
+        const float4 a = gd[nl - c + cw - 1], b = gs[nl + c];
+        float2 u = make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
         if (adjoint) u.y = -u.y;
 #pragma unroll
         for (int r = 0; r < MT; ++r) {
-          const float2 x = xs[r][c];
+          const float2 x = xs[r * kToepChunk + c];
           acc[r].x = fmaf(u.x, x.x, fmaf(-u.y, x.y, acc[r].x));
           acc[r].y = fmaf(u.x, x.y, fmaf(u.y, x.x, acc[r].y));
         }
       }
     }
   }
-  if (ty > 0) {
+  // the parts of one output inside a warp sit on lanes nl, nl + TN, ...
 #pragma unroll
-    for (int r = 0; r < MT; ++r) part[ty - 1][r][tx] = acc[r];
-  }
-  __syncthreads();
-  if (ty == 0 && n < N) {
-    const float sc = (float)rows.scale;
+  for (int off = TN; off < 32; off <<= 1) {
 #pragma unroll
     for (int r = 0; r < MT; ++r) {
-      if (r >= nr) break;
-      float2 y = acc[r];
+      acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+      acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+    }
+  }
+  __syncthreads();  // every reader of xs is done: it now holds the partials
+  float2* part = xs;  // [warp][r][o]
+  if (lane < TN) {
 #pragma unroll
-      for (int t = 0; t < kToepSplit - 1; ++t) {
-        y.x += part[t][r][tx].x;
-        y.y += part[t][r][tx].y;
+    for (int r = 0; r < MT; ++r) part[(warp * MT + r) * TN + lane] = acc[r];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < MT * TN; e += 256) {
+    const int r = e / TN, o = e % TN;
+    const int no = n0 + o;
+    if (r < nr && no < N) {
+      float2 y = part[r * TN + o];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) {
+        y.x += part[(w * MT + r) * TN + o].x;
+        y.y += part[(w * MT + r) * TN + o].y;
       }
-      float2* d = half + rowmap_out(rows, i0 + r) * N + n;
+      float2* d = half + rowmap_out(rows, i0 + r) * N + no;
       if (rows.accumulate) {
         y.x += d->x;
         y.y += d->y;
         if (rows.scale != 1.0) {
+          const float sc = (float)rows.scale;
           y.x *= sc;
           y.y *= sc;
         }
@@ -993,18 +1044,32 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
   }
 }
 
+template <int MT>
+void toeplitz_rows_tn(int tn, dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
+                      const RowMap& rows, int64_t m) {
+  if (tn == 32)
+    k_toeplitz_rows<MT, 32><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
+  else if (tn == 16)
+    k_toeplitz_rows<MT, 16><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
+  else
+    k_toeplitz_rows<MT, 8><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
+}
+
 hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
                                 cudaStream_t st) {
-  const int N = 1 << n_s;
+  const int64_t N = 1LL << n_s;
   const int mt = m >= 16 ? 16 : (int)m;  // m is a power of two here
-  dim3 grid((unsigned)((N + kToepCols - 1) / kToepCols), (unsigned)((m + mt - 1) / mt));
+  const int64_t groups = (m + mt - 1) / mt;
+  int tn = 32;  // outputs per block: the widest that still gives two blocks per SM
+  while (tn > 8 && ((N + tn - 1) / tn) * groups < 2 * 152) tn /= 2;
+  dim3 grid((unsigned)((N + tn - 1) / tn), (unsigned)groups);
   HHL_PROF_BEGIN(st);
   switch (mt) {
-    case 1: k_toeplitz_rows<1><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 2: k_toeplitz_rows<2><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 4: k_toeplitz_rows<4><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    case 8: k_toeplitz_rows<8><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
-    default: k_toeplitz_rows<16><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m); break;
+    case 1: toeplitz_rows_tn<1>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 2: toeplitz_rows_tn<2>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 4: toeplitz_rows_tn<4>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 8: toeplitz_rows_tn<8>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    default: toeplitz_rows_tn<16>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
   }
   HHL_LAUNCH_CHECK("k_toeplitz_rows");
   return HHL_OK;
