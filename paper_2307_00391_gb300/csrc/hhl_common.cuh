@@ -376,12 +376,14 @@ void tc_work_free(TcWork& w);
 // The split-FP16 tcgen05 GEMM with explicit operands (row gather + stream-K GEMM of one
 // controlled product) on m_sub (a multiple of 128) rows mapped by `rows`: bn = 128 or 256
 // output real columns per tile; the maps describe the FP16 a_hi / a_lo (M_sub x 2N) and the
-// embedded operand hi / lo (2N x 2N, both scaled by 2^15) with boxes (64 x 128) and (64 x bn).
+// embedded operand hi / lo (2N x 2N, both scaled by 2^15) with boxes (32 x 128) and (32 x bn).
 // streamk = 0: one CTA per output tile; 1: stream-K over the SMs when the tiles are few.
+// slice4 (optional): the embedded operand's hi / lo maps with a (32 x bn / 4) box, which lets
+// a one-CTA-per-tile launch share each B tile across a cluster of 4 CTAs (TMA multicast).
 hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& rows, void* half, void* a_hi, void* a_lo,
                               const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
                               const CUtensorMap& map_blo, int bn, int* err, const TcWork& w, int streamk,
-                              cudaStream_t st);
+                              cudaStream_t st, const CUtensorMap* slice4 = nullptr);
 // The plan's tcgen05 product on mapped rows (m_sub a multiple of 128).
 hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, int64_t m_sub, int k, bool adjoint,
                                 cudaStream_t st);

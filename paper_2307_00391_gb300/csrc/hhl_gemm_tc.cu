@@ -22,14 +22,18 @@
 // straight back into those state rows.
 //
 // Kernel (persistent, stream-K): the work is the list of (output tile, K step) units, tile-major,
-// 128 x BN tiles of K / 64 steps each; the grid has one CTA per SM (fewer when there are few
+// 128 x BN tiles of K / 32 steps each; the grid has one CTA per SM (fewer when there are few
 // units, every CTA keeping at least a quarter of a tile's steps) and CTA b takes the contiguous
 // units [b U / G, (b + 1) U / G), so every SM does the same number of MMAs whatever the number
 // of rows (a 128-row product no longer runs on 8 SMs only). When the tiles alone fill most of
-// the SMs the grid is one CTA per tile instead (each range is one whole tile): the large
-// products are bound by the operand stream from L2, which a finer split does not shorten, and
-// the split tiles' partials would cost a second pass. Its range is a sequence of tile
-// segments. Roles: warp 0 (one lane) issues the TMA loads (128-byte swizzle) into a ring of
+// the SMs the grid is one CTA per tile instead (each range is one whole tile): a large product
+// is bound by the operand bytes each SM takes in per stage (48 KiB of A and B for six MMAs),
+// which a finer split does not reduce, and the split tiles' partials would cost a second pass.
+// One CTA per tile also lets clusters of four CTAs (four consecutive row tiles of one column
+// tile) share the B operand: each loads a quarter of every B stage and multicasts it to all
+// four, which cuts the L2 reads by 43% (the SM intake stays the same). Its range is a sequence of tile
+// segments. Roles: warp 0 (one lane) issues the TMA loads (64-byte swizzle, 32 K elements per
+// stage: four stages at BN = 256, six at 128) into a ring of
 // shared-memory stages, across segment boundaries; warp 1 (one lane) issues the MMAs
 // (M = 128, N = BN, K = 16) into one of two BN-column TMEM accumulators, alternating per
 // segment, so that the epilogue of one segment overlaps the MMAs of the next; warps 2-5 drain
@@ -61,15 +65,15 @@ namespace {
 
 constexpr int kBM = 128;           // output rows per CTA (MMA M)
 constexpr int kBN = 256;           // output real columns per CTA (MMA N), plan path
-constexpr int kBK = 64;            // fp16 K elements per stage (128 bytes: one swizzle row)
-constexpr int kTileA = kBM * kBK * 2;   // 16 KiB
+constexpr int kBK = 32;            // fp16 K elements per stage (64 bytes: one swizzle row)
+constexpr int kTileA = kBM * kBK * 2;   // 8 KiB
 constexpr int kThreadsTc = 192;    // producer warp, MMA warp, four epilogue warps
 constexpr float kOpScale = 32768.0f;    // 2^15 on each operand
 constexpr float kUnscale = 1.0f / (32768.0f * 32768.0f);  // 2^-30 on the product
 template <int BN> struct TcShape {
-  static constexpr int kTileB = BN * kBK * 2;                     // 32 KiB at BN = 256
+  static constexpr int kTileB = BN * kBK * 2;                     // 16 KiB at BN = 256
   static constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;     // A_hi, A_lo, B_hi, B_lo
-  static constexpr int kStages = BN == 256 ? 2 : 3;               // 192 KiB of stages either way
+  static constexpr int kStages = BN == 256 ? 4 : 6;               // 192 KiB of stages either way
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
   static constexpr int kTmemCols = 2 * BN;                        // two fp32 accumulators
 };
@@ -84,6 +88,7 @@ struct TcState {
   TcWork work;             // stream-K partials and tile counters
   int bn = kBN;           // output tile width (128 or 256)
   std::vector<CUtensorMap> maps;  // [0] A_hi, [1] A_lo, then per k: fwd_hi, fwd_lo, adj_hi, adj_lo
+  std::vector<CUtensorMap> smaps; // per k the same four with a quarter-height box (cluster slices)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -159,14 +164,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+// The same box delivered to the same shared-memory offset of every CTA in `mask` (this GPU's
+// own memory; each destination's mbarrier at the same offset receives the bytes it got).
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle (rows of 32 FP16), 8-row
+// atoms 512 B apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;                   // descriptor version
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
   return d;
 }
 
@@ -187,6 +208,16 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// Arrive on the mbarrier at the same offset in every CTA of `mask` once this thread's MMAs so
+// far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
@@ -211,7 +242,7 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
 }
 
 
-template <int BN>
+template <int BN, int CL>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_ctrl_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                    const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
@@ -234,12 +265,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int64_t G = gridDim.x, cta = blockIdx.x;
-  const int64_t u_begin = sk_start(cta, units, G), u_end = sk_start(cta + 1, units, G);
+  int64_t u_begin = sk_start(cta, units, G), u_end = sk_start(cta + 1, units, G);
+  const int crank = (int)(cta % CL);  // rank in the cluster (clusters of CL consecutive CTAs)
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+  if (CL > 1) {
+    // one whole tile per CTA: the cluster's CL CTAs take CL consecutive row tiles of one column
+    // tile and share its B operand, each loading 1 / CL of it for all of them
+    const int64_t rest = cta / CL;
+    const int64_t t = ((rest / tiles_n) * CL + crank) * tiles_n + rest % tiles_n;
+    u_begin = t * k_iters;
+    u_end = u_begin + k_iters;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], CL);  // a stage is free once every CTA it is delivered to has read it
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&tfull_bar[s], 1);
@@ -258,6 +299,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (CL > 1) cluster_sync_all();  // every CTA's barriers are initialised before any remote signal
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
@@ -277,8 +319,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           const int kx = it * kBK;
           tma_load_2d(st, &map_ahi, &full_bar[s], kx, m0);
           tma_load_2d(st + kTileA, &map_alo, &full_bar[s], kx, m0);
-          tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
-          tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
+          if (CL > 1) {  // this CTA's slice of B (BN / CL rows; the maps' box), to every CTA of the cluster
+            const uint32_t so = (uint32_t)crank * (kTileB / CL);
+            tma_load_2d_mc(st + 2 * kTileA + so, &map_bhi, &full_bar[s], kx, n0 + crank * (BN / CL), kMask);
+            tma_load_2d_mc(st + 2 * kTileA + kTileB + so, &map_blo, &full_bar[s], kx, n0 + crank * (BN / CL), kMask);
+          } else {
+            tma_load_2d(st + 2 * kTileA, &map_bhi, &full_bar[s], kx, n0);
+            tma_load_2d(st + 2 * kTileA + kTileB, &map_blo, &full_bar[s], kx, n0);
+          }
           issued = gi + 1;
         }
         u += ke - kb;
@@ -320,11 +368,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           for (int kk = 0; kk < kBK / 16; ++kk) {
             const uint32_t off = kk * 32;  // 16 fp16 = 32 bytes along K inside the swizzled row
             const uint32_t acc0 = (it > kb || kk > 0) ? 1u : 0u;
-            mma_f16(d, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, acc0);
-            mma_f16(d, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
-            mma_f16(d, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+            mma_f16(d, desc_sw64(a_hi + off), desc_sw64(b_hi + off), idesc, acc0);
+            mma_f16(d, desc_sw64(a_hi + off), desc_sw64(b_lo + off), idesc, 1u);
+            mma_f16(d, desc_sw64(a_lo + off), desc_sw64(b_hi + off), idesc, 1u);
           }
-          mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+          if (CL > 1)
+            mma_commit_mc(&empty_bar[s], kMask);  // every CTA that delivers into this stage waits on it
+          else
+            mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
         }
         if (!ok) break;
         mma_commit(&tfull_bar[buf]);  // the segment's accumulator is complete
@@ -401,6 +452,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+  // no CTA leaves while a partner may still signal its barriers or deliver into its stages
+  if (CL > 1) cluster_sync_all();
 }
 
 // The tiles the stream-K GEMM split over several CTAs: one thread per 4 output columns adds
@@ -516,7 +569,7 @@ hhl_status make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t 
   cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(HHL_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return HHL_OK;
@@ -562,6 +615,10 @@ hhl_status tc_prepare_operands(Plan& p, const double2* d_u, int k, cudaStream_t 
     for (int kk = 0; kk < p.n_c && s == HHL_OK; ++kk)
       for (int j = 0; j < 4 && s == HHL_OK; ++j)
         s = make_map(&t->maps[2 + 4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, t->bn);
+    t->smaps.resize(4 * (size_t)p.n_c);
+    for (int kk = 0; kk < p.n_c && s == HHL_OK; ++kk)
+      for (int j = 0; j < 4 && s == HHL_OK; ++j)
+        s = make_map(&t->smaps[4 * kk + j], t->b + ((size_t)kk * 4 + j) * mat, N2, N2, t->bn / 4);
     if (s != HHL_OK) return s;
     s = tc_init_kernels();
     if (s != HHL_OK) return s;
@@ -583,8 +640,9 @@ hhl_status launch_ctrl_u_tc_map(const Plan& p, void* half, const RowMap& rows, i
   const TcState* t = static_cast<const TcState*>(p.d_tc);
   if (t == nullptr) return fail(HHL_ERR_INVALID_ARG, "tcgen05 operands not prepared");
   const CUtensorMap* mb = &t->maps[2 + 4 * (size_t)k + (adjoint ? 2 : 0)];
+  const CUtensorMap* ms = &t->smaps[4 * (size_t)k + (adjoint ? 2 : 0)];
   return launch_tc_gemm_map(p.n_s, m_sub, rows, half, t->a_hi, t->a_lo, t->maps[0], t->maps[1], mb[0], mb[1], t->bn,
-                            t->err, t->work, 1, st);
+                            t->err, t->work, 1, st, ms);
 }
 
 int tc_num_sms() {
@@ -616,7 +674,7 @@ void tc_work_free(TcWork& w) {
 hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* half, void* a_hi, void* a_lo,
                               const CUtensorMap& map_ahi, const CUtensorMap& map_alo, const CUtensorMap& map_bhi,
                               const CUtensorMap& map_blo, int bn, int* err, const TcWork& w, int streamk,
-                              cudaStream_t st) {
+                              cudaStream_t st, const CUtensorMap* slice4) {
   const int64_t N2 = 2LL << n_s;
   if (m_sub < kBM || m_sub % kBM != 0) return fail(HHL_ERR_INVALID_ARG, "tcgen05 GEMM rows must be a multiple of 128");
   if (bn != 128 && bn != 256) return fail(HHL_ERR_INVALID_ARG, "tcgen05 tile width must be 128 or 256");
@@ -645,15 +703,50 @@ hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* hal
     if (G < 1) G = 1;
     if (G > w.grid_cap) G = w.grid_cap;
   }
+  // one CTA per tile with quarter-height B maps: clusters of 4 consecutive row tiles share the
+  // B operand (HHL_TC_CLUSTER=1 turns the sharing off)
+  static const int cl_env = [] {
+    const char* e = getenv("HHL_TC_CLUSTER");
+    return e != nullptr ? atoi(e) : 4;
+  }();
+  const int64_t tiles_m = m_sub / kBM;
+  const int cl = (G == tiles && slice4 != nullptr && cl_env == 4 && tiles_m % 4 == 0) ? 4 : 1;
   HHL_PROF_BEGIN(st);
-  if (bn == 256)
-    k_ctrl_gemm_tc<256><<<(unsigned)G, kThreadsTc, TcShape<256>::kSmemBytes, st>>>(
+  if (cl == 4) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(kThreadsTc);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 4;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    float* sh = (float*)half;
+    float* wsp = w.ws;
+    const int ti = (int)tiles_n;
+    cudaError_t e;
+    if (bn == 256) {
+      cfg.dynamicSmemBytes = TcShape<256>::kSmemBytes;
+      e = cudaLaunchKernelEx(&cfg, k_ctrl_gemm_tc<256, 4>, map_ahi, map_alo, slice4[0], slice4[1], sh, n_s, k, k_iters,
+                             ti, units, wsp, err, wait_cycles, fault);
+    } else {
+      cfg.dynamicSmemBytes = TcShape<128>::kSmemBytes;
+      e = cudaLaunchKernelEx(&cfg, k_ctrl_gemm_tc<128, 4>, map_ahi, map_alo, slice4[0], slice4[1], sh, n_s, k, k_iters,
+                             ti, units, wsp, err, wait_cycles, fault);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "k_ctrl_gemm_tc (cluster launch)");
+  } else if (bn == 256) {
+    k_ctrl_gemm_tc<256, 1><<<(unsigned)G, kThreadsTc, TcShape<256>::kSmemBytes, st>>>(
         map_ahi, map_alo, map_bhi, map_blo, (float*)half, n_s, k, k_iters, (int)tiles_n, units, w.ws, err,
         wait_cycles, fault);
-  else
-    k_ctrl_gemm_tc<128><<<(unsigned)G, kThreadsTc, TcShape<128>::kSmemBytes, st>>>(
+  } else {
+    k_ctrl_gemm_tc<128, 1><<<(unsigned)G, kThreadsTc, TcShape<128>::kSmemBytes, st>>>(
         map_ahi, map_alo, map_bhi, map_blo, (float*)half, n_s, k, k_iters, (int)tiles_n, units, w.ws, err,
         wait_cycles, fault);
+  }
   HHL_LAUNCH_CHECK("k_ctrl_gemm_tc");
   // the split tiles, if any (a range boundary inside a tile): partials added in CTA order
   bool split = false;
@@ -672,9 +765,13 @@ hhl_status launch_tc_gemm_map(int n_s, int64_t m_sub, const RowMap& k, void* hal
 }
 
 hhl_status tc_init_kernels() {
-  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcShape<256>::kSmemBytes));
-  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcShape<128>::kSmemBytes));
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcShape<256>::kSmemBytes));
+  HHL_CUDA_TRY(cudaFuncSetAttribute(k_ctrl_gemm_tc<128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcShape<128>::kSmemBytes));
   return HHL_OK;
 }
