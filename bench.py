@@ -216,6 +216,7 @@ def _oracle_batch_sample(budget_s: float) -> dict:
             break
     est = sum(flops) / (f_sum / t_sum)
     return {"value": len(inst) / est, "unit": "HHL solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "extrapolated": True,
             "sample": f"{len(done)} oracle solves of batch instances with n_s <= 9 ({t_sum:.1f} s, plan excluded); "
                       f"batch time extrapolated by controlled-product flops"}
 
@@ -358,6 +359,7 @@ def _oracle_trotter_sample(wl: dict, budget_s: float) -> dict:
     est = 2 * (R // 2) * sum(t_row.values()) + N * (t_clock + t_h)
     value = algorithmic_bytes_per_solve(wl) / est / 1e9
     return {"value": value, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+            "extrapolated": True,
             "sample": f"oracle units of one solve ({sum(t_cnt.values())} controlled Strang products on one "
                       f"2^{n_s}-amplitude row each, over {len(t_row)} clock bits; one clock-block column, one Hadamard column; "
                       f"{time.perf_counter() - t_start:.1f} s), extrapolated to the whole solve "
@@ -385,6 +387,7 @@ def _oracle_qft_sample(wl: dict, budget_s: float) -> dict:
     est = t0 * (n * (n + 1) * 2.0 ** n) / (n0 * (n0 + 1) * 2.0 ** n0) * wl["states"]
     value = 4.0 * wl["states"] * (2 ** n) * 8 / est / 1e9
     return {"value": value, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+            "extrapolated": not (n == n0 and wl["states"] == 1),
             "sample": f"{len(times)} oracle QFT-IQFT circuits on {n0}-qubit random states "
                       f"({sum(times):.1f} s)" + ("" if n == n0 and wl["states"] == 1 else
                                                  f", extrapolated to {wl['states']} x {n} qubits by gates x amplitudes")}
@@ -411,6 +414,7 @@ def cpu_baseline_sample(workload: str, budget_s: float = 30.0) -> dict:
         if time.perf_counter() - t_start > budget_s or len(times) >= 50:
             break
     return {"value": len(times) / sum(times), "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
+            "extrapolated": False,
             "sample": f"{len(times)} whole oracle solve(s) of {workload} (plan excluded), "
                       f"{sum(times):.1f} s, numpy BLAS threads = {os.environ.get('OPENBLAS_NUM_THREADS', 'default')}"}
 
@@ -492,7 +496,7 @@ def run_reference(args, rank: int, world: int) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"]}, "impl": "reference",
         "cpu_baseline": {"value": value, "unit": wl["unit"], "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{len(times)} whole oracle solves (plan excluded)"},
+                         "extrapolated": False, "sample": f"{len(times)} whole oracle solves (plan excluded)"},
         "e2e": {"value": value, "unit": wl["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -698,6 +702,9 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
             n_c, N = wl["n_c"], 1 << wl["n_s"]
             tc_steps = max(1, n_c - 7)
             alg["k_ctrl_gemm_tc"] = ("flop", 2.0 * 8.0 * sum(1 << k for k in range(7, n_c)) * N * N / (2 * tc_steps))
+            # the steps below 128 rows: on-the-fly Toeplitz products on the CUDA cores
+            small = [k for k in range(n_c) if k < 7]
+            alg["k_toeplitz_rows"] = ("flop", 2.0 * 8.0 * sum(1 << k for k in small) * N * N / (2 * len(small)))
     hbm_bytes_step, hbm_ms_step = 0.0, 0.0
     for name, (n, ms) in prof.items():
         kind, per = alg.get(name, (None, 0.0))
