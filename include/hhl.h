@@ -359,9 +359,11 @@ hhl_status hhl_dissipation(hhl_plan_t plan, const void* state_dev, double* eps_o
  * QPE by doubling and the uncompute by halving as controlled-U GEMMs on 2^k rows, tcgen05 where
  * 2^k >= 128, the clock block), with the outputs of hhl_measure_async and
  * hhl_dissipation_async; A must be a
- * Toeplitz tridiagonal matrix, because U_k is generated just in time from its analytic
- * eigenbasis (U_k[n][m] = g_k(|n-m|) - g_k(n+m), an O(N^2) FP64 kernel per k) instead of
- * being stored. */
+ * Toeplitz tridiagonal matrix, because U_k is not stored but expanded from its analytic
+ * eigenbasis (U_k[n][m] = g_k(|n-m|) - g_k(n+m)): hhl_batch_create computes the g_k of every
+ * instance (an O(N^2) FP64 kernel per k, kept on the device as double-float pairs), and each
+ * run generates U_k from them on the fly (tree steps below 128 rows) or expands it into a
+ * per-stream GEMM operand right before its product. */
 typedef struct hhl_batch_s* hhl_batch_t;
 
 typedef struct hhl_batch_info {

@@ -1,26 +1,30 @@
 // Batched HHL: many instances of uneven size (system register n_s, clock n_c, right-hand
 // side, T0), complex64 amplitudes, run as one CUDA graph.
 //
-// Each instance is the same circuit as the single-plan path (same kernels). What changes is
+// Each instance runs the postselected solve of the single-plan path (hhl_solve_postselected:
+// QPE by doubling from the prepared clock = 0 row, the clock block with the anc = 0 weights
+// summed, the uncompute and final Hadamards folded by halving into one row). What changes is
 // how the controlled products get their operands: a batch of a few hundred instances cannot
 // hold every U_k (at N = 4096 the split-FP16 operands of one instance alone are ~6.4 GB), so
-// every U_k is generated just in time from the eigen-decomposition of the Toeplitz
-// tridiagonal A. With v_j(i) = sqrt(2/(N+1)) sin(i j pi/(N+1)), the product formula
+// every U_k comes from the eigen-decomposition of the Toeplitz tridiagonal A. With
+// v_j(i) = sqrt(2/(N+1)) sin(i j pi/(N+1)), the product formula
 // sin a sin b = (cos(a-b) - cos(a+b))/2 turns U_k = V diag(e^{i lambdahat_j t_k}) V^T into
 //     U_k[n][m] = g_k(|n - m|) - g_k(n + m)   (1-based n, m),
-//     g_k(d) = 1/(N+1) sum_{j=1..N} cos(d j pi/(N+1)) e^{i lambdahat_j t_k},
-// so one FP64 kernel computes the 2N+2 values of g_k for every k of an instance (O(N^2)
-// each), and one expansion kernel writes the GEMM operand of a controlled product (the
-// split-FP16 real embedding for the tensor-core GEMM, or the complex64 matrix for the
-// CUDA-core GEMM) into a per-stream workspace right before it is used.
+//     g_k(d) = 1/(N+1) sum_{j=1..N} cos(d j pi/(N+1)) e^{i lambdahat_j t_k}.
+// The g_k of every instance (2N+2 values per k, O(N^2) FP64 work each, kept as double-float
+// pairs: n_c (2N+2) x 16 bytes per instance) depend on A, T0 and k only, so one FP64 kernel
+// computes them when the batch is created, as a plan computes its U_k. The tree steps on
+// fewer than 128 rows generate U_k on the fly from g_k (k_toeplitz_rows); the larger ones get
+// their GEMM operand (the split-FP16 real embedding for the tensor-core GEMM, or the complex64
+// matrix for the CUDA-core GEMM) from one expansion kernel into a per-stream workspace right
+// before it is used.
 //
 // Instances are spread over worker streams by decreasing GEMM work (longest processing
 // time first); every stream owns a workspace sized for its largest instance. The whole
-// batch (state preparation, 2 n_c controlled products, clock block, clock Hadamards,
-// postselection statistics, dissipation, for every instance) is captured once into a
-// graph, forked over the worker streams, and replayed with one launch per run. The GEMM
-// implementation of each instance (CUDA cores, or tcgen05 with 128- or 256-column tiles)
-// is given by the caller (an autotuned table) or by a size rule.
+// batch (every instance's solve, from the preparation of its right-hand side to its
+// dissipation) is captured once into a graph, forked over the worker streams, and replayed
+// with one launch per run. The GEMM implementation of each instance (CUDA cores, or tcgen05
+// with 128- or 256-column tiles) is given by the caller (an autotuned table) or by a size rule.
 #include <math.h>
 #include <string.h>
 
@@ -199,15 +203,6 @@ hhl_status enqueue_instance(hhl_batch_s* B, int i) {
   // hhl_solve_postselected): only the clock = 0 row of the anc = 0 half is prepared
   if (s == HHL_OK) s = launch_prep_row(p, b, state, st);
   if (s != HHL_OK) return s;
-  // g_k for every k of this instance
-  {
-    const int M = (int)(2 * p.N + 2);
-    dim3 grid((unsigned)((M + 255) / 256), (unsigned)p.n_c);
-    HHL_PROF_BEGIN(st);
-    k_ugen_g<<<grid, 256, p.N * sizeof(double2), st>>>((int)p.N, B->d_ph + B->ph_off[i], B->d_cos + B->cos_off[i],
-                                                       B->d_g + B->g_off[i]);
-    HHL_LAUNCH_CHECK("k_ugen_g");
-  }
   const int M = (int)(2 * p.N + 2);
   // tree step k: expansion (rows [2^k, 2^(k+1)) = U_k rows [0, 2^k), anc = 0 half) or
   // reduction (rows [0, 2^k) += U_k^dagger rows [2^k, 2^(k+1)), anc = 1 half, the last step
@@ -453,6 +448,15 @@ hhl_status hhl_batch_create(const hhl_problem* probs, const hhl_params* params, 
     cudaError_t e = cudaFuncSetAttribute(k_ugen_g, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<int64_t>(maxN * (int64_t)sizeof(double2), 1024));
     if (e != cudaSuccess) s = cuda_fail(e, "cudaFuncSetAttribute(k_ugen_g)");
+  }
+  // g_k for every k of every instance, once (they depend on A, T0 and k only)
+  for (int i = 0; i < count && s == HHL_OK; ++i) {
+    const Plan& p = B->plans[i];
+    const int M = (int)(2 * p.N + 2);
+    dim3 grid((unsigned)((M + 255) / 256), (unsigned)p.n_c);
+    k_ugen_g<<<grid, 256, p.N * sizeof(double2), B->work[B->stream_of[i]].s>>>(
+        (int)p.N, B->d_ph + B->ph_off[i], B->d_cos + B->cos_off[i], B->d_g + B->g_off[i]);
+    if (cudaError_t le = cudaGetLastError(); le != cudaSuccess) s = cuda_fail(le, "k_ugen_g");
   }
   if (s == HHL_OK) {
     cudaError_t e = cudaDeviceSynchronize();
