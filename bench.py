@@ -69,6 +69,9 @@ WORKLOADS = {
 # source is unchanged (otherwise null, the counters no longer describe the kernel).
 KERNEL_TRAFFIC = {
     ("poiseuille_2p18", "c64", "k_trotter_pass"): (0.9623, "hhl_trotter.cu", "6a3e7c3a12a397fd"),
+    # DRAM bytes per launch of the full-size product (mean of three launches of one capture; the
+    # operands A and B once each, hi and lo; the rows it writes stay in L2)
+    ("couette_1024", "c64", "k_ctrl_gemm_tc"): (33.635e6, "hhl_gemm_tc.cu", "1ff6a778caf96620", "bytes"),
 }
 
 
@@ -82,7 +85,9 @@ def _traffic(workload: str, precision: str, kernel: str, algorithmic: float):
         digest = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return ent[0] * algorithmic if digest == ent[2] else None
+    if digest != ent[2]:
+        return None
+    return ent[0] if len(ent) > 3 and ent[3] == "bytes" else ent[0] * algorithmic
 
 
 def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
@@ -722,7 +727,7 @@ def solve_block(pkg, workload: str, precision: str, gemm: str, steps: int, warmu
         "precision": precision, "value": value, "unit": wl["unit"],
         "solves_per_s": replica_rate(steps, world, total_s),
         "ms_per_step": 1e3 * total_s / steps, "steps": steps, "warmup": warmup,
-        "roofline": _roofline(prof, alg, _peaks(), workload, precision,
+        "roofline": _roofline(prof, alg, _peaks(), workload + ("_postselected" if postselected else ""), precision,
                               "per-launch CUDA events on the launching stream, second timed loop of the same steps"),
         "gate_gbs": {"bytes_per_step": hbm_bytes_step, "ms_per_step": hbm_ms_step,
                      "achieved_gbs": hbm_bytes_step / (hbm_ms_step / 1e3) / 1e9 if hbm_ms_step else None},
