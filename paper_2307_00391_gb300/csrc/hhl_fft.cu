@@ -1048,11 +1048,19 @@ __device__ __forceinline__ void split_tile(const SplitArgs& a, const TilePos& q,
   }
 }
 
+// CTAs per SM the register budget is set for: three for complex64 and for the double-float
+// passes with one transform per tile (80 registers, no spills; measured faster than two at
+// 122-127 registers), two for the FP64-pipe forms and the double-float pass B (two transforms
+// and the rotation per tile: measured slower at three).
+template <class R, int OP>
+constexpr int kSplitMinBlocks =
+    (sizeof(R) == 4 || (std::is_same<R, df>::value && OP != kSplitMid && OP != kSplitMidSums)) ? 3 : 2;
+
 // WHOLE: the register is the whole index range [0, lo + m) of each outer block, the tile
 // rows are its bits [lo + b0, lo + b0 + NB) and the twiddles are those of the 2^(lo + m) point
 // transform (four-level shared-memory tables); only the DIF and DIT passes are used this way.
 template <class R, int OP, bool FULL, int NB, bool WHOLE = false>
-__global__ void __launch_bounds__(kSplitThreads, sizeof(R) == 4 ? 3 : 2) k_split_pass(SplitArgs a) {
+__global__ void __launch_bounds__(kSplitThreads, kSplitMinBlocks<R, OP>) k_split_pass(SplitArgs a) {
   using T = typename Cx<R>::T;
   constexpr int LW = SplitGeom<T>::LW;
   constexpr int per = 16 / sizeof(T);
