@@ -87,6 +87,23 @@ void prof_end(const char* name) {
   t_begin_ev = nullptr;
 }
 
+// The largest dynamic shared memory set so far per (device, kernel): the attribute is only
+// ever raised. Launches of one kernel with different sizes (the instances of a batch, captured
+// into one graph) then all stay within the attribute, whichever size was set last.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set_to;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set_to[{dev, func}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 void set_error(const std::string& msg) { t_last_error = msg; }
 hhl_status fail(hhl_status s, const std::string& msg) {
   t_last_error = msg;

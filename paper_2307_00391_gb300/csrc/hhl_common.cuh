@@ -14,6 +14,8 @@ namespace hhl {
 
 // ------------------------------------------------------------------ error reporting
 void set_error(const std::string& msg);
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current device.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
 hhl_status fail(hhl_status s, const std::string& msg);
 hhl_status cuda_fail(cudaError_t e, const char* what);
 extern std::atomic<uint64_t> g_launches;

@@ -574,7 +574,7 @@ hhl_status lowbits_transform(void* state, int n, int m, int mode, R scale, cudaS
   const int L = 1 << m, Lp = L + L / 16 + 1, Lpa = (Lp + 1) & ~1;
   const size_t smem = ((size_t)twiddle_entries(m) + 1 + 2 * (size_t)Lpa) * sizeof(T);
   auto kern = k_lowbits_transform<R>;
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -630,7 +630,7 @@ bool choose_shape(int m, int64_t limit, int buffers, int* W_out, int* cb_out, si
 template <class Kern>
 hhl_status launch_cluster(Kern kernel, int grid, int cb, size_t smem, cudaStream_t st, const char* name,
                           void** args) {
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kernel, smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kFftThreads);
@@ -1145,7 +1145,7 @@ hhl_status launch_split_nb(const SplitArgs& a, cudaStream_t st, const char* name
   const size_t tile = ((size_t)1 << (NB + SplitGeom<T>::LW)) * sizeof(T);
   const size_t smem = (size_t)(WHOLE ? 1024 : twiddle_entries(a.m)) * sizeof(T) + ((OP == kSplitMid && FULL) ? 3 : 2) * tile;
   auto kern = k_split_pass<R, OP, FULL, NB, WHOLE>;
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1311,7 +1311,7 @@ hhl_status launch_group_nb(const GroupArgs& g, int outer, cudaStream_t st, const
   auto kern = k_group_pass<R, KIND, FULL, NBH, NBL>;
   int G = 8, budget = 128;
   group_shape(&G, &budget);
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   if (G > 8) HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kSplitThreads);
@@ -1534,7 +1534,7 @@ hhl_status hadamard_cluster_nb(void* half_base, int n_s, int m, int outer, cudaS
   constexpr int W = kClusterSegBytes / (int)sizeof(T);
   auto kern = k_hadamard_cluster<R, NB>;
   const size_t smem = ((size_t)1 << NB) * kClusterSegBytes;
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   R scale = (R)(1.0 / sqrt((double)(1LL << m)));
   for (int o = 0; o < outer; ++o) {
     cudaLaunchConfig_t cfg = {};
@@ -1613,7 +1613,7 @@ hhl_status clock_cluster_nb(const Plan& p, void* state, cudaStream_t st) {
   Twiddle3<T> tw{(const T*)tabs[0], (const T*)tabs[1], (const T*)tabs[2]};
   auto kern = k_clock_cluster<R, NB>;
   const size_t smem = clock_cluster_smem<R>(p.n_c);
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((p.N / W) * kClusterCtas));
   cfg.blockDim = dim3(kClusterThreads);

@@ -829,7 +829,7 @@ hhl_status tree_impl(const Plan& p, void* half, const TrotPassDesc& d, cudaStrea
   const int64_t segs = (p.N + Geo<LA>::INTER - 1) / Geo<LA>::INTER;
   const size_t smem = trotter_smem<R, DF>();
   auto kern = k_trotter_tree<R, DF, RED>;
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -866,7 +866,7 @@ hhl_status trotter_impl(const Plan& p, void* half, bool adjoint, cudaStream_t st
   const LayerList* lists = (const LayerList*)p.d_trot_lists;
   const size_t smem = trotter_smem<R, DF>();
   auto kern = k_trotter_pass<R, DF>;
-  HHL_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HHL_CUDA_TRY(raise_dyn_smem((const void*)kern, smem));
   int dev = 0, sms = 0, occ = 0;
   HHL_CUDA_TRY(cudaGetDevice(&dev));
   HHL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
