@@ -304,8 +304,12 @@ hhl_status hhl_apply_stage(hhl_plan_t plan, int32_t stage, void* state_dev, void
  * state_dev is the plan's state buffer used as workspace: afterwards only the clock = 0 row of
  * the anc = 1 half is defined (it holds v, so hhl_dissipation, hhl_sample and
  * hhl_qpp_dissipation may read it; hhl_measure may not). Asynchronous.
- * Dense plans run the two trees as controlled-U GEMMs on 2^k rows (tcgen05 where 2^k >= 128,
- * CUDA cores below); Strang-Trotter plans as grouped Strang passes.
+ * Dense plans run the two trees as controlled-U products on 2^k rows: tcgen05 GEMMs where
+ * 2^k >= 128 (a stream-K grid over the SMs when the product has few tiles, its split tiles added
+ * in a fixed order, so results repeat bit for bit), below that on the CUDA cores (for a
+ * Toeplitz tridiagonal A with U_k generated on the fly from its eigenbasis; the threshold moves
+ * with the environment variable HHL_TOEP_ROWS=<rows>); Strang-Trotter plans as grouped Strang
+ * passes.
  * Errors: HHL_ERR_UNSUPPORTED unless full_uncompute = 0 and, for Strang-Trotter plans, every
  * clock bit's layer list fits one pass (2 r_k + 1 <= 17). */
 hhl_status hhl_solve_postselected(hhl_plan_t plan, const double* b_dev, void* state_dev, double* out_dev,
