@@ -925,12 +925,16 @@ hhl_status launch_g_to_df(int N, const double2* d_g, float4* gdf, cudaStream_t s
 // operand is written or read. A block owns TN output columns n of MT rows (MT = min(16, rows
 // of the step); TN = 8, 16 or 32, the largest that still gives two blocks per SM) and splits
 // the sum over m in 256 / TN parts: thread t takes n = n0 + t % TN and every (256 / TN)-th
-// column of each chunk of 256 columns. Per chunk the block stages the x rows and the g entries
-// the chunk needs (its TN + 255 differences n - m and sums n + m + 2) in shared memory, the
-// loads of a thread issued together; the parts of each output are added by shuffles inside the
-// warp, then across the 8 warps in shared memory (reusing the x buffer). Output rows are mapped
-// as the GEMMs' (write, or add to the row and scale).
-constexpr int kToepChunk = 256;
+// column of each chunk of CH columns (1024 for blocks of up to 4 rows, whose chunks are
+// latency-bound round trips with little arithmetic, else 256). Per chunk the block stages the
+// x rows and the g entries the chunk needs (its TN + CH - 1 differences n - m and sums
+// n + m + 2) in shared memory, the loads of a thread issued together; the parts of each output
+// are added by shuffles inside the warp, then across the 8 warps in shared memory (reusing the
+// x buffer). Output rows are mapped as the GEMMs' (write, or add to the row and scale).
+template <int MT> constexpr int toep_chunk() { return MT <= 4 ? 1024 : 256; }
+template <int MT, int TN> constexpr int toep_smem() {
+  return MT * toep_chunk<MT>() * (int)sizeof(float2) + 2 * (TN + toep_chunk<MT>()) * (int)sizeof(float4);
+}
 
 // Tree steps on fewer rows than this take the on-the-fly Toeplitz product instead of a GEMM
 // (128 by default: the tensor-core tiles start at 128 rows); HHL_TOEP_ROWS=<power of two>
@@ -948,11 +952,15 @@ template <int MT, int TN>
 __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half, int n_s, const float4* __restrict__ g,
                                                        int adjoint, RowMap rows, int64_t m_rows) {
   constexpr int P = 256 / TN;                      // parts of each output
-  constexpr int kXs = MT * kToepChunk;             // staged x values per chunk
+  constexpr int CH = toep_chunk<MT>();             // columns per chunk
+  constexpr int kXs = MT * CH;                     // staged x values per chunk
   constexpr int kLd = (kXs + 255) / 256;           // x loads per thread per chunk
+  constexpr int kGl = (TN + CH + 255) / 256;       // g entries per thread per chunk
   static_assert(8 * MT * TN <= kXs, "partials reuse the x buffer");
-  __shared__ float2 xs[kXs];
-  __shared__ float4 gd[TN + kToepChunk], gs[TN + kToepChunk];
+  extern __shared__ __align__(16) unsigned char toep_smem_raw[];
+  float2* xs = reinterpret_cast<float2*>(toep_smem_raw);   // [kXs]
+  float4* gd = reinterpret_cast<float4*>(xs + kXs);        // [TN + CH]: g(|n - m|)
+  float4* gs = gd + (TN + CH);                             // [TN + CH]: g(n + m + 2)
   const int N = 1 << n_s;
   const int gmax = 2 * N + 1;  // last entry of the g table
   const int nl = threadIdx.x % TN, cs = threadIdx.x / TN;
@@ -965,14 +973,25 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
   float2 acc[MT];
 #pragma unroll
   for (int r = 0; r < MT; ++r) acc[r] = make_float2(0.f, 0.f);
-  for (int c0 = 0; c0 < N; c0 += kToepChunk) {
-    const int cw = min(kToepChunk, N - c0);
+  for (int c0 = 0; c0 < N; c0 += CH) {
+    const int cw = min(CH, N - c0);
+    // differences n - m = (n0 - c0 - cw + 1) + j and sums n + m + 2 = (n0 + c0 + 2) + j
+    const int dlo = n0 - c0 - cw + 1, slo = n0 + c0 + 2;
     float2 v[kLd];
+    float4 ga[kGl], gb[kGl];
 #pragma unroll
     for (int j = 0; j < kLd; ++j) {
       const int e = threadIdx.x + j * 256;
-      const int r = e / kToepChunk, c = e % kToepChunk;
+      const int r = e / CH, c = e % CH;
       v[j] = (e < kXs && r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kGl; ++q) {
+      const int j = threadIdx.x + q * 256;
+      const int ia = abs(dlo + j), is = slo + j;
+      const bool in = j < TN + cw - 1;
+      ga[q] = in && ia <= gmax ? g[ia] : z4;
+      gb[q] = in && is <= gmax ? g[is] : z4;
     }
     __syncthreads();  // the previous chunk's readers are done
 #pragma unroll
@@ -980,12 +999,13 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
       const int e = threadIdx.x + j * 256;
       if (e < kXs) xs[e] = v[j];
     }
-    // differences n - m = (n0 - c0 - cw + 1) + j and sums n + m + 2 = (n0 + c0 + 2) + j
-    const int dlo = n0 - c0 - cw + 1, slo = n0 + c0 + 2;
-    for (int j = threadIdx.x; j < TN + cw - 1; j += 256) {
-      const int ia = abs(dlo + j), is = slo + j;
-      gd[j] = ia <= gmax ? g[ia] : z4;
-      gs[j] = is <= gmax ? g[is] : z4;
+#pragma unroll
+    for (int q = 0; q < kGl; ++q) {
+      const int j = threadIdx.x + q * 256;
+      if (j < TN + CH) {
+        gd[j] = ga[q];
+        gs[j] = gb[q];
+      }
     }
     __syncthreads();
     if (n < N) {
@@ -996,7 +1016,7 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
         if (adjoint) u.y = -u.y;
 #pragma unroll
         for (int r = 0; r < MT; ++r) {
-          const float2 x = xs[r * kToepChunk + c];
+          const float2 x = xs[r * CH + c];
           acc[r].x = fmaf(u.x, x.x, fmaf(-u.y, x.y, acc[r].x));
           acc[r].y = fmaf(u.x, x.y, fmaf(u.y, x.x, acc[r].y));
         }
@@ -1044,15 +1064,22 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
   }
 }
 
+template <int MT, int TN>
+cudaError_t toeplitz_rows_launch(dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
+                                 const RowMap& rows, int64_t m) {
+  constexpr int smem = toep_smem<MT, TN>();
+  cudaError_t e = raise_dyn_smem((const void*)k_toeplitz_rows<MT, TN>, smem);
+  if (e != cudaSuccess) return e;
+  k_toeplitz_rows<MT, TN><<<grid, 256, smem, st>>>(half, n_s, g, adjoint, rows, m);
+  return cudaSuccess;
+}
+
 template <int MT>
-void toeplitz_rows_tn(int tn, dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
-                      const RowMap& rows, int64_t m) {
-  if (tn == 32)
-    k_toeplitz_rows<MT, 32><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
-  else if (tn == 16)
-    k_toeplitz_rows<MT, 16><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
-  else
-    k_toeplitz_rows<MT, 8><<<grid, 256, 0, st>>>(half, n_s, g, adjoint, rows, m);
+cudaError_t toeplitz_rows_tn(int tn, dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
+                             const RowMap& rows, int64_t m) {
+  if (tn == 32) return toeplitz_rows_launch<MT, 32>(grid, st, half, n_s, g, adjoint, rows, m);
+  if (tn == 16) return toeplitz_rows_launch<MT, 16>(grid, st, half, n_s, g, adjoint, rows, m);
+  return toeplitz_rows_launch<MT, 8>(grid, st, half, n_s, g, adjoint, rows, m);
 }
 
 hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjoint, const RowMap& rows, int64_t m,
@@ -1064,13 +1091,15 @@ hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjo
   while (tn > 8 && ((N + tn - 1) / tn) * groups < 2 * 152) tn /= 2;
   dim3 grid((unsigned)((N + tn - 1) / tn), (unsigned)groups);
   HHL_PROF_BEGIN(st);
+  cudaError_t e;
   switch (mt) {
-    case 1: toeplitz_rows_tn<1>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
-    case 2: toeplitz_rows_tn<2>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
-    case 4: toeplitz_rows_tn<4>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
-    case 8: toeplitz_rows_tn<8>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
-    default: toeplitz_rows_tn<16>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 1: e = toeplitz_rows_tn<1>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 2: e = toeplitz_rows_tn<2>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 4: e = toeplitz_rows_tn<4>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    case 8: e = toeplitz_rows_tn<8>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
+    default: e = toeplitz_rows_tn<16>(tn, grid, st, half, n_s, g, adjoint, rows, m); break;
   }
+  if (e != cudaSuccess) return cuda_fail(e, "k_toeplitz_rows (shared-memory limit)");
   HHL_LAUNCH_CHECK("k_toeplitz_rows");
   return HHL_OK;
 }
