@@ -12,6 +12,8 @@
 
 #include <stdlib.h>
 
+#include <cooperative_groups.h>
+
 #include "hhl_common.cuh"
 
 namespace hhl {
@@ -1064,6 +1066,165 @@ __global__ void __launch_bounds__(256) k_toeplitz_rows(float2* __restrict__ half
   }
 }
 
+// Blocks of MT = 4, 8 or 16 rows with the sum over m split across a cluster of 4 CTAs: CTA q of
+// the cluster takes the columns [q N / 4, (q + 1) N / 4) for the same TN outputs and MT rows (the
+// direct product above on a quarter of the columns, chunks of 256), so each CTA stages a quarter
+// of the x rows for TN outputs, and TN can be 32 with as many blocks as 8 outputs per block
+// give without the split. The CTAs' partial tiles (16 x TN, in shared memory) are added through
+// distributed shared memory in the order of the cluster ranks (the same sum on every run),
+// CTA q writing a quarter of the outputs; a second cluster barrier keeps every tile alive
+// until its readers are done.
+constexpr int kToepKs = 4;
+
+template <int MT, int TN>
+__global__ void __launch_bounds__(256) k_toeplitz_rows_ks(float2* __restrict__ half, int n_s, const float4* __restrict__ g,
+                                                          int adjoint, RowMap rows, int64_t m_rows) {
+  namespace cg = cooperative_groups;
+  constexpr int P = 256 / TN, CH = 256;
+  constexpr int kXs = MT * CH, kLd = kXs / 256, kGl = (TN + CH + 255) / 256;
+  static_assert(8 * MT * TN <= kXs, "partials reuse the x buffer");
+  __shared__ float2 xs[kXs];
+  __shared__ float4 gd[TN + CH], gs[TN + CH];
+  __shared__ float2 red[MT * TN];  // this CTA's partial tile
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int N = 1 << n_s;
+  const int gmax = 2 * N + 1;
+  const int nl = threadIdx.x % TN, cs = threadIdx.x / TN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = (int)(blockIdx.x / kToepKs) * TN, n = n0 + nl;
+  const int64_t i0 = (int64_t)blockIdx.y * MT;
+  const int64_t left = m_rows - i0;
+  const int nr = left < MT ? (int)left : MT;
+  const int kq = N / kToepKs, k_begin = q * kq, k_end = k_begin + kq;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 acc[MT];
+#pragma unroll
+  for (int r = 0; r < MT; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int c0 = k_begin; c0 < k_end; c0 += CH) {
+    const int cw = min(CH, k_end - c0);
+    const int dlo = n0 - c0 - cw + 1, slo = n0 + c0 + 2;
+    float2 v[kLd];
+    float4 ga[kGl], gb[kGl];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const int e = threadIdx.x + j * 256;
+      const int r = e / CH, c = e % CH;
+      v[j] = (r < nr && c < cw) ? half[rowmap_in(rows, i0 + r) * N + c0 + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int qq = 0; qq < kGl; ++qq) {
+      const int j = threadIdx.x + qq * 256;
+      const int ia = abs(dlo + j), is = slo + j;
+      const bool in = j < TN + cw - 1;
+      ga[qq] = in && ia <= gmax ? g[ia] : z4;
+      gb[qq] = in && is <= gmax ? g[is] : z4;
+    }
+    __syncthreads();  // the previous chunk's readers are done
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) xs[threadIdx.x + j * 256] = v[j];
+#pragma unroll
+    for (int qq = 0; qq < kGl; ++qq) {
+      const int j = threadIdx.x + qq * 256;
+      if (j < TN + CH) {
+        gd[j] = ga[qq];
+        gs[j] = gb[qq];
+      }
+    }
+    __syncthreads();
+    if (n < N) {
+#pragma unroll 4
+      for (int c = cs; c < cw; c += P) {
+        const float4 a = gd[nl - c + cw - 1], b = gs[nl + c];
+        float2 u = make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
+        if (adjoint) u.y = -u.y;
+#pragma unroll
+        for (int r = 0; r < MT; ++r) {
+          const float2 x = xs[r * CH + c];
+          acc[r].x = fmaf(u.x, x.x, fmaf(-u.y, x.y, acc[r].x));
+          acc[r].y = fmaf(u.x, x.y, fmaf(u.y, x.x, acc[r].y));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = TN; off < 32; off <<= 1) {
+#pragma unroll
+    for (int r = 0; r < MT; ++r) {
+      acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+      acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+    }
+  }
+  __syncthreads();
+  float2* part = xs;  // [warp][r][o]
+  if (lane < TN) {
+#pragma unroll
+    for (int r = 0; r < MT; ++r) part[(warp * MT + r) * TN + lane] = acc[r];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < MT * TN; e += 256) {
+    float2 y = part[e];  // e = r * TN + o
+#pragma unroll
+    for (int w = 1; w < 8; ++w) {
+      y.x += part[w * MT * TN + e].x;
+      y.y += part[w * MT * TN + e].y;
+    }
+    red[e] = y;
+  }
+  cl.sync();  // every CTA's partial tile is complete
+  constexpr int kOut = MT * TN / kToepKs;  // outputs this CTA writes (MT * TN divides by 4)
+  for (int e = q * kOut + threadIdx.x; e < (q + 1) * kOut; e += 256) {
+    const int r = e / TN, o = e % TN;
+    const int no = n0 + o;
+    float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int rr = 0; rr < kToepKs; ++rr) {
+      const float2 p = cl.map_shared_rank(red, rr)[e];
+      y.x += p.x;
+      y.y += p.y;
+    }
+    if (r < nr && no < N) {
+      float2* d = half + rowmap_out(rows, i0 + r) * N + no;
+      if (rows.accumulate) {
+        y.x += d->x;
+        y.y += d->y;
+        if (rows.scale != 1.0) {
+          const float sc = (float)rows.scale;
+          y.x *= sc;
+          y.y *= sc;
+        }
+      }
+      *d = y;
+    }
+  }
+  cl.sync();  // the partial tiles stay until every reader is done
+}
+
+template <int MT, int TN>
+cudaError_t toeplitz_rows_ks_launch(dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
+                                    const RowMap& rows, int64_t m) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kToepKs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_toeplitz_rows_ks<MT, TN>, half, n_s, g, adjoint, rows, m);
+}
+
+template <int MT>
+cudaError_t toeplitz_rows_ks_tn(int tk, dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g,
+                                int adjoint, const RowMap& rows, int64_t m) {
+  if (tk == 32) return toeplitz_rows_ks_launch<MT, 32>(grid, st, half, n_s, g, adjoint, rows, m);
+  if (tk == 16) return toeplitz_rows_ks_launch<MT, 16>(grid, st, half, n_s, g, adjoint, rows, m);
+  return toeplitz_rows_ks_launch<MT, 8>(grid, st, half, n_s, g, adjoint, rows, m);
+}
+
 template <int MT, int TN>
 cudaError_t toeplitz_rows_launch(dim3 grid, cudaStream_t st, float2* half, int n_s, const float4* g, int adjoint,
                                  const RowMap& rows, int64_t m) {
@@ -1087,6 +1248,18 @@ hhl_status launch_toeplitz_rows(float2* half, int n_s, const float4* g, int adjo
   const int64_t N = 1LL << n_s;
   const int mt = m >= 16 ? 16 : (int)m;  // m is a power of two here
   const int64_t groups = (m + mt - 1) / mt;
+  if (mt >= 4 && N >= 512) {  // the sum over m split across clusters of 4 CTAs
+    int tk = 32;
+    while (tk > 8 && ((N + tk - 1) / tk) * groups * kToepKs < 2 * 152) tk /= 2;
+    dim3 gk((unsigned)(((N + tk - 1) / tk) * kToepKs), (unsigned)groups);
+    HHL_PROF_BEGIN(st);
+    cudaError_t e = mt == 16  ? toeplitz_rows_ks_tn<16>(tk, gk, st, half, n_s, g, adjoint, rows, m)
+                    : mt == 8 ? toeplitz_rows_ks_tn<8>(tk, gk, st, half, n_s, g, adjoint, rows, m)
+                              : toeplitz_rows_ks_tn<4>(tk, gk, st, half, n_s, g, adjoint, rows, m);
+    if (e != cudaSuccess) return cuda_fail(e, "k_toeplitz_rows_ks");
+    HHL_LAUNCH_CHECK("k_toeplitz_rows");
+    return HHL_OK;
+  }
   int tn = 32;  // outputs per block: the widest that still gives two blocks per SM
   while (tn > 8 && ((N + tn - 1) / tn) * groups < 2 * 152) tn /= 2;
   dim3 grid((unsigned)((N + tn - 1) / tn), (unsigned)groups);

@@ -116,3 +116,17 @@ def test_toeplitz_threshold_keeps_oracle_parity(hhl, tmp_path, rows):
     v_ref = run_stages(b, n_s, pl)["final_h"].reshape(2, 1 << n_c, 1 << n_s)[1, 0]
     got = _child(tmp_path, {"HHL_TOEP_ROWS": rows}, n_s=n_s, n_c=n_c, mode="postselected")
     assert np.abs(got - v_ref).max() <= 1e-5
+
+
+def test_toeplitz_cluster_split_matches_oracle_and_repeats(hhl):
+    """N = 1024: the tree steps of 4-64 rows take the Toeplitz product with the sum over m
+    split across clusters of 4 CTAs (partial tiles added through distributed shared memory in
+    rank order); the postselected row against the oracle's whole circuit, and bit for bit
+    across two runs."""
+    n_s, n_c = 10, 8
+    diag, off, b, walls = problem("couette", n_s)
+    pl = o.plan(o.dense_from_tridiag(diag, off), n_c, t0_rule="range_fill")
+    v_ref = run_stages(b, n_s, pl)["final_h"].reshape(2, 1 << n_c, 1 << n_s)[1, 0]
+    a = _solve(hhl, n_s, n_c, "postselected")
+    assert np.abs(a - v_ref).max() <= 1e-5
+    assert np.array_equal(a, _solve(hhl, n_s, n_c, "postselected"))
