@@ -100,6 +100,16 @@ def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The sum of the ranks' values (counts of units done on each rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
 def replica_rate(units_per_rank: float, world: int, slowest_s: float) -> float:
     """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
     return world * units_per_rank / slowest_s
@@ -919,7 +929,10 @@ def batch_block(pkg, args, world: int, local_rank: int) -> dict:
     rate with host buffers, and every instance again through the complex128 single-instance
     plan path (CUDA-core FP64 GEMMs) on the same GPU: that loop is timed with CUDA events (the
     FP64 single-instance solves/s) and is the reference of the fidelity count
-    F = |<xhat_c128 | xhat_c64>| >= 1 - 1e-6 over all instances."""
+    F = |<xhat_c128 | xhat_c64>| >= 1 - 1e-6 over all instances.
+    With N ranks every rank runs a batch of 256 instances of its own (independent problems drawn
+    with the rank as seed offset; rank 0's batch is the one-GPU batch); the whole-job rate is all
+    ranks' instances over the slowest rank's time and the fidelity counts are summed."""
     import numpy as np
     import torch
 
@@ -927,7 +940,8 @@ def batch_block(pkg, args, world: int, local_rank: int) -> dict:
     from synth_inputs import batch_instances, walls
 
     wl = WORKLOADS["batch_256"]
-    inst = batch_instances(wl["count"])
+    rank = torch.distributed.get_rank() if world > 1 else 0
+    inst = batch_instances(wl["count"], seed_offset=rank)
     probs = []
     for it in inst:
         diag, off = pkg.laplacian(1 << it["n_s"])
@@ -1033,6 +1047,10 @@ def batch_block(pkg, args, world: int, local_rank: int) -> dict:
     elif dom is not None:
         roofline = {"kernel": dom, "bound": None, "note": "no algorithmic work model for this kernel"}
     ok = [f for f in fids if f >= 1 - 1e-6]
+    n_inst = sum_over_ranks(float(len(fids)), world)  # every rank's batch
+    n_ok = sum_over_ranks(float(len(ok)), world)
+    f_min = -max_over_ranks(-min(fids), world)
+    fp64_slowest = max_over_ranks(fp64_s, world)
     return {
         "workload": "batch_256", "desc": wl["desc"], "precision": "c64", "value": replica_rate(wl["count"] * steps, world, total_s),
         "unit": wl["unit"], "ms_per_step": 1e3 * total_s / steps, "steps": steps, "warmup": max(args.warmup, 1),
@@ -1040,10 +1058,10 @@ def batch_block(pkg, args, world: int, local_rank: int) -> dict:
                    "gemm_choices": "tuning.json" if choices else "size rule",
                    "l2": "inputs larger than L2 (all states %.1f GB)" % (binf["state_bytes"] / 1e9)},
         "roofline": roofline,
-        "fidelity": {"instances": len(fids), "at_1e-6": len(ok), "min": min(fids),
-                     "solves_per_s_at_1e-6": replica_rate(len(ok) * steps, world, total_s),
+        "fidelity": {"instances": int(n_inst), "at_1e-6": int(n_ok), "min": f_min,
+                     "solves_per_s_at_1e-6": n_ok * steps / total_s,
                      "reference": "complex128 single-instance plan path (CUDA-core FP64 GEMM), same GPU"},
-        "fp64_single_instance": {"solves_per_s": wl["count"] / fp64_s, "seconds": fp64_s, "plan_seconds": fp64_plan_s,
+        "fp64_single_instance": {"solves_per_s": n_inst / fp64_slowest, "seconds": fp64_slowest, "plan_seconds": fp64_plan_s,
                                  "timing": "CUDA events around each instance's prepare, circuit, measure and "
                                            "dissipation (plans outside), every instance"},
         "breakdown": {name: {"launches": n, "ms": ms} for name, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])},
