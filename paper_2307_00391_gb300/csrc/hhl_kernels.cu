@@ -932,7 +932,9 @@ hhl_status launch_g_to_df(int N, const double2* d_g, float4* gdf, cudaStream_t s
 // x rows and the g entries the chunk needs (its TN + CH - 1 differences n - m and sums
 // n + m + 2) in shared memory, the loads of a thread issued together; the parts of each output
 // are added by shuffles inside the warp, then across the 8 warps in shared memory (reusing the
-// x buffer). Output rows are mapped as the GEMMs' (write, or add to the row and scale).
+// x buffer). Output rows are mapped as the GEMMs' (write, or add to the row and scale). At
+// N >= 512 blocks of 4-16 rows take k_toeplitz_rows_ks below instead (the sum over m split
+// across a cluster of 4 CTAs); this kernel serves the 1- and 2-row steps and small N.
 template <int MT> constexpr int toep_chunk() { return MT <= 4 ? 1024 : 256; }
 template <int MT, int TN> constexpr int toep_smem() {
   return MT * toep_chunk<MT>() * (int)sizeof(float2) + 2 * (TN + toep_chunk<MT>()) * (int)sizeof(float4);
